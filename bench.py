@@ -1,0 +1,296 @@
+"""Benchmark: cell-updates per second of full SSP-RK3 steps of the two-phase
+WENO-IS / MOOD / HLLC solver on the 2D planar-shock / air-bubble workload
+(1024 x 1024 cells, Ms = 1.5 water shock, air bubble of radius 0.2).
+
+One "step" is one SSP-RK3 step of the whole grid: CFL reduction, and per stage
+the ghost layers, the primitive cache, the x and y face sweeps (projection,
+WENO-IS, MOOD, HLLC) and the flux-divergence + RK update, all in this
+library's CUDA kernels, with the state resident in HBM.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|mixed]
+  python bench.py --impl reference ...   # the FP64 CPU oracle on the host cores
+
+Multi-GPU (torchrun): every rank advances its own replica of the workload
+(the problems are independent; no data-path collective), value = all cells
+updated by all ranks / the slowest rank's time.  Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1707_00592_gb300 import workloads as wl  # noqa: E402
+
+METRIC = "cell-updates/s per RK3 step"
+UNIT = "cell-updates/s"
+L2_BYTES = 129 * 2**20
+
+# FP64 operations of one face (add/sub/mul/div/sqrt/min/max each 1), counted
+# from the face formulas with nq = ndim + 4 characteristic variables:
+#   setup (averages, non-zero L/R entries) 12, projection of 6 cells 48,
+#   WENO-IS 100 per variable and side (2 nq x 100), back-projection 16,
+#   MOOD admissibility 6, HLLC 114 + 8 (nq - 5) + 11 nq.
+def face_flops(ndim: int) -> int:
+    nq = ndim + 4
+    return 12 + 48 + 200 * nq + 16 + 6 + (114 + 8 * (nq - 5) + 11 * nq)
+
+
+# algorithmic HBM bytes of one fully fused RK3 cell-update with an FP64 state:
+# 3 stages read U^n and U^(s) and write U^(s+1) -> (2 + 3 + 3) nv 8 B
+def cell_update_bytes(ndim: int) -> int:
+    return 8 * (ndim + 4) * 8
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or not self.path or not os.path.exists(self.path):
+            return None
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx = max(mx, float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    ws_size = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws_size, rank, local
+
+
+def sample_case(n: int, rows: int):
+    """A bounded sample of the workload for CPU timing: the full-width strip of
+    `rows` rows through the bubble's centre (transmissive at the cut rows)."""
+    case = wl.shock_bubble_2d(n)
+    y0 = n // 2 - rows // 2
+    Q = case.Q[:, :, 3 + y0 - 3:3 + y0 + rows + 3, :].copy()
+    return case, Q, rows
+
+
+def cpu_oracle_rate(n: int, rows: int, steps: int):
+    import oracle
+    case, Q, rows = sample_case(n, rows)
+    g = oracle.Grid(2, (n, rows), (case.dx[0], case.dx[1]), case.bc)
+    U = oracle.prim_to_cons(2, Q)
+    times = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        U, _, _ = oracle.step(g, U)
+        times.append(time.perf_counter() - t0)
+    return n * rows, times, oracle.get_threads()
+
+
+def run_reference(args):
+    ws_size, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    n, rows = args.n, args.ref_rows
+    cells, times, cores = cpu_oracle_rate(n, rows, args.warmup + args.steps)
+    t = sum(times[args.warmup:])
+    value = cells * args.steps / t
+    sample = f"{n}x{rows} strip of the {n}^2 workload through the bubble centre, one oracle RK3 step per step"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"shock_bubble_2d_{n}x{n}", "grid": [n, n], "rk3_steps": "CFL 0.5",
+                       "l2": "inputs larger than L2 are not applicable (CPU)"},
+            "cpu_baseline": {"kind": "oracle", "value": value, "unit": UNIT, "cores": cores, "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    import paper_1707_00592_gb300 as ws
+
+    ws_size, rank, local = dist_setup()
+    if ws_size > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    stream = torch.cuda.Stream()
+    n = args.n
+    case = wl.shock_bubble_2d(n)
+    with torch.cuda.stream(stream):
+        s = ws.Solver(2, case.n, case.dx, case.bc, precision=args.precision, stream=stream)
+        Q = s.tensor(case.Q)
+        U0 = s.prim_to_cons(Q)
+        U = U0.clone()
+        flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+        for _ in range(args.warmup):
+            s.step(U)
+        stream.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        if ws_size > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        ws.ws_profile(s.ctx, True)
+        with ClockSampler(dev) as clk:
+            for k in range(args.steps):
+                flush.zero_()  # evict the state from L2 between timed steps
+                ev[k][0].record(stream)
+                s.step(U)
+                ev[k][1].record(stream)
+            stream.synchronize()
+        torch.cuda.synchronize()
+        prof = ws.ws_profile_read(s.ctx)
+        ws.ws_profile(s.ctx, False)
+        ms = sum(a.elapsed_time(b) for a, b in ev)
+        if ws_size > 1:
+            t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms = float(t.item())
+        cells = case.cells
+        value = ws_size * cells * args.steps / (ms * 1e-3)
+        launches = int(sum(v[1] for v in prof.values()))
+
+        # end to end through the public C ABI with host buffers: H2D of the
+        # state, one RK3 step, D2H of the state, per step
+        Uh = U0.cpu().pin_memory()
+        ws.ws_run_host(s.ctx, Uh, 1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            ws.ws_run_host(s.ctx, Uh, 1)
+        e2e_t = (time.perf_counter() - t0) / args.steps
+        state_bytes = s.size * 8
+
+    clocks = clk.summary()
+    if rank != 0:
+        if ws_size > 1:
+            torch.distributed.destroy_process_group()
+        return
+    peaks, which = load_peaks()
+    face_ms, face_n = prof["face"]
+    per_launch_s = face_ms * 1e-3 / max(face_n, 1)
+    faces_per_launch = (n + 1) * n  # one direction of the 2D grid
+    flops = face_flops(2) * faces_per_launch
+    achieved = flops / per_launch_s / 1e12
+    fp64_peak = args.fp64_peak
+    if fp64_peak is None:
+        fp64_peak = ws.ws_peak_probe("fp64")
+    roofline = {"bound": "alu", "kernel": "face sweep (FP64)", "achieved": achieved, "peak": fp64_peak,
+                "unit": "TFLOP/s", "frac": achieved / fp64_peak, "traffic": None,
+                "peak_source": "FP64 FMA chain probe on this GPU (2 flops per DFMA)",
+                "flops_per_face": face_flops(2), "faces_per_launch": faces_per_launch,
+                "face_ms_per_launch": per_launch_s * 1e3,
+                "share_of_step": face_ms / ms,
+                "hbm_bytes_per_cell_update": cell_update_bytes(2),
+                "hbm_peak_gbs": peaks.get("hbm_gbs"), "hbm_peak_source": which}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws_size, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+            "data": "synthetic",
+            "config": {"workload": f"shock_bubble_2d_{n}x{n}", "grid": [n, n], "precision": args.precision,
+                       "cfl": 0.5, "mood": True, "weights": "modified",
+                       "l2": "L2 flushed (258 MB write) between timed steps",
+                       "parallelism": f"replicas x{ws_size}"},
+            "gpu_launches": launches,
+            "kernel_ms": {k: v[0] for k, v in prof.items() if v[1]},
+            "roofline": roofline,
+            "e2e": {"value": cells / e2e_t, "unit": UNIT, "h2d_bytes_per_step": state_bytes,
+                    "d2h_bytes_per_step": state_bytes}}
+    if clocks:
+        line["clocks"] = clocks
+    if ws_size == 1 and not args.no_cpu_baseline:
+        cells_c, times, cores = cpu_oracle_rate(n, args.cpu_rows, args.cpu_steps)
+        line["cpu_baseline"] = {"kind": "oracle", "value": cells_c * len(times) / sum(times), "unit": UNIT,
+                                "cores": cores,
+                                "sample": f"{args.cpu_steps} oracle RK3 steps on the {n}x{args.cpu_rows} strip "
+                                          f"of the {n}^2 workload through the bubble centre"}
+    print(json.dumps(line), flush=True)
+    if ws_size > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--n", type=int, default=1024)
+    ap.add_argument("--cpu-rows", type=int, default=128)
+    ap.add_argument("--cpu-steps", type=int, default=3)
+    ap.add_argument("--ref-rows", type=int, default=128)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fp64-peak", type=float, default=None)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,198 @@
+/*
+ * ws.h -- C ABI of the GB300 WENO-IS two-phase solver library (libws_gb300.so).
+ *
+ * The library advances the quasi-conservative two-phase model of Wang, Xiang,
+ * Zhang & Hu (arXiv 1707.00592): the Euler equations with the stiffened-gas
+ * EOS rho e = Gamma p + Pi (Sec. 2, Eqs. governing-equation and eos) and the
+ * non-conservative advection of phi = (Gamma, Pi) = (1/(gamma-1),
+ * gamma P_inf/(gamma-1)) (Eqs. material-equation, material-properties).
+ * Space: cell-averaged finite volumes (Sec. 3.1), characteristic
+ * primitive-variable WENO-IS reconstruction (Secs. 3.2, 3.3), MOOD positivity
+ * cascade (Sec. 3.4) and HLLC fluxes (Sec. 3.2.1); time: SSP-RK3 (Sec. 3.1).
+ *
+ * Conventions for every entry point
+ *  - All state pointers are DEVICE pointers (cudaMalloc'd or torch tensors on
+ *    the context's device) unless the name ends in _host.  The caller owns
+ *    them; the library never frees them and never keeps them past the call.
+ *  - A state buffer holds nv = ndim + 4 fields of FP64 in structure-of-arrays
+ *    order (rho, rho u_1 .. rho u_ndim, E, Gamma, Pi), each field a padded
+ *    [z][y][x] block (x fastest) with 3 ghost cells on both sides of every
+ *    active direction: padded extent n[d] + 6 for d < ndim, 1 otherwise.
+ *    ws_state_size() returns the number of doubles.  In batched-tube mode
+ *    (ws_grid.ntubes > 0) each field is the concatenation of the tubes' padded
+ *    segments, tube t on [tube_offsets[t], tube_offsets[t+1]).
+ *  - Ghost cells of a state passed to ws_step / ws_flux_divergence /
+ *    ws_cfl_dt are overwritten from the boundary conditions; interior cells
+ *    are only written by ws_step.
+ *  - Work is enqueued on the CUDA stream given to ws_init, in order.  Calls
+ *    return once the work is enqueued, except where a host-side result is
+ *    requested (noted per call), which synchronises that stream.
+ *  - Every call returns a WS_* status; ws_last_error() gives a message.  No
+ *    call aborts the process or lets a C++ exception cross the ABI.  A context
+ *    is not thread-safe: one host thread at a time.
+ */
+#ifndef WS_GB300_H
+#define WS_GB300_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define WS_API __attribute__((visibility("default")))
+#else
+#define WS_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define WS_OK 0
+#define WS_EINVAL 1    /* bad argument: grid, options, size or pointer */
+#define WS_ECUDA 2     /* a CUDA runtime call failed */
+#define WS_ENONPHYS 3  /* a cell ended the step with rho <= 0, Gamma <= 0 or (Gamma+1)p + Pi <= 0 */
+#define WS_ETIMEOUT 4  /* a bounded device-side wait gave up */
+#define WS_ENOTSUP 5   /* combination of options not built */
+
+/* boundary kinds (per direction and side) */
+#define WS_BC_TRANSMISSIVE 0 /* zero-gradient ("constant extrapolation", non-reflecting), Sec. 6 */
+#define WS_BC_PERIODIC 1     /* Sec. 4 */
+#define WS_BC_REFLECTIVE 2   /* slip wall: mirror, normal momentum negated */
+
+/* arithmetic of the sweep */
+#define WS_PREC_FP64 0  /* everything in FP64; same operation order as the FP64 oracle */
+#define WS_PREC_MIXED 1 /* FP32 projection, WENO-IS and HLLC; FP64 pressure recovery,
+                           MOOD test, flux divergence and RK accumulation */
+
+/* nonlinear weights */
+#define WS_W_MODIFIED 0 /* Sec. 3.3.2, Eq. (weighting-modification): the scheme */
+#define WS_W_BASIC 1    /* Sec. 3.3.1, Eq. (weight-new) with q = 1 */
+
+typedef struct ws_grid {
+  int ndim;                    /* 1, 2 or 3 */
+  int n[3];                    /* interior cells per direction (n[d] >= 1; unused dims ignored) */
+  double dx[3];                /* uniform cell size per direction (> 0) */
+  int bc[3][2];                /* WS_BC_* per direction, [d][0] low side, [d][1] high side */
+  int64_t ntubes;              /* > 0: batched independent 1D tubes (ndim must be 1) */
+  const int64_t *tube_offsets; /* HOST array of ntubes+1 padded offsets; each tube has
+                                  len = off[t+1]-off[t]-6 >= 6 interior cells, dx = 1/len,
+                                  transmissive ends; copied at ws_init */
+} ws_grid;
+
+typedef struct ws_opts {
+  int precision; /* WS_PREC_* */
+  int weights;   /* WS_W_* */
+  int mood;      /* 1: MOOD positivity cascade 5th -> 3rd -> 1st (Sec. 3.4); 0: off */
+  int learned;   /* 1: smooth-face gate by the face-classifier MLP (mixed precision only) */
+  double eps;    /* WENO epsilon (the paper leaves it open); <= 0 selects 1e-40 (FP64) / 1e-30 (mixed) */
+  double cfl;    /* CFL number; <= 0 selects 0.5 (Secs. 5, 6) */
+  int check;     /* 1: ws_step synchronises and returns WS_ENONPHYS when a cell is inadmissible */
+} ws_opts;
+
+typedef struct ws_ctx ws_ctx;
+
+/* Create a context on the current CUDA device.  Validates the grid (ndim,
+ * n, dx, bc, tube offsets) and options, allocates the context's scratch
+ * (primitive cache, face fluxes, RK stage state, MOOD masks) and returns it in
+ * *out.  stream: a cudaStream_t (NULL = legacy default stream).
+ * Errors: WS_EINVAL (bad grid/options; *out untouched), WS_ECUDA. */
+WS_API int ws_init(const ws_grid *grid, const ws_opts *opts, void *stream, ws_ctx **out);
+
+/* Number of doubles in one state buffer (nv fields x padded cells). */
+WS_API int64_t ws_state_size(const ws_ctx *ctx);
+
+/* Number of MOOD mask bytes written per RHS evaluation (all directions).  The
+ * mask of direction d covers faces i+1/2, i = -1..n_d-1, at every interior
+ * transverse position, laid out [z][y][x] with extent n_d+1 along d;
+ * directions follow one another.  Byte = code(left) | code(right) << 2 with
+ * code 0/1/2 for 5th/3rd/1st order. */
+WS_API int64_t ws_mask_size(const ws_ctx *ctx);
+
+/* Primitive (rho, u_1..u_ndim, p, Gamma, Pi) -> conservative state, every
+ * padded cell (Eq. eos: E = Gamma p + Pi + rho |u|^2 / 2).  Q, U: device
+ * buffers of ws_state_size() doubles; Q may not alias U. */
+WS_API int ws_prim_to_cons(ws_ctx *ctx, const double *Q, double *U);
+
+/* Conservative -> primitive, every padded cell; p = (E - rho|u|^2/2 - Pi)/Gamma in FP64. */
+WS_API int ws_cons_to_prim(ws_ctx *ctx, const double *U, double *Q);
+
+/* The semi-discrete operator of Sec. 3.1, Eqs. (semi-discrezization-euler)
+ * and (semi-discrezization-material): L(U) = -sum_d (F_{i+1/2} - F_{i-1/2})/dx_d,
+ * plus phi_i sum_d (u_{i+1/2} - u_{i-1/2})/dx_d for Gamma and Pi, on interior
+ * cells (ghost entries of L are not written).  U's ghosts are filled first.
+ * The MOOD mask of this evaluation is kept (see ws_get_mood, stage 0).
+ * Not available in batched-tube mode (WS_ENOTSUP). */
+WS_API int ws_flux_divergence(ws_ctx *ctx, double *U, double *L);
+
+/* CFL step of U: dt = cfl / max_cells sum_d (|u_d| + c)/dx_d.  Synchronises;
+ * *dt is a host double (batched-tube mode: the minimum over tubes). */
+WS_API int ws_cfl_dt(ws_ctx *ctx, double *U, double *dt);
+
+/* One SSP-RK3 step (Shu & Osher; Sec. 3.1) of U in place:
+ *   U1 = U + dt L(U);  U2 = 3/4 U + 1/4 (U1 + dt L(U1));  U <- 1/3 U + 2/3 (U2 + dt L(U2)).
+ * dt <= 0 takes the CFL step computed on the device from U (per tube in
+ * batched-tube mode); dt > 0 is used as given (every tube).  dt_used
+ * (nullable, HOST) receives the step (ntubes values in batched-tube mode) and
+ * then the call synchronises.  With opts.check = 1 the call synchronises and
+ * returns WS_ENONPHYS if any interior cell ends inadmissible (U is left as
+ * computed).  The MOOD masks of the three stages are kept for ws_get_mood. */
+WS_API int ws_step(ws_ctx *ctx, double *U, double dt, double *dt_used);
+
+/* End-to-end form for host-resident data: copies the state from HOST memory
+ * U_host (ws_state_size() doubles; pinned memory gives full copy speed) to
+ * the context's device buffer, runs nsteps ws_step's (dt as in ws_step), and
+ * copies the state back to U_host.  Synchronises.  dt_used (nullable, HOST)
+ * receives the last step's dt (ntubes values in batched-tube mode). */
+WS_API int ws_run_host(ws_ctx *ctx, double *U_host, int nsteps, double dt, double *dt_used);
+
+/* MOOD record of the last ws_step (3 stages) or ws_flux_divergence (stage 0
+ * only).  mask (nullable, DEVICE): receives 3 x ws_mask_size() bytes, stage
+ * major.  counts (nullable, HOST int64[9]): faces-sides per direction d and
+ * level k (5th, 3rd, 1st) at counts[3*d + k], summed over the stages of that
+ * call and both sides.  Synchronises when counts is given. */
+WS_API int ws_get_mood(ws_ctx *ctx, uint8_t *mask, int64_t counts[9]);
+
+/* Number of inadmissible interior cells found at the end of the last
+ * ws_step (HOST out).  Synchronises. */
+WS_API int ws_nonphysical(ws_ctx *ctx, int64_t *count);
+
+/* ---- measurement helpers (not part of the method) ---- */
+
+/* kernel classes for ws_profile_read */
+#define WS_K_GHOST 0   /* ghost layers */
+#define WS_K_PRIM 1    /* conservative -> primitive cache */
+#define WS_K_CFL 2     /* CFL max-reduction and dt */
+#define WS_K_FACE 3    /* face sweep: projection, WENO-IS, MOOD, HLLC */
+#define WS_K_UPDATE 4  /* flux divergence + RK stage */
+#define WS_K_OTHER 5
+#define WS_NKERNEL 8
+
+/* enable != 0: from now on record a CUDA event pair around every kernel the
+ * context launches (on its stream) and reset the totals; 0: stop recording. */
+WS_API int ws_profile(ws_ctx *ctx, int enable);
+
+/* Device time (ms, summed over launches, from the recorded events) and launch
+ * count per kernel class since the last ws_profile(ctx, 1).  ms and launches
+ * are HOST arrays of WS_NKERNEL entries (either may be NULL).  Launch counts
+ * are kept even when recording is off.  Synchronises. */
+WS_API int ws_profile_read(ws_ctx *ctx, double ms[WS_NKERNEL], int64_t launches[WS_NKERNEL]);
+
+/* Throughput of dependent fused multiply-add chains on the current device:
+ * kind 0 = FP64 (DFMA), 1 = FP32 (FFMA); *tflops receives 2 x FMAs / s / 1e12
+ * over a launch of blocks x 256 threads (blocks <= 0: 8 per SM).  Synchronises. */
+WS_API int ws_peak_probe(int kind, int blocks, double *tflops);
+
+/* Message of the last failing call on ctx (never NULL; "" when none). */
+WS_API const char *ws_last_error(const ws_ctx *ctx);
+
+/* Message of the last ws_init failure (for calls that got no context). */
+WS_API const char *ws_init_error(void);
+
+/* Free the context and its scratch.  NULL is a no-op. */
+WS_API void ws_destroy(ws_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WS_GB300_H */

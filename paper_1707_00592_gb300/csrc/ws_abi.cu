@@ -1,0 +1,496 @@
+// Host side of the C ABI declared in include/ws.h: validation, scratch
+// ownership and the stream-ordered launch sequence of an SSP-RK3 step.
+#include <cuda_runtime.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "ws_internal.h"
+
+using namespace ws;
+
+namespace {
+
+char g_init_err[512] = "";
+
+int fail(ws_ctx* c, int code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(c ? c->err : g_init_err, 512, fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+#define CK(ctx, call)                                                                              \
+  do {                                                                                             \
+    cudaError_t e_ = (call);                                                                       \
+    if (e_ != cudaSuccess) return fail(ctx, WS_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+int check_launch(ws_ctx* c, const char* what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(c, WS_ECUDA, "%s launch failed: %s", what, cudaGetErrorString(e));
+  return WS_OK;
+}
+
+template <typename T>
+int dalloc(ws_ctx* c, T** p, int64_t count) {
+  *p = nullptr;
+  if (count <= 0) return WS_OK;
+  cudaError_t e = cudaMalloc((void**)p, sizeof(T) * (size_t)count);
+  if (e != cudaSuccess) return fail(c, WS_ECUDA, "cudaMalloc(%lld bytes): %s", (long long)(sizeof(T) * count),
+                                    cudaGetErrorString(e));
+  return WS_OK;
+}
+
+// Records an event pair around the launches of its scope when profiling is on,
+// and counts the kernel launches of its class.
+struct KScope {
+  ws_ctx* c;
+  int cls;
+  int n;
+  size_t slot = (size_t)-1;
+  KScope(ws_ctx* c_, int cls_, int nkernels = 1) : c(c_), cls(cls_), n(nkernels) {
+    if (!c->prof_on) return;
+    if (c->ev_used + 2 > c->ev.size()) {
+      for (int k = 0; k < 64; ++k) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return;
+        c->ev.push_back(e);
+      }
+      c->ev_cls.resize(c->ev.size() / 2);
+    }
+    slot = c->ev_used;
+    c->ev_used += 2;
+    c->ev_cls[slot / 2] = cls;
+    cudaEventRecord(c->ev[slot], c->stream);
+  }
+  ~KScope() {
+    c->nlaunch[cls] += n;
+    if (slot != (size_t)-1) cudaEventRecord(c->ev[slot + 1], c->stream);
+  }
+};
+
+void free_all(ws_ctx* c) {
+  cudaFree(c->S1);
+  cudaFree(c->Q);
+  for (int d = 0; d < 3; ++d) {
+    cudaFree(c->Fh[d]);
+    cudaFree(c->us[d]);
+    cudaFree(c->Fh32[d]);
+    cudaFree(c->us32[d]);
+  }
+  cudaFree(c->mask);
+  cudaFree(c->dt_dev);
+  cudaFree(c->lmax);
+  cudaFree(c->nbad);
+  cudaFree(c->Uhost_dev);
+  cudaFree(c->off_dev);
+  cudaFree(c->cell_tube);
+  cudaFree(c->mood_counts);
+  cudaFree(c->mask_off_dev);
+  for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+  c->ev.clear();
+}
+
+bool tubes(const ws_ctx* c) { return c->grid.ntubes > 0; }
+
+// one RHS evaluation of the stage state Us into the face arrays
+int rhs_faces(ws_ctx* c, double* Us) {
+  const GridDev& g = c->gd;
+  {
+    KScope k(c, WS_K_GHOST, g.ndim);
+    for (int d = 0; d < g.ndim; ++d) launch_ghost(g, Us, d, c->stream);
+  }
+  {
+    KScope k(c, WS_K_PRIM);
+    launch_prim(g, Us, c->Q, c->stream);
+  }
+  return check_launch(c, "ghost/prim");
+}
+
+int faces(ws_ctx* c, int stage_slot) {
+  const GridDev& g = c->gd;
+  uint8_t* mbase = c->mask + (int64_t)stage_slot * c->nmask;
+  for (int d = 0; d < g.ndim; ++d) {
+    KScope k(c, WS_K_FACE);
+    if (c->opts.precision == WS_PREC_FP64)
+      launch_face_fp64(g, d, c->Q, c->Fh[d], c->us[d], mbase + c->mask_off[d], c->opts.eps, c->opts.mood,
+                       c->opts.weights, c->stream);
+    else
+      return fail(c, WS_ENOTSUP, "mixed precision sweep not built");
+  }
+  return check_launch(c, "face sweep");
+}
+
+int update(ws_ctx* c, int stage, const double* Un, const double* Us, double* Uout) {
+  KScope k(c, WS_K_UPDATE);
+  launch_update(c->gd, stage, Un, Us, Uout, c->Fh, c->us, c->dt_dev, c->nbad, c->stream);
+  return check_launch(c, "update");
+}
+
+// ---- batched tubes ----
+int tube_rhs(ws_ctx* c, double* Us, int stage_slot, bool cfl) {
+  {
+    KScope k(c, WS_K_GHOST);
+    launch_tubes_ghost(c->td, Us, c->stream);
+  }
+  {
+    KScope k(c, WS_K_PRIM);
+    launch_tubes_prim(c->td, Us, c->Q, c->stream);
+  }
+  if (cfl) {
+    CK(c, cudaMemsetAsync(c->lmax, 0, sizeof(unsigned long long) * c->td.ntubes, c->stream));
+    KScope k(c, WS_K_CFL);
+    launch_tubes_cfl(c->td, c->Q, c->lmax, c->stream);
+  }
+  uint8_t* mbase = c->mask + (int64_t)stage_slot * c->nmask;
+  KScope k(c, WS_K_FACE);
+  launch_tubes_face_fp64(c->td, c->Q, c->Fh[0], c->us[0], mbase, c->opts.eps, c->opts.mood, c->opts.weights,
+                         c->stream);
+  return check_launch(c, "tube sweep");
+}
+
+int step_device(ws_ctx* c, double* U, double dt) {
+  const GridDev& g = c->gd;
+  int rc;
+  CK(c, cudaMemsetAsync(c->nbad, 0, sizeof(unsigned long long), c->stream));
+  if (tubes(c)) {
+    const int64_t nt = c->td.ntubes;
+    for (int s = 0; s < 3; ++s) {
+      double* Us = s == 0 ? U : c->S1;
+      if ((rc = tube_rhs(c, Us, s, s == 0 && dt <= 0.0))) return rc;
+      if (s == 0) {
+        KScope k(c, WS_K_CFL);
+        launch_set_dt(nullptr, dt, c->opts.cfl, c->lmax, c->dt_dev, nt, c->stream);
+      }
+      double* Uout = s == 2 ? U : c->S1;
+      KScope k(c, WS_K_UPDATE);
+      launch_tubes_update(c->td, s, U, Us, Uout, c->Fh[0], c->us[0], c->dt_dev, c->nbad, c->stream);
+      if ((rc = check_launch(c, "tube update"))) return rc;
+    }
+    c->last_stages = 3;
+    return WS_OK;
+  }
+  for (int s = 0; s < 3; ++s) {
+    double* Us = s == 0 ? U : c->S1;
+    if ((rc = rhs_faces(c, Us))) return rc;
+    if (s == 0) {
+      if (dt <= 0.0) {
+        CK(c, cudaMemsetAsync(c->lmax, 0, sizeof(unsigned long long), c->stream));
+        KScope k(c, WS_K_CFL);
+        launch_cfl(g, c->Q, c->lmax, c->stream);
+      }
+      KScope k(c, WS_K_CFL);
+      launch_set_dt(nullptr, dt, c->opts.cfl, c->lmax, c->dt_dev, 1, c->stream);
+    }
+    if ((rc = faces(c, s))) return rc;
+    double* Uout = s == 2 ? U : c->S1;
+    if ((rc = update(c, s, U, Us, Uout))) return rc;
+  }
+  c->last_stages = 3;
+  return WS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* ws_init_error(void) { return g_init_err; }
+
+const char* ws_last_error(const ws_ctx* ctx) { return ctx ? ctx->err : g_init_err; }
+
+int ws_init(const ws_grid* grid, const ws_opts* opts, void* stream, ws_ctx** out) {
+  g_init_err[0] = 0;
+  if (!grid || !opts || !out) return fail(nullptr, WS_EINVAL, "null argument");
+  ws_grid gr = *grid;
+  ws_opts op = *opts;
+  bool tb = gr.ntubes > 0;
+  if (gr.ndim < 1 || gr.ndim > 3) return fail(nullptr, WS_EINVAL, "ndim must be 1, 2 or 3 (got %d)", gr.ndim);
+  if (tb && gr.ndim != 1) return fail(nullptr, WS_EINVAL, "batched tubes need ndim = 1");
+  if (tb && !gr.tube_offsets) return fail(nullptr, WS_EINVAL, "tube_offsets is NULL");
+  if (!tb) {
+    for (int d = 0; d < gr.ndim; ++d) {
+      if (gr.n[d] < 1) return fail(nullptr, WS_EINVAL, "n[%d] = %d < 1", d, gr.n[d]);
+      if (!(gr.dx[d] > 0.0)) return fail(nullptr, WS_EINVAL, "dx[%d] must be > 0", d);
+      for (int s = 0; s < 2; ++s)
+        if (gr.bc[d][s] < 0 || gr.bc[d][s] > 2) return fail(nullptr, WS_EINVAL, "bad bc[%d][%d]", d, s);
+      if ((gr.bc[d][0] == WS_BC_PERIODIC) != (gr.bc[d][1] == WS_BC_PERIODIC))
+        return fail(nullptr, WS_EINVAL, "periodic bc must be set on both sides of direction %d", d);
+      if (gr.n[d] < NG && (gr.bc[d][0] != WS_BC_TRANSMISSIVE || gr.bc[d][1] != WS_BC_TRANSMISSIVE))
+        return fail(nullptr, WS_EINVAL, "n[%d] = %d < 3 needs transmissive ends", d, gr.n[d]);
+    }
+  }
+  if (op.precision != WS_PREC_FP64 && op.precision != WS_PREC_MIXED)
+    return fail(nullptr, WS_EINVAL, "bad precision %d", op.precision);
+  if (op.weights != WS_W_MODIFIED && op.weights != WS_W_BASIC) return fail(nullptr, WS_EINVAL, "bad weights");
+  if (op.mood != 0 && op.mood != 1) return fail(nullptr, WS_EINVAL, "mood must be 0 or 1");
+  if (op.learned && op.precision != WS_PREC_MIXED)
+    return fail(nullptr, WS_EINVAL, "the learned gate runs in mixed precision only");
+  if (op.eps <= 0.0) op.eps = op.precision == WS_PREC_FP64 ? 1e-40 : 1e-30;
+  if (op.cfl <= 0.0) op.cfl = 0.5;
+  if (op.precision == WS_PREC_MIXED || op.learned)
+    return fail(nullptr, WS_ENOTSUP, "mixed precision path not built in this library");
+
+  ws_ctx* c = new (std::nothrow) ws_ctx();
+  if (!c) return fail(nullptr, WS_ECUDA, "out of host memory");
+  c->grid = gr;
+  c->opts = op;
+  c->stream = (cudaStream_t)stream;
+  c->grid.tube_offsets = nullptr;
+  cudaGetDevice(&c->dev);
+  GridDev& g = c->gd;
+  g.ndim = gr.ndim;
+  g.nv = gr.ndim + 4;
+  int rc = WS_OK;
+  if (!tb) {
+    for (int d = 0; d < 3; ++d) {
+      bool act = d < gr.ndim;
+      g.n[d] = act ? gr.n[d] : 1;
+      g.G[d] = act ? NG : 0;
+      g.P[d] = act ? (int64_t)gr.n[d] + 2 * NG : 1;
+      g.dx[d] = act ? gr.dx[d] : 1.0;
+      g.bc[d][0] = act ? gr.bc[d][0] : 0;
+      g.bc[d][1] = act ? gr.bc[d][1] : 0;
+    }
+    g.st[0] = 1;
+    g.st[1] = g.P[0];
+    g.st[2] = g.P[0] * g.P[1];
+    g.N = g.P[0] * g.P[1] * g.P[2];
+    g.ncell = (int64_t)g.n[0] * g.n[1] * g.n[2];
+    int64_t off = 0;
+    for (int d = 0; d < 3; ++d) {
+      for (int e = 0; e < 3; ++e) g.fe[d][e] = g.n[e] + (e == d ? 1 : 0);
+      g.nfaces[d] = d < gr.ndim ? g.fe[d][0] * g.fe[d][1] * g.fe[d][2] : 0;
+      c->mask_off[d] = off;
+      off += g.nfaces[d];
+    }
+    c->nmask = off;
+    c->nstate = (int64_t)g.nv * g.N;
+    if ((rc = dalloc(c, &c->S1, c->nstate)) || (rc = dalloc(c, &c->Q, (int64_t)(g.nv + 1) * g.N)) ||
+        (rc = dalloc(c, &c->mask, 3 * c->nmask)) || (rc = dalloc(c, &c->dt_dev, 1)) ||
+        (rc = dalloc(c, &c->lmax, 1)) || (rc = dalloc(c, &c->nbad, 1)))
+      goto bad;
+    for (int d = 0; d < gr.ndim; ++d)
+      if ((rc = dalloc(c, &c->Fh[d], (int64_t)g.nv * g.nfaces[d])) || (rc = dalloc(c, &c->us[d], g.nfaces[d])))
+        goto bad;
+  } else {
+    int64_t nt = gr.ntubes;
+    std::vector<int64_t> off(grid->tube_offsets, grid->tube_offsets + nt + 1);
+    if (off[0] != 0) {
+      rc = fail(c, WS_EINVAL, "tube_offsets[0] must be 0");
+      goto bad;
+    }
+    int64_t nface = 0;
+    for (int64_t t = 0; t < nt; ++t) {
+      int64_t len = off[t + 1] - off[t] - 2 * NG;
+      if (len < 2 * NG) {
+        rc = fail(c, WS_EINVAL, "tube %lld has %lld interior cells (< 6)", (long long)t, (long long)len);
+        goto bad;
+      }
+      nface += len + 1;
+    }
+    int64_t total = off[nt];
+    std::vector<int> ct(total);
+    for (int64_t t = 0; t < nt; ++t)
+      for (int64_t i = off[t]; i < off[t + 1]; ++i) ct[i] = (int)t;
+    g.n[0] = 1;  // unused in tube mode
+    g.n[1] = g.n[2] = 1;
+    g.N = total;
+    g.nv = 5;
+    c->nstate = 5 * total;
+    c->nmask = total;  // one byte per padded cell: face i+1/2 stored at cell i (faces -1/2 .. len-1/2)
+    c->mask_off[0] = 0;
+    c->td.ntubes = nt;
+    c->td.total = total;
+    (void)nface;
+    if ((rc = dalloc(c, &c->S1, c->nstate)) || (rc = dalloc(c, &c->Q, 6 * total)) ||
+        (rc = dalloc(c, &c->mask, 3 * c->nmask)) || (rc = dalloc(c, &c->dt_dev, nt)) ||
+        (rc = dalloc(c, &c->lmax, nt)) || (rc = dalloc(c, &c->nbad, 1)) || (rc = dalloc(c, &c->Fh[0], 5 * total)) ||
+        (rc = dalloc(c, &c->us[0], total)) || (rc = dalloc(c, &c->off_dev, nt + 1)) ||
+        (rc = dalloc(c, &c->cell_tube, total)))
+      goto bad;
+    if (cudaMemcpy(c->off_dev, off.data(), sizeof(int64_t) * (nt + 1), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(c->cell_tube, ct.data(), sizeof(int) * total, cudaMemcpyHostToDevice) != cudaSuccess) {
+      rc = fail(c, WS_ECUDA, "copying tube offsets failed");
+      goto bad;
+    }
+    c->td.off = c->off_dev;
+    c->td.cell_tube = c->cell_tube;
+  }
+  if ((rc = dalloc(c, &c->mood_counts, 9)) || (rc = dalloc(c, &c->mask_off_dev, 3))) goto bad;
+  if (cudaMemcpy(c->mask_off_dev, c->mask_off, 3 * sizeof(int64_t), cudaMemcpyHostToDevice) != cudaSuccess) {
+    rc = fail(c, WS_ECUDA, "copying mask offsets failed");
+    goto bad;
+  }
+  if (cudaMemset(c->mask, 0, 3 * c->nmask) != cudaSuccess) {
+    rc = fail(c, WS_ECUDA, "cudaMemset failed");
+    goto bad;
+  }
+  *out = c;
+  return WS_OK;
+bad:
+  snprintf(g_init_err, sizeof g_init_err, "%s", c->err);
+  free_all(c);
+  delete c;
+  return rc;
+}
+
+int64_t ws_state_size(const ws_ctx* ctx) { return ctx ? ctx->nstate : -1; }
+
+int64_t ws_mask_size(const ws_ctx* ctx) { return ctx ? ctx->nmask : -1; }
+
+int ws_prim_to_cons(ws_ctx* c, const double* Q, double* U) {
+  if (!c || !Q || !U || Q == U) return fail(c, WS_EINVAL, "bad pointers");
+  GridDev g = c->gd;
+  if (tubes(c)) {
+    g.ndim = 1;
+    g.n[0] = (int)1;
+  }
+  launch_prim_to_cons(g, Q, U, c->stream);
+  return check_launch(c, "prim_to_cons");
+}
+
+int ws_cons_to_prim(ws_ctx* c, const double* U, double* Q) {
+  if (!c || !Q || !U || Q == U) return fail(c, WS_EINVAL, "bad pointers");
+  launch_cons_to_prim_all(c->gd, U, Q, c->stream);
+  return check_launch(c, "cons_to_prim");
+}
+
+int ws_flux_divergence(ws_ctx* c, double* U, double* L) {
+  if (!c || !U || !L || U == L) return fail(c, WS_EINVAL, "bad pointers");
+  if (tubes(c)) return fail(c, WS_ENOTSUP, "ws_flux_divergence is not available for batched tubes");
+  int rc;
+  if ((rc = rhs_faces(c, U)) || (rc = faces(c, 0)) || (rc = update(c, -1, U, U, L))) return rc;
+  c->last_stages = 1;
+  return WS_OK;
+}
+
+int ws_cfl_dt(ws_ctx* c, double* U, double* dt) {
+  if (!c || !U || !dt) return fail(c, WS_EINVAL, "bad pointers");
+  int64_t n = tubes(c) ? c->td.ntubes : 1;
+  if (tubes(c)) {
+    launch_tubes_ghost(c->td, U, c->stream);
+    launch_tubes_prim(c->td, U, c->Q, c->stream);
+    CK(c, cudaMemsetAsync(c->lmax, 0, sizeof(unsigned long long) * n, c->stream));
+    launch_tubes_cfl(c->td, c->Q, c->lmax, c->stream);
+  } else {
+    int rc = rhs_faces(c, U);
+    if (rc) return rc;
+    CK(c, cudaMemsetAsync(c->lmax, 0, sizeof(unsigned long long), c->stream));
+    launch_cfl(c->gd, c->Q, c->lmax, c->stream);
+  }
+  launch_set_dt(nullptr, 0.0, c->opts.cfl, c->lmax, c->dt_dev, n, c->stream);
+  int rc = check_launch(c, "cfl");
+  if (rc) return rc;
+  std::vector<double> h(n);
+  CK(c, cudaMemcpyAsync(h.data(), c->dt_dev, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  double m = h[0];
+  for (int64_t i = 1; i < n; ++i) m = h[i] < m ? h[i] : m;
+  *dt = m;
+  return WS_OK;
+}
+
+int ws_step(ws_ctx* c, double* U, double dt, double* dt_used) {
+  if (!c || !U) return fail(c, WS_EINVAL, "bad pointers");
+  int rc = step_device(c, U, dt);
+  if (rc) return rc;
+  if (dt_used) {
+    int64_t n = tubes(c) ? c->td.ntubes : 1;
+    CK(c, cudaMemcpyAsync(dt_used, c->dt_dev, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+  }
+  if (c->opts.check) {
+    unsigned long long nb = 0;
+    CK(c, cudaMemcpyAsync(&nb, c->nbad, sizeof nb, cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    if (nb) return fail(c, WS_ENONPHYS, "%llu inadmissible cells after the step", nb);
+  }
+  return WS_OK;
+}
+
+int ws_run_host(ws_ctx* c, double* U_host, int nsteps, double dt, double* dt_used) {
+  if (!c || !U_host || nsteps < 0) return fail(c, WS_EINVAL, "bad arguments");
+  if (!c->Uhost_dev) {
+    int rc = dalloc(c, &c->Uhost_dev, c->nstate);
+    if (rc) return rc;
+  }
+  size_t bytes = sizeof(double) * (size_t)c->nstate;
+  CK(c, cudaMemcpyAsync(c->Uhost_dev, U_host, bytes, cudaMemcpyHostToDevice, c->stream));
+  for (int k = 0; k < nsteps; ++k) {
+    int rc = step_device(c, c->Uhost_dev, dt);
+    if (rc) return rc;
+  }
+  CK(c, cudaMemcpyAsync(U_host, c->Uhost_dev, bytes, cudaMemcpyDeviceToHost, c->stream));
+  if (dt_used) {
+    int64_t n = tubes(c) ? c->td.ntubes : 1;
+    CK(c, cudaMemcpyAsync(dt_used, c->dt_dev, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
+  }
+  CK(c, cudaStreamSynchronize(c->stream));
+  return WS_OK;
+}
+
+int ws_get_mood(ws_ctx* c, uint8_t* mask, int64_t counts[9]) {
+  if (!c) return fail(c, WS_EINVAL, "null context");
+  if (mask) CK(c, cudaMemcpyAsync(mask, c->mask, 3 * c->nmask, cudaMemcpyDeviceToDevice, c->stream));
+  if (counts) {
+    int ndim = tubes(c) ? 1 : c->gd.ndim;
+    CK(c, cudaMemsetAsync(c->mood_counts, 0, 9 * sizeof(unsigned long long), c->stream));
+    if (c->last_stages > 0)
+      launch_mood_count(c->mask, c->nmask, c->last_stages, c->mask_off_dev, ndim, c->mood_counts, c->stream);
+    unsigned long long h[9];
+    CK(c, cudaMemcpyAsync(h, c->mood_counts, sizeof h, cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    for (int i = 0; i < 9; ++i) counts[i] = (int64_t)h[i];
+  }
+  return check_launch(c, "mood count");
+}
+
+int ws_nonphysical(ws_ctx* c, int64_t* count) {
+  if (!c || !count) return fail(c, WS_EINVAL, "bad pointers");
+  unsigned long long nb = 0;
+  CK(c, cudaMemcpyAsync(&nb, c->nbad, sizeof nb, cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  *count = (int64_t)nb;
+  return WS_OK;
+}
+
+int ws_profile(ws_ctx* c, int enable) {
+  if (!c) return fail(c, WS_EINVAL, "null context");
+  if (enable) {
+    CK(c, cudaStreamSynchronize(c->stream));
+    c->ev_used = 0;
+    for (int k = 0; k < WS_NKERNEL; ++k) c->nlaunch[k] = 0;
+  }
+  c->prof_on = enable != 0;
+  return WS_OK;
+}
+
+int ws_profile_read(ws_ctx* c, double ms[WS_NKERNEL], int64_t launches[WS_NKERNEL]) {
+  if (!c) return fail(c, WS_EINVAL, "null context");
+  CK(c, cudaStreamSynchronize(c->stream));
+  double acc[WS_NKERNEL] = {0};
+  for (size_t i = 0; i + 1 < c->ev_used; i += 2) {
+    float t = 0.f;
+    CK(c, cudaEventElapsedTime(&t, c->ev[i], c->ev[i + 1]));
+    acc[c->ev_cls[i / 2]] += t;
+  }
+  for (int k = 0; k < WS_NKERNEL; ++k) {
+    if (ms) ms[k] = acc[k];
+    if (launches) launches[k] = c->nlaunch[k];
+  }
+  return WS_OK;
+}
+
+void ws_destroy(ws_ctx* c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  free_all(c);
+  delete c;
+}
+
+}  // extern "C"

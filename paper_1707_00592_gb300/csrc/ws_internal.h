@@ -1,0 +1,113 @@
+// Internal declarations shared by the library's translation units (never
+// installed; the public surface is include/ws.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/ws.h"
+
+namespace ws {
+
+constexpr int NG = 3;    // ghost layers per side
+constexpr int MAXV = 7;  // rho, 3 momenta, E, Gamma, Pi
+
+// Grid description passed by value to every kernel.
+struct GridDev {
+  int ndim, nv;
+  int n[3];          // interior cells (1 for unused dims)
+  int G[3];          // ghost offset (NG for active dims, 0 otherwise)
+  int64_t P[3];      // padded extents
+  int64_t st[3];     // strides of x, y, z in a field
+  int64_t N;         // padded cells per field
+  double dx[3];
+  int bc[3][2];
+  int64_t fe[3][3];  // face-array extents per direction: n[e], n[d]+1 along d
+  int64_t nfaces[3];
+  int64_t ncell;     // interior cells
+};
+
+// Batched 1D tubes (independent Riemann problems of uneven length).
+struct TubesDev {
+  int64_t ntubes;
+  int64_t total;        // padded cells per field
+  const int64_t* off;   // device, ntubes+1
+  const int* cell_tube; // device, tube index of every padded cell
+};
+
+}  // namespace ws
+
+struct ws_ctx {
+  int dev = 0;
+  cudaStream_t stream = nullptr;
+  ws_grid grid{};
+  ws_opts opts{};
+  ws::GridDev gd{};
+  int64_t nstate = 0;   // doubles per state buffer
+  int64_t nmask = 0;    // mask bytes per RHS evaluation
+  int64_t mask_off[3] = {0, 0, 0};
+  // scratch (device)
+  double* S1 = nullptr;         // RK stage state
+  double* Q = nullptr;          // primitives + sound speed, nv+1 fields
+  double* Fh[3] = {nullptr, nullptr, nullptr};  // face fluxes per direction (nv fields)
+  double* us[3] = {nullptr, nullptr, nullptr};  // face velocities per direction
+  float* Fh32[3] = {nullptr, nullptr, nullptr}; // mixed precision face fluxes
+  float* us32[3] = {nullptr, nullptr, nullptr};
+  uint8_t* mask = nullptr;      // 3 stages x nmask
+  double* dt_dev = nullptr;     // 1 (grid) or ntubes
+  unsigned long long* lmax = nullptr;  // 1 or ntubes, max wave rate as ordered bits
+  unsigned long long* nbad = nullptr;  // inadmissible cells of the last step
+  double* Uhost_dev = nullptr;  // device state for ws_run_host
+  int last_stages = 0;
+  // batched tubes
+  ws::TubesDev td{};
+  int64_t* off_dev = nullptr;
+  int* cell_tube = nullptr;
+  // measurement: event pairs around launches, launch counts per kernel class
+  bool prof_on = false;
+  std::vector<cudaEvent_t> ev;  // 2 per recorded launch
+  std::vector<int> ev_cls;
+  size_t ev_used = 0;
+  int64_t nlaunch[WS_NKERNEL] = {0};
+  // ws_get_mood scratch
+  unsigned long long* mood_counts = nullptr;
+  int64_t* mask_off_dev = nullptr;
+  char err[512] = {0};
+};
+
+namespace ws {
+
+// ---- launchers (ws_common.cu, built with -fmad=false) ----
+void launch_ghost(const GridDev& g, double* U, int d, cudaStream_t s);
+void launch_prim(const GridDev& g, const double* U, double* Q, cudaStream_t s);
+void launch_prim_to_cons(const GridDev& g, const double* Q, double* U, cudaStream_t s);
+void launch_cons_to_prim_all(const GridDev& g, const double* U, double* Q, cudaStream_t s);
+void launch_cfl(const GridDev& g, const double* Q, unsigned long long* lmax, cudaStream_t s);
+void launch_set_dt(const double* dt_fixed_or_null, double dt_fixed, double cfl, const unsigned long long* lmax,
+                   double* dt_dev, int64_t n, cudaStream_t s);
+void launch_update(const GridDev& g, int stage, const double* Un, const double* Us, double* Uout,
+                   double* const Fh[3], double* const us[3], const double* dt_dev, unsigned long long* nbad,
+                   cudaStream_t s);
+void launch_update_mixed(const GridDev& g, int stage, const double* Un, const double* Us, double* Uout,
+                         float* const Fh[3], float* const us[3], const double* dt_dev, unsigned long long* nbad,
+                         cudaStream_t s);
+void launch_mood_count(const uint8_t* mask, int64_t n, int64_t nstage, const int64_t* dir_off, int ndim,
+                       unsigned long long* counts, cudaStream_t s);
+
+// ---- FP64 sweep (ws_fp64.cu, built with -fmad=false) ----
+void launch_face_fp64(const GridDev& g, int d, const double* Q, double* Fh, double* us, uint8_t* mask,
+                      double eps, int mood, int weights, cudaStream_t s);
+
+// ---- batched tubes (ws_tubes.cu) ----
+void launch_tubes_ghost(const TubesDev& t, double* U, cudaStream_t s);
+void launch_tubes_prim(const TubesDev& t, const double* U, double* Q, cudaStream_t s);
+void launch_tubes_cfl(const TubesDev& t, const double* Q, unsigned long long* lmax, cudaStream_t s);
+void launch_tubes_face_fp64(const TubesDev& t, const double* Q, double* Fh, double* us, uint8_t* mask, double eps,
+                            int mood, int weights, cudaStream_t s);
+void launch_tubes_update(const TubesDev& t, int stage, const double* Un, const double* Us, double* Uout,
+                         const double* Fh, const double* us, const double* dt_dev, unsigned long long* nbad,
+                         cudaStream_t s);
+
+}  // namespace ws
