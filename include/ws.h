@@ -182,6 +182,35 @@ WS_API int ws_profile_read(ws_ctx *ctx, double ms[WS_NKERNEL], int64_t launches[
  * over a launch of blocks x 256 threads (blocks <= 0: 8 per SM).  Synchronises. */
 WS_API int ws_peak_probe(int kind, int blocks, double *tflops);
 
+/* ---- allocation-free flux divergence ----
+ * The paper has no counterpart to this entry point: it serves callers that
+ * cannot call cudaMalloc, such as a host application whose device memory is
+ * owned by another allocator or a fixed budget (a framework's caching pool, a
+ * plugin host), or a latency-critical loop that must not allocate after
+ * start-up.  They cannot create a ws_ctx (ws_init allocates scratch), so this
+ * call takes the grid and options directly and uses as scratch one file-scope
+ * device array of WS_NOALLOC_SCRATCH_BYTES that every GPU loading the library
+ * holds until the process exits.  It allocates nothing: no cudaMalloc, no
+ * cudaFree, no allocating library routine.
+ *
+ * Computes the same L(U) as ws_flux_divergence (FP64, same kernels, same bits;
+ * no MOOD mask is kept).  U (DEVICE, ghosts overwritten from the boundary
+ * conditions) and L (DEVICE, interior written) are caller buffers in the state
+ * layout above.  Grids whose primitive cache plus face fluxes exceed the
+ * scratch (beyond 313 x 313 cells in 2D, 38^3 in 3D or 174756 cells in 1D) are
+ * rejected with WS_EINVAL; batched tubes and mixed precision with WS_ENOTSUP.
+ * err (nullable, HOST, err_len bytes) receives a message on failure.
+ * Work is enqueued on `stream` (a cudaStream_t; NULL = legacy default).
+ * The first call on each device looks up the scratch's device address with
+ * cudaGetSymbolAddress, with that device current; make that first call
+ * before any stream capture.  All calls share the one array and it keeps the
+ * last call's contents (each call writes what it reads first, so nothing needs
+ * clearing); calls whose work overlaps on the GPU, from any thread or stream,
+ * race on it and must be serialised by the caller. */
+#define WS_NOALLOC_SCRATCH_BYTES (16LL * 1024 * 1024)
+WS_API int ws_flux_divergence_noalloc(const ws_grid *grid, const ws_opts *opts, void *stream, double *U,
+                                      double *L, char *err, int err_len);
+
 /* Message of the last failing call on ctx (never NULL; "" when none). */
 WS_API const char *ws_last_error(const ws_ctx *ctx);
 

@@ -81,6 +81,8 @@ def load():
         "ws_profile": (ctypes.c_int, [vp, ctypes.c_int]),
         "ws_profile_read": (ctypes.c_int, [vp, dp, ctypes.POINTER(ctypes.c_int64)]),
         "ws_peak_probe": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, dp]),
+        "ws_flux_divergence_noalloc": (ctypes.c_int, [ctypes.POINTER(ws_grid), ctypes.POINTER(ws_opts), vp, vp, vp,
+                                                      ctypes.c_char_p, ctypes.c_int]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -210,6 +212,17 @@ def ws_peak_probe(kind: str, blocks: int = 0) -> float:
     if rc != WS_OK:
         raise WsError(rc, "peak probe failed")
     return t.value
+
+
+def ws_flux_divergence_noalloc(grid: ws_grid, opts: ws_opts, stream: int, U, L):
+    """L(U) without any device allocation (static scratch inside the library);
+    for callers that cannot call cudaMalloc.  Raises WsError with the
+    library's message on failure."""
+    buf = ctypes.create_string_buffer(256)
+    rc = load().ws_flux_divergence_noalloc(ctypes.byref(grid), ctypes.byref(opts), ctypes.c_void_p(stream), _ptr(U),
+                                           _ptr(L), buf, 256)
+    if rc != WS_OK:
+        raise WsError(rc, buf.value.decode())
 
 
 def ws_destroy(ctx):
