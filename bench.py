@@ -163,6 +163,26 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def l1_vs_fp64(ws, case, s_mixed, stream, steps):
+    """L1 relative density error of the mixed path against the FP64 path (which
+    is bit-identical to the FP64 oracle) after `steps` steps from the same
+    initial state, both with the FP64 path's CFL time steps."""
+    import torch
+    s64 = ws.Solver(2, case.n, case.dx, case.bc, precision="fp64", stream=stream)
+    U64 = s64.prim_to_cons(s64.tensor(case.Q))
+    U32 = s_mixed.prim_to_cons(s_mixed.tensor(case.Q))
+    for _ in range(steps):
+        dt = s64.step(U64, want_dt=True)
+        s_mixed.step(U32, dt)
+    torch.cuda.synchronize()
+    sl = wl.interior(2, case.n)
+    a = U32[sl][0].double()
+    b = U64[sl][0]
+    s64.close()
+    return {"steps": steps, "value": float((a - b).abs().sum() / b.abs().sum()),
+            "reference": "FP64 path (bit-identical to the FP64 oracle)"}
+
+
 def run_ours(args):
     import torch
     import paper_1707_00592_gb300 as ws
@@ -222,6 +242,10 @@ def run_ours(args):
         e2e_t = (time.perf_counter() - t0) / args.steps
         state_bytes = s.size * 8
 
+        l1 = None
+        if args.precision == "mixed" and args.l1_steps > 0:
+            l1 = l1_vs_fp64(ws, case, s, stream, args.l1_steps)
+
     clocks = clk.summary()
     if rank != 0:
         if ws_size > 1:
@@ -233,12 +257,15 @@ def run_ours(args):
     faces_per_launch = (n + 1) * n  # one direction of the 2D grid
     flops = face_flops(2) * faces_per_launch
     achieved = flops / per_launch_s / 1e12
-    fp64_peak = args.fp64_peak
-    if fp64_peak is None:
-        fp64_peak = ws.ws_peak_probe("fp64")
-    roofline = {"bound": "alu", "kernel": "face sweep (FP64)", "achieved": achieved, "peak": fp64_peak,
-                "unit": "TFLOP/s", "frac": achieved / fp64_peak, "traffic": None,
-                "peak_source": "FP64 FMA chain probe on this GPU (2 flops per DFMA)",
+    if args.precision == "fp64":
+        peak = args.fp64_peak if args.fp64_peak is not None else ws.ws_peak_probe("fp64")
+        kname, psrc = "face sweep (FP64)", "FP64 FMA chain probe on this GPU (2 flops per DFMA)"
+    else:
+        peak = args.fp32_peak if args.fp32_peak is not None else ws.ws_peak_probe("fp32")
+        kname, psrc = "face sweep (FP32 mixed)", "FP32 FMA chain probe on this GPU (2 flops per FFMA)"
+    roofline = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "peak_source": psrc,
                 "flops_per_face": face_flops(2), "faces_per_launch": faces_per_launch,
                 "face_ms_per_launch": per_launch_s * 1e3,
                 "share_of_step": face_ms / ms,
@@ -259,6 +286,8 @@ def run_ours(args):
                     "d2h_bytes_per_step": state_bytes}}
     if clocks:
         line["clocks"] = clocks
+    if l1 is not None:
+        line["l1_density_vs_fp64"] = l1
     if ws_size == 1 and not args.no_cpu_baseline:
         cells_c, times, cores = cpu_oracle_rate(n, args.cpu_rows, args.cpu_steps)
         line["cpu_baseline"] = {"kind": "oracle", "value": cells_c * len(times) / sum(times), "unit": UNIT,
@@ -283,6 +312,8 @@ def main():
     ap.add_argument("--ref-rows", type=int, default=128)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-peak", type=float, default=None)
+    ap.add_argument("--fp32-peak", type=float, default=None)
+    ap.add_argument("--l1-steps", type=int, default=0)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -84,7 +84,9 @@ typedef struct ws_opts {
   int weights;   /* WS_W_* */
   int mood;      /* 1: MOOD positivity cascade 5th -> 3rd -> 1st (Sec. 3.4); 0: off */
   int learned;   /* 1: smooth-face gate by the face-classifier MLP (mixed precision only) */
-  double eps;    /* WENO epsilon (the paper leaves it open); <= 0 selects 1e-40 (FP64) / 1e-30 (mixed) */
+  double eps;    /* WENO epsilon (the paper leaves it open).  FP64: absolute, <= 0 selects 1e-40.
+                    Mixed: relative to beta1 + beta2 + tau5 of the stencil (floor 1e-30), <= 0
+                    selects 1e-10 -- keeps tau5/(beta+eps) within FP32 range for p ~ 1e9 */
   double cfl;    /* CFL number; <= 0 selects 0.5 (Secs. 5, 6) */
   int check;     /* 1: ws_step synchronises and returns WS_ENONPHYS when a cell is inadmissible */
 } ws_opts;

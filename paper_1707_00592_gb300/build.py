@@ -25,6 +25,7 @@ UNITS = {
     "ws_fp64.cu": ["-fmad=false"],
     "ws_tubes.cu": ["-fmad=false"],
     "ws_probe.cu": [],
+    "ws_mixed.cu": [],
     "ws_noalloc.cu": ["-fmad=false"],
 }
 

@@ -1,0 +1,241 @@
+// Mixed-precision arithmetic of one face i+1/2: characteristic projection
+// (Sec. 3.2), WENO-IS of both sides (Secs. 3.3.1, 3.3.2), back-projection,
+// MOOD cascade (Sec. 3.4) and stiffened-gas HLLC (Sec. 3.2.1) in FP32 with
+// FMA, except the MOOD admissibility test, whose sign is decided exactly
+// (as an FP64 evaluation on the FP32 operands would decide it).
+//
+// FP32-specific choices (the method itself is unchanged):
+//  - WENO epsilon is relative: eps_eff = eps_rel * (beta1 + beta2 + tau5) +
+//    eps_abs, which keeps tau5/(beta+eps) and its products inside the FP32
+//    range for dimensional variables (p ~ 1e9) while acting, like the FP64
+//    epsilon, only where a smoothness indicator vanishes;
+//  - divisions use the hardware reciprocal (rcp.approx, about 1 ulp).
+#pragma once
+
+#include "ws_internal.h"
+
+namespace ws {
+namespace fp32 {
+
+struct WenoParams {
+  float eps_rel;  // relative epsilon
+  float eps_abs;  // absolute floor (keeps 0/0 away on flat stencils)
+  int weights;    // WS_W_MODIFIED or WS_W_BASIC
+};
+
+__device__ __forceinline__ float frcp(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ float fdiv(float a, float b) { return __fdividef(a, b); }
+
+// Sec. 3.3.1-3.3.2: left value at x_{i+1/2} from q_{i-2..i+2}; order 5 or 3.
+__device__ __forceinline__ float weno_is(float qm2, float qm1, float q0, float qp1, float qp2, const WenoParams& P,
+                                         int order) {
+  const float c13_12 = 13.0f / 12.0f;
+  float dp1 = qp1 - q0, dm1 = q0 - qm1;
+  float delta1 = 0.5f * dp1;
+  float delta2 = 0.5f * dm1;
+  float beta1 = dp1 * dp1;
+  float beta2 = dm1 * dm1;
+  float a = (qm1 - 2.0f * q0) + qp1;
+  float b = qm1 - qp1;
+  float beta12 = fmaf(c13_12, a * a, 0.25f * (b * b));
+  a = ((qp2 - 2.0f * qp1) + 2.0f * qm1) - qm2;
+  b = ((((qp2 - 4.0f * qp1) + 6.0f * q0) - 4.0f * qm1) + qm2);
+  float tau5 = fmaf(0.25f, a * a, c13_12 * (b * b));
+  float eps = fmaf(P.eps_rel, (beta1 + beta2) + tau5, P.eps_abs);
+  float r1 = fdiv(tau5, beta1 + eps);
+  float r2 = fdiv(tau5, beta2 + eps);
+  float alpha1, alpha2;
+  if (P.weights == WS_W_MODIFIED) {
+    float r12 = fdiv(tau5, beta12 + eps);
+    alpha1 = 4.0f * fmaf(r1, r12, 1.0f);
+    alpha2 = 2.0f * fmaf(r2, r12, 1.0f);
+  } else {
+    alpha1 = 4.0f * (1.0f + r1);
+    alpha2 = 2.0f * (1.0f + r2);
+  }
+  float num = fmaf(alpha1, delta1, alpha2 * delta2);
+  float den = alpha1 + alpha2;
+  if (order == 5) {
+    float d3 = qp2 - q0, d4 = qm2 - q0;
+    float delta3 = fmaf(5.0f / 6.0f, dp1, -(1.0f / 6.0f) * d3);
+    float delta4 = fmaf(1.0f / 3.0f, d4, (7.0f / 6.0f) * dm1);  // -(7/6)(q_{i-1}-q_i) = (7/6) dm1
+    a = (q0 - 2.0f * qp1) + qp2;
+    b = ((3.0f * q0) - (4.0f * qp1)) + qp2;
+    float beta3 = fmaf(c13_12, a * a, 0.25f * (b * b));
+    a = (qm2 - 2.0f * qm1) + q0;
+    b = (qm2 - (4.0f * qm1)) + (3.0f * q0);
+    float beta4 = fmaf(c13_12, a * a, 0.25f * (b * b));
+    float alpha3 = 3.0f * (1.0f + fdiv(tau5, beta3 + eps));
+    float alpha4 = 1.0f + fdiv(tau5, beta4 + eps);
+    num = fmaf(alpha3, delta3, fmaf(alpha4, delta4, num));
+    den = (den + alpha3) + alpha4;
+  }
+  return fmaf(num, frcp(den), q0);
+}
+
+__device__ __forceinline__ float sound_speed2(float rho, float p, float Gam, float Pi) {
+  return fdiv(fmaf(Gam + 1.0f, p, Pi), Gam * rho);
+}
+
+// Exact sign test of (Gamma+1) p + Pi > 0 on FP32 operands: the FP32 value is
+// trusted when it clears its rounding-error bound, otherwise the expression
+// is evaluated in FP64 (exact for these operands up to the final rounding,
+// which preserves the sign).
+__device__ __forceinline__ bool pressure_admissible(float Gam, float p, float Pi) {
+  float g1 = Gam + 1.0f;
+  float t = fmaf(g1, p, Pi);
+  float bound = 4.0e-7f * (fabsf(g1 * p) + fabsf(Pi)) + 1e-37f;
+  if (t > bound) return true;
+  if (t < -bound) return false;
+  double e = ((double)Gam + 1.0) * (double)p + (double)Pi;
+  return e > 0.0;
+}
+
+template <int NQ>
+__device__ __forceinline__ bool admissible(const float* q) {
+  return (q[0] > 0.0f) && (q[NQ - 2] > 0.0f) && pressure_admissible(q[NQ - 2], q[NQ - 3], q[NQ - 1]);
+}
+
+// Characteristic variable r of the sweep-frame primitive q (Eq. eigen-vectors).
+template <int NQ>
+__device__ __forceinline__ float project(const float* q, int r, float hrc, float ic2) {
+  constexpr int NT = NQ - 5, IP = 2 + NT;
+  if (r == 0) return 0.5f * fmaf(-2.0f * hrc, q[1], q[IP]) ;
+  if (r == 1) return fmaf(-ic2, q[IP], q[0]);
+  if (r == NQ - 1) return 0.5f * fmaf(2.0f * hrc, q[1], q[IP]);
+  if (r < IP) return q[r];
+  return q[r + 1];
+}
+
+template <int NQ>
+__device__ __forceinline__ void back_project(const float* w, float ic2, float irc, float* q) {
+  constexpr int NT = NQ - 5, IP = 2 + NT;
+  q[0] = fmaf(ic2, w[0] + w[NQ - 1], w[1]);
+  q[1] = irc * (w[NQ - 1] - w[0]);
+#pragma unroll
+  for (int t = 0; t < NT; ++t) q[2 + t] = w[2 + t];
+  q[IP] = w[0] + w[NQ - 1];
+  q[IP + 1] = w[IP];
+  q[IP + 2] = w[IP + 1];
+}
+
+// Sec. 3.2.1 HLLC in FP32.
+template <int NQ>
+__device__ __forceinline__ void hllc(const float* ql, const float* qr, float* Fhat, float& ustar) {
+  constexpr int NT = NQ - 5;
+  float U[2][NQ], F[2][NQ], c2[2], cc[2];
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const float* q = k == 0 ? ql : qr;
+    float rho = q[0], un = q[1], p = q[2 + NT], Gam = q[3 + NT], Pi = q[4 + NT];
+    float usq = un * un;
+#pragma unroll
+    for (int t = 0; t < NT; ++t) usq = fmaf(q[2 + t], q[2 + t], usq);
+    float E = fmaf(Gam, p, Pi) + (0.5f * rho) * usq;
+    float mn = rho * un;
+    U[k][0] = rho;
+    U[k][1] = mn;
+    F[k][0] = mn;
+    F[k][1] = fmaf(mn, un, p);
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+      U[k][2 + t] = rho * q[2 + t];
+      F[k][2 + t] = mn * q[2 + t];
+    }
+    U[k][2 + NT] = E;
+    F[k][2 + NT] = (E + p) * un;
+    U[k][3 + NT] = Gam;
+    F[k][3 + NT] = Gam * un;
+    U[k][4 + NT] = Pi;
+    F[k][4 + NT] = Pi * un;
+    c2[k] = sound_speed2(rho, p, Gam, Pi);
+    cc[k] = sqrtf(c2[k]);
+  }
+  float rl = ql[0], ul = ql[1], pl = ql[2 + NT];
+  float rr = qr[0], ur = qr[1], pr = qr[2 + NT];
+  float sl = sqrtf(rl), sr = sqrtf(rr);
+  float iden = frcp(sl + sr);
+  float ubar = fmaf(sl, ul, sr * ur) * iden;
+  float du = ur - ul;
+  float c2bar = fmaf(sl, c2[0], sr * c2[1]) * iden + (0.5f * (sl * sr) * (iden * iden)) * (du * du);
+  float cbar = sqrtf(c2bar);
+  float Sl = fminf(fminf(ubar - cbar, ul - cc[0]), 0.0f);
+  float Sr = fmaxf(fmaxf(ubar + cbar, ur + cc[1]), 0.0f);
+  float ml = rl * (Sl - ul), mr = rr * (Sr - ur);
+  float Ss = fdiv(fmaf(ml, ul, pr - pl) - mr * ur, ml - mr);
+  float s = (Ss > 0.0f) ? 1.0f : ((Ss < 0.0f) ? -1.0f : 0.0f);
+  float wl = 0.5f * (1.0f + s), wr = 0.5f * (1.0f - s);
+  float Fs[2][NQ], us[2];
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const float* q = k == 0 ? ql : qr;
+    float S = k == 0 ? Sl : Sr;
+    float rho = q[0], un = q[1], p = q[2 + NT];
+    if (S == Ss) {
+#pragma unroll
+      for (int m = 0; m < NQ; ++m) Fs[k][m] = F[k][m];
+      us[k] = un;
+    } else {
+      float Pk = fmaf(rho * (S - un), Ss - un, p);
+      float SP = S * Pk;
+      float idS = frcp(S - Ss);
+#pragma unroll
+      for (int m = 0; m < NQ; ++m) {
+        float t = Ss * fmaf(S, U[k][m], -F[k][m]);
+        if (m == 1) t += SP;
+        if (m == 2 + NT) t = fmaf(SP, Ss, t);
+        Fs[k][m] = t * idS;
+      }
+      us[k] = Ss * (S - un) * idS;
+    }
+  }
+#pragma unroll
+  for (int m = 0; m < NQ; ++m) Fhat[m] = fmaf(wl, Fs[0][m], wr * Fs[1][m]);
+  ustar = fmaf(wl, us[0], wr * us[1]);
+}
+
+// One face from sweep-frame FP32 primitives of cells i-2..i+3 and their sound
+// speeds.  code_l / code_r: 0, 1, 2 for 5th, 3rd, 1st order.
+template <int NQ>
+__device__ __forceinline__ void face(const float (&qc)[6][NQ], const float (&cc)[6], const WenoParams& P, int mood,
+                                     float* Fhat, float& ustar, int& code_l, int& code_r) {
+  float rho_bar = 0.5f * (qc[2][0] + qc[3][0]);
+  float c_bar = 0.5f * (cc[2] + cc[3]);
+  float rc = rho_bar * c_bar;
+  float hrc = 0.5f * rc;
+  float ic2 = frcp(c_bar * c_bar);
+  float irc = frcp(rc);
+  float q[2][NQ];
+  int code[2];
+#pragma unroll
+  for (int side = 0; side < 2; ++side) {
+    int order = 5;
+    code[side] = 0;
+    for (int pass = 0; pass < 2; ++pass) {
+      float wt[NQ];
+#pragma unroll
+      for (int r = 0; r < NQ; ++r) {
+        float v[5];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) v[k] = project<NQ>(qc[side == 0 ? k : 5 - k], r, hrc, ic2);
+        wt[r] = weno_is(v[0], v[1], v[2], v[3], v[4], P, order);
+      }
+      back_project<NQ>(wt, ic2, irc, q[side]);
+      if (!mood || admissible<NQ>(q[side])) break;
+      if (pass == 0) {
+        order = 3;
+        code[side] = 1;
+        continue;
+      }
+#pragma unroll
+      for (int r = 0; r < NQ; ++r) q[side][r] = qc[2 + side][r];
+      code[side] = 2;
+    }
+  }
+  code_l = code[0];
+  code_r = code[1];
+  hllc<NQ>(q[0], q[1], Fhat, ustar);
+}
+
+}  // namespace fp32
+}  // namespace ws

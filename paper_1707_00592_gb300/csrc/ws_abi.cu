@@ -77,6 +77,7 @@ struct KScope {
 void free_all(ws_ctx* c) {
   cudaFree(c->S1);
   cudaFree(c->Q);
+  cudaFree(c->Q32);
   for (int d = 0; d < 3; ++d) {
     cudaFree(c->Fh[d]);
     cudaFree(c->us[d]);
@@ -97,6 +98,7 @@ void free_all(ws_ctx* c) {
 }
 
 bool tubes(const ws_ctx* c) { return c->grid.ntubes > 0; }
+bool mixed(const ws_ctx* c) { return c->opts.precision == WS_PREC_MIXED; }
 
 // one RHS evaluation of the stage state Us into the face arrays
 int rhs_faces(ws_ctx* c, double* Us) {
@@ -107,7 +109,10 @@ int rhs_faces(ws_ctx* c, double* Us) {
   }
   {
     KScope k(c, WS_K_PRIM);
-    launch_prim(g, Us, c->Q, c->stream);
+    if (mixed(c))
+      launch_prim32(g, Us, c->Q32, c->stream);
+    else
+      launch_prim(g, Us, c->Q, c->stream);
   }
   return check_launch(c, "ghost/prim");
 }
@@ -117,18 +122,22 @@ int faces(ws_ctx* c, int stage_slot) {
   uint8_t* mbase = c->mask + (int64_t)stage_slot * c->nmask;
   for (int d = 0; d < g.ndim; ++d) {
     KScope k(c, WS_K_FACE);
-    if (c->opts.precision == WS_PREC_FP64)
+    if (mixed(c))
+      launch_face_mixed(g, d, c->Q32, c->Fh32[d], c->us32[d], mbase + c->mask_off[d], (float)c->opts.eps,
+                        c->opts.mood, c->opts.weights, c->stream);
+    else
       launch_face_fp64(g, d, c->Q, c->Fh[d], c->us[d], mbase + c->mask_off[d], c->opts.eps, c->opts.mood,
                        c->opts.weights, c->stream);
-    else
-      return fail(c, WS_ENOTSUP, "mixed precision sweep not built");
   }
   return check_launch(c, "face sweep");
 }
 
 int update(ws_ctx* c, int stage, const double* Un, const double* Us, double* Uout) {
   KScope k(c, WS_K_UPDATE);
-  launch_update(c->gd, stage, Un, Us, Uout, c->Fh, c->us, c->dt_dev, c->nbad, c->stream);
+  if (mixed(c))
+    launch_update_mixed(c->gd, stage, Un, Us, Uout, c->Fh32, c->us32, c->Q32, c->dt_dev, c->nbad, c->stream);
+  else
+    launch_update(c->gd, stage, Un, Us, Uout, c->Fh, c->us, c->dt_dev, c->nbad, c->stream);
   return check_launch(c, "update");
 }
 
@@ -182,7 +191,10 @@ int step_device(ws_ctx* c, double* U, double dt) {
       if (dt <= 0.0) {
         CK(c, cudaMemsetAsync(c->lmax, 0, sizeof(unsigned long long), c->stream));
         KScope k(c, WS_K_CFL);
-        launch_cfl(g, c->Q, c->lmax, c->stream);
+        if (mixed(c))
+          launch_cfl32(g, c->Q32, c->lmax, c->stream);
+        else
+          launch_cfl(g, c->Q, c->lmax, c->stream);
       }
       KScope k(c, WS_K_CFL);
       launch_set_dt(nullptr, dt, c->opts.cfl, c->lmax, c->dt_dev, 1, c->stream);
@@ -230,10 +242,11 @@ int ws_init(const ws_grid* grid, const ws_opts* opts, void* stream, ws_ctx** out
   if (op.mood != 0 && op.mood != 1) return fail(nullptr, WS_EINVAL, "mood must be 0 or 1");
   if (op.learned && op.precision != WS_PREC_MIXED)
     return fail(nullptr, WS_EINVAL, "the learned gate runs in mixed precision only");
-  if (op.eps <= 0.0) op.eps = op.precision == WS_PREC_FP64 ? 1e-40 : 1e-30;
+  if (op.eps <= 0.0) op.eps = op.precision == WS_PREC_FP64 ? 1e-40 : 1e-10;
   if (op.cfl <= 0.0) op.cfl = 0.5;
-  if (op.precision == WS_PREC_MIXED || op.learned)
-    return fail(nullptr, WS_ENOTSUP, "mixed precision path not built in this library");
+  if (op.learned) return fail(nullptr, WS_ENOTSUP, "the learned face gate is not built in this library");
+  if (tb && op.precision == WS_PREC_MIXED)
+    return fail(nullptr, WS_ENOTSUP, "batched tubes run in FP64 in this library");
 
   ws_ctx* c = new (std::nothrow) ws_ctx();
   if (!c) return fail(nullptr, WS_ECUDA, "out of host memory");
@@ -270,13 +283,21 @@ int ws_init(const ws_grid* grid, const ws_opts* opts, void* stream, ws_ctx** out
     }
     c->nmask = off;
     c->nstate = (int64_t)g.nv * g.N;
-    if ((rc = dalloc(c, &c->S1, c->nstate)) || (rc = dalloc(c, &c->Q, (int64_t)(g.nv + 1) * g.N)) ||
-        (rc = dalloc(c, &c->mask, 3 * c->nmask)) || (rc = dalloc(c, &c->dt_dev, 1)) ||
-        (rc = dalloc(c, &c->lmax, 1)) || (rc = dalloc(c, &c->nbad, 1)))
+    if ((rc = dalloc(c, &c->S1, c->nstate)) || (rc = dalloc(c, &c->mask, 3 * c->nmask)) ||
+        (rc = dalloc(c, &c->dt_dev, 1)) || (rc = dalloc(c, &c->lmax, 1)) || (rc = dalloc(c, &c->nbad, 1)))
       goto bad;
-    for (int d = 0; d < gr.ndim; ++d)
-      if ((rc = dalloc(c, &c->Fh[d], (int64_t)g.nv * g.nfaces[d])) || (rc = dalloc(c, &c->us[d], g.nfaces[d])))
-        goto bad;
+    if (op.precision == WS_PREC_MIXED) {
+      if ((rc = dalloc(c, &c->Q32, (int64_t)(g.nv + 1) * g.N))) goto bad;
+      for (int d = 0; d < gr.ndim; ++d)
+        if ((rc = dalloc(c, &c->Fh32[d], (int64_t)g.nv * g.nfaces[d])) ||
+            (rc = dalloc(c, &c->us32[d], g.nfaces[d])))
+          goto bad;
+    } else {
+      if ((rc = dalloc(c, &c->Q, (int64_t)(g.nv + 1) * g.N))) goto bad;
+      for (int d = 0; d < gr.ndim; ++d)
+        if ((rc = dalloc(c, &c->Fh[d], (int64_t)g.nv * g.nfaces[d])) || (rc = dalloc(c, &c->us[d], g.nfaces[d])))
+          goto bad;
+    }
   } else {
     int64_t nt = gr.ntubes;
     std::vector<int64_t> off(grid->tube_offsets, grid->tube_offsets + nt + 1);
@@ -381,7 +402,10 @@ int ws_cfl_dt(ws_ctx* c, double* U, double* dt) {
     int rc = rhs_faces(c, U);
     if (rc) return rc;
     CK(c, cudaMemsetAsync(c->lmax, 0, sizeof(unsigned long long), c->stream));
-    launch_cfl(c->gd, c->Q, c->lmax, c->stream);
+    if (mixed(c))
+      launch_cfl32(c->gd, c->Q32, c->lmax, c->stream);
+    else
+      launch_cfl(c->gd, c->Q, c->lmax, c->stream);
   }
   launch_set_dt(nullptr, 0.0, c->opts.cfl, c->lmax, c->dt_dev, n, c->stream);
   int rc = check_launch(c, "cfl");

@@ -308,13 +308,6 @@ void launch_update(const GridDev& g, int stage, const double* Un, const double* 
                                                       us[2], dt_dev, nbad);
 }
 
-void launch_update_mixed(const GridDev& g, int stage, const double* Un, const double* Us, double* Uout,
-                         float* const Fh[3], float* const us[3], const double* dt_dev, unsigned long long* nbad,
-                         cudaStream_t s) {
-  k_update<float><<<blocks_for(g.ncell), BS, 0, s>>>(g, stage, Un, Us, Uout, Fh[0], Fh[1], Fh[2], us[0], us[1],
-                                                     us[2], dt_dev, nbad);
-}
-
 void launch_mood_count(const uint8_t* mask, int64_t n, int64_t nstage, const int64_t* dir_off, int ndim,
                        unsigned long long* counts, cudaStream_t s) {
   int b = blocks_for(n * nstage);

@@ -51,6 +51,7 @@ struct ws_ctx {
   // scratch (device)
   double* S1 = nullptr;         // RK stage state
   double* Q = nullptr;          // primitives + sound speed, nv+1 fields
+  float* Q32 = nullptr;         // mixed precision: FP32 primitives + sound speed
   double* Fh[3] = {nullptr, nullptr, nullptr};  // face fluxes per direction (nv fields)
   double* us[3] = {nullptr, nullptr, nullptr};  // face velocities per direction
   float* Fh32[3] = {nullptr, nullptr, nullptr}; // mixed precision face fluxes
@@ -90,15 +91,21 @@ void launch_set_dt(const double* dt_fixed_or_null, double dt_fixed, double cfl, 
 void launch_update(const GridDev& g, int stage, const double* Un, const double* Us, double* Uout,
                    double* const Fh[3], double* const us[3], const double* dt_dev, unsigned long long* nbad,
                    cudaStream_t s);
-void launch_update_mixed(const GridDev& g, int stage, const double* Un, const double* Us, double* Uout,
-                         float* const Fh[3], float* const us[3], const double* dt_dev, unsigned long long* nbad,
-                         cudaStream_t s);
 void launch_mood_count(const uint8_t* mask, int64_t n, int64_t nstage, const int64_t* dir_off, int ndim,
                        unsigned long long* counts, cudaStream_t s);
 
 // ---- FP64 sweep (ws_fp64.cu, built with -fmad=false) ----
 void launch_face_fp64(const GridDev& g, int d, const double* Q, double* Fh, double* us, uint8_t* mask,
                       double eps, int mood, int weights, cudaStream_t s);
+
+// ---- mixed-precision sweep (ws_mixed.cu, FMA allowed) ----
+void launch_prim32(const GridDev& g, const double* U, float* Q, cudaStream_t s);
+void launch_cfl32(const GridDev& g, const float* Q, unsigned long long* lmax, cudaStream_t s);
+void launch_face_mixed(const GridDev& g, int d, const float* Q, float* Fh, float* us, uint8_t* mask, float eps_rel,
+                       int mood, int weights, cudaStream_t s);
+void launch_update_mixed(const GridDev& g, int stage, const double* Un, const double* Us, double* Uout,
+                         float* const Fh[3], float* const us[3], const float* Q, const double* dt_dev,
+                         unsigned long long* nbad, cudaStream_t s);
 
 // ---- batched tubes (ws_tubes.cu) ----
 void launch_tubes_ghost(const TubesDev& t, double* U, cudaStream_t s);

@@ -1,0 +1,118 @@
+"""Mixed-precision path (FP32 projection / WENO-IS / HLLC, FP64 pressure
+recovery, MOOD sign test and RK accumulation) against the FP64 oracle.
+
+Tolerances follow from FP32 arithmetic (unit roundoff 6e-8): a single
+evaluation of L(U) agrees with the oracle to ~1e-5 of the field's flux scale
+(the divergence subtracts fluxes of neighbouring faces), and short
+trajectories agree in L1 to well inside the 1e-4 relative density bound the
+mixed form is held to."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1707_00592_gb300 import workloads as wl
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("needs a GPU", allow_module_level=True)
+
+import paper_1707_00592_gb300 as ws  # noqa: E402
+
+
+def solver_for(case, **kw):
+    return ws.Solver(case.ndim, case.n, case.dx, case.bc, precision="mixed", **kw)
+
+
+def ogrid(case, mood=True):
+    return oracle.Grid(case.ndim, case.n, case.dx, case.bc, mood=mood)
+
+
+CASES = [(1, (61,), "smooth"), (1, (97,), "two_phase"), (2, (37, 29), "smooth"), (2, (33, 18), "shock"),
+         (2, (40, 35), "two_phase"), (3, (13, 11, 9), "smooth"), (3, (12, 10, 14), "two_phase")]
+
+
+@pytest.mark.parametrize("ndim,n,kind", CASES)
+def test_flux_divergence_close(ndim, n, kind):
+    case = wl.random_state(ndim, n, seed=5, kind=kind)
+    s = solver_for(case)
+    Uo = oracle.prim_to_cons(ndim, case.Q)
+    L = s.flux_divergence(s.tensor(Uo)).cpu().numpy()
+    Lo, mo = oracle.rhs(ogrid(case), Uo)
+    sl = wl.interior(ndim, case.n)
+    # flux scale of each field: |F| ~ |U| (|u| + c), divided by dx
+    Qo = oracle.cons_to_prim(ndim, Uo)[sl]
+    c = np.sqrt(((Qo[-2] + 1) * Qo[-3] + Qo[-1]) / (Qo[-2] * Qo[0]))
+    speed = c + sum(np.abs(Qo[1 + d]) for d in range(ndim))
+    dxmin = min(case.dx[:ndim])
+    _, mask = s.mood(with_mask=True)
+    agree = np.mean(mask.cpu().numpy()[:s.nmask] == np.concatenate([m.ravel() for m in mo]))
+    assert agree > 0.99
+    for f in range(case.nv):
+        scale = np.abs(Uo[sl][f] * speed).max() / dxmin
+        err = np.abs(L[sl][f] - Lo[sl][f]).max()
+        assert err <= 2e-5 * scale, (f, err, scale)
+
+
+def l1_rel(a, b):
+    return np.abs(a - b).sum() / np.abs(b).sum()
+
+
+def test_gas_water_tube_l1():
+    """The gas-water shock tube to t = 2.4e-4 s: L1 density error vs the oracle."""
+    case = wl.gas_water_tube(200)
+    s = solver_for(case, check=True)
+    g = ogrid(case)
+    Uo = oracle.prim_to_cons(1, case.Q)
+    U = s.tensor(Uo)
+    t = 0.0
+    while t < case.t_end:
+        dt = min(oracle.cfl_dt(g, Uo), case.t_end - t)
+        s.step(U, dt)
+        Uo, _, _ = oracle.step(g, Uo, dt=dt)
+        t += dt
+    sl = wl.interior(1, case.n)
+    assert l1_rel(U.cpu().numpy()[sl][0], Uo[sl][0]) < 1e-5
+
+
+def test_shock_bubble_small_l1():
+    """96^2 shock-bubble, 40 steps with the oracle's time steps: L1 density error."""
+    case = wl.shock_bubble_2d(96)
+    s = solver_for(case, check=True)
+    g = ogrid(case)
+    Uo = oracle.prim_to_cons(2, case.Q)
+    U = s.tensor(Uo)
+    for _ in range(40):
+        dt = oracle.cfl_dt(g, Uo)
+        s.step(U, dt)
+        Uo, _, _ = oracle.step(g, Uo, dt=dt)
+    sl = wl.interior(2, case.n)
+    assert l1_rel(U.cpu().numpy()[sl][0], Uo[sl][0]) < 1e-5
+
+
+def test_interface_equilibrium_mixed():
+    """Sec. 5.1 interface transport: p and u stay uniform to the accuracy FP32
+    fluxes allow.  In the liquid E ~ 8.5e3 (Pi = 3.5e3, rho u^2/2 = 5e3) while
+    Gamma p = 0.17, so a flux rounded to FP32 (6e-8 relative) moves p by about
+    6e-8 x 8.5e3 / 0.17 = 3e-3 per rounding: the bound on p is 2e-2, on u 1e-4.
+    (The FP64 path keeps both to ~1e-10.)"""
+    case = wl.interface_transport(200)
+    s = solver_for(case)
+    U = s.prim_to_cons(s.tensor(case.Q))
+    t = 0.0
+    while t < case.t_end:
+        dt = min(s.cfl_dt(U), case.t_end - t)
+        s.step(U, dt)
+        t += dt
+    Q = s.cons_to_prim(U).cpu().numpy()[wl.interior(1, case.n)]
+    assert np.abs(Q[2] - 1.0).max() < 2e-2
+    assert np.abs(Q[1] / 100.0 - 1.0).max() < 1e-4
+
+
+def test_mixed_cfl_close_to_fp64():
+    case = wl.shock_bubble_2d(128)
+    s = solver_for(case)
+    Uo = oracle.prim_to_cons(2, case.Q)
+    dt = s.cfl_dt(s.tensor(Uo))
+    assert dt == pytest.approx(oracle.cfl_dt(ogrid(case), Uo), rel=1e-6)
