@@ -26,6 +26,7 @@ UNITS = {
     "ws_tubes.cu": ["-fmad=false"],
     "ws_probe.cu": [],
     "ws_mixed.cu": [],
+    "ws_fused2d.cu": [],
     "ws_noalloc.cu": ["-fmad=false"],
 }
 

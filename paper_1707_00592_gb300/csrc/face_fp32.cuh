@@ -9,7 +9,7 @@
 //    eps_abs, which keeps tau5/(beta+eps) and its products inside the FP32
 //    range for dimensional variables (p ~ 1e9) while acting, like the FP64
 //    epsilon, only where a smoothness indicator vanishes;
-//  - divisions use the hardware reciprocal (rcp.approx, about 1 ulp).
+//  - divisions and square roots use the hardware approximations (about 1 ulp).
 #pragma once
 
 #include "ws_internal.h"
@@ -23,8 +23,19 @@ struct WenoParams {
   int weights;    // WS_W_MODIFIED or WS_W_BASIC
 };
 
-__device__ __forceinline__ float frcp(float x) { return __frcp_rn(x); }
-__device__ __forceinline__ float fdiv(float a, float b) { return __fdividef(a, b); }
+// hardware approximations (MUFU): rcp and sqrt to about 1 ulp, no IEEE
+// special-case sequences; subnormals flush to zero
+__device__ __forceinline__ float frcp(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float fsqrt(float x) {
+  float r;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float fdiv(float a, float b) { return a * frcp(b); }
 
 // Sec. 3.3.1-3.3.2: left value at x_{i+1/2} from q_{i-2..i+2}; order 5 or 3.
 __device__ __forceinline__ float weno_is(float qm2, float qm1, float q0, float qp1, float qp2, const WenoParams& P,
@@ -71,6 +82,51 @@ __device__ __forceinline__ float weno_is(float qm2, float qm1, float q0, float q
     den = (den + alpha3) + alpha4;
   }
   return fmaf(num, frcp(den), q0);
+}
+
+// Both MOOD levels of one side at once: v5 (all four candidates) and v3
+// (d3 = d4 = 0, the same tau5 and modified alpha1, alpha2).
+__device__ __forceinline__ void weno_is_both(float qm2, float qm1, float q0, float qp1, float qp2,
+                                             const WenoParams& P, float& v5, float& v3) {
+  const float c13_12 = 13.0f / 12.0f;
+  float dp1 = qp1 - q0, dm1 = q0 - qm1;
+  float beta1 = dp1 * dp1;
+  float beta2 = dm1 * dm1;
+  float a = (qm1 - 2.0f * q0) + qp1;
+  float b = qm1 - qp1;
+  float beta12 = fmaf(c13_12, a * a, 0.25f * (b * b));
+  a = ((qp2 - 2.0f * qp1) + 2.0f * qm1) - qm2;
+  b = ((((qp2 - 4.0f * qp1) + 6.0f * q0) - 4.0f * qm1) + qm2);
+  float tau5 = fmaf(0.25f, a * a, c13_12 * (b * b));
+  float eps = fmaf(P.eps_rel, (beta1 + beta2) + tau5, P.eps_abs);
+  float r1 = fdiv(tau5, beta1 + eps);
+  float r2 = fdiv(tau5, beta2 + eps);
+  float alpha1, alpha2;
+  if (P.weights == WS_W_MODIFIED) {
+    float r12 = fdiv(tau5, beta12 + eps);
+    alpha1 = 4.0f * fmaf(r1, r12, 1.0f);
+    alpha2 = 2.0f * fmaf(r2, r12, 1.0f);
+  } else {
+    alpha1 = 4.0f * (1.0f + r1);
+    alpha2 = 2.0f * (1.0f + r2);
+  }
+  float num3 = 0.5f * fmaf(alpha1, dp1, alpha2 * dm1);
+  float den3 = alpha1 + alpha2;
+  float d3 = qp2 - q0, d4 = qm2 - q0;
+  float delta3 = fmaf(5.0f / 6.0f, dp1, -(1.0f / 6.0f) * d3);
+  float delta4 = fmaf(1.0f / 3.0f, d4, (7.0f / 6.0f) * dm1);
+  a = (q0 - 2.0f * qp1) + qp2;
+  b = ((3.0f * q0) - (4.0f * qp1)) + qp2;
+  float beta3 = fmaf(c13_12, a * a, 0.25f * (b * b));
+  a = (qm2 - 2.0f * qm1) + q0;
+  b = (qm2 - (4.0f * qm1)) + (3.0f * q0);
+  float beta4 = fmaf(c13_12, a * a, 0.25f * (b * b));
+  float alpha3 = 3.0f * (1.0f + fdiv(tau5, beta3 + eps));
+  float alpha4 = 1.0f + fdiv(tau5, beta4 + eps);
+  float num5 = fmaf(alpha3, delta3, fmaf(alpha4, delta4, num3));
+  float den5 = (den3 + alpha3) + alpha4;
+  v3 = fmaf(num3, frcp(den3), q0);
+  v5 = fmaf(num5, frcp(den5), q0);
 }
 
 __device__ __forceinline__ float sound_speed2(float rho, float p, float Gam, float Pi) {
@@ -149,16 +205,16 @@ __device__ __forceinline__ void hllc(const float* ql, const float* qr, float* Fh
     U[k][4 + NT] = Pi;
     F[k][4 + NT] = Pi * un;
     c2[k] = sound_speed2(rho, p, Gam, Pi);
-    cc[k] = sqrtf(c2[k]);
+    cc[k] = fsqrt(c2[k]);
   }
   float rl = ql[0], ul = ql[1], pl = ql[2 + NT];
   float rr = qr[0], ur = qr[1], pr = qr[2 + NT];
-  float sl = sqrtf(rl), sr = sqrtf(rr);
+  float sl = fsqrt(rl), sr = fsqrt(rr);
   float iden = frcp(sl + sr);
   float ubar = fmaf(sl, ul, sr * ur) * iden;
   float du = ur - ul;
   float c2bar = fmaf(sl, c2[0], sr * c2[1]) * iden + (0.5f * (sl * sr) * (iden * iden)) * (du * du);
-  float cbar = sqrtf(c2bar);
+  float cbar = fsqrt(c2bar);
   float Sl = fminf(fminf(ubar - cbar, ul - cc[0]), 0.0f);
   float Sr = fmaxf(fmaxf(ubar + cbar, ur + cc[1]), 0.0f);
   float ml = rl * (Sl - ul), mr = rr * (Sr - ur);

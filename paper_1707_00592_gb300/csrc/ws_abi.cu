@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <stdarg.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <new>
@@ -78,6 +79,8 @@ void free_all(ws_ctx* c) {
   cudaFree(c->S1);
   cudaFree(c->Q);
   cudaFree(c->Q32);
+  cudaFree(c->Ka);
+  cudaFree(c->Kb);
   for (int d = 0; d < 3; ++d) {
     cudaFree(c->Fh[d]);
     cudaFree(c->us[d]);
@@ -184,6 +187,28 @@ int step_device(ws_ctx* c, double* U, double dt) {
     c->last_stages = 3;
     return WS_OK;
   }
+  if (c->fused) {
+    if (dt <= 0.0) {
+      CK(c, cudaMemsetAsync(c->lmax, 0, sizeof(unsigned long long), c->stream));
+      KScope k(c, WS_K_CFL);
+      launch_cfl_u(g, U, c->lmax, c->stream);
+    }
+    {
+      KScope k(c, WS_K_CFL);
+      launch_set_dt(nullptr, dt, c->opts.cfl, c->lmax, c->dt_dev, 1, c->stream);
+    }
+    for (int s = 0; s < 3; ++s) {
+      uint8_t* mb = c->mask + (int64_t)s * c->nmask;
+      KScope k(c, WS_K_FACE);
+      const double* Un = s == 2 ? c->S1 : U;
+      const float* Kin = s == 1 ? c->Ka : c->Kb;
+      float* Kout = s == 0 ? c->Ka : c->Kb;
+      launch_stage2d(g, s, Un, c->S1, U, Kin, Kout, c->dt_dev, mb + c->mask_off[0], mb + c->mask_off[1],
+                     (float)c->opts.eps, c->opts.mood, c->opts.weights, c->nbad, c->stream);
+    }
+    c->last_stages = 3;
+    return check_launch(c, "fused stage");
+  }
   for (int s = 0; s < 3; ++s) {
     double* Us = s == 0 ? U : c->S1;
     if ((rc = rhs_faces(c, Us))) return rc;
@@ -288,6 +313,14 @@ int ws_init(const ws_grid* grid, const ws_opts* opts, void* stream, ws_ctx** out
       goto bad;
     if (op.precision == WS_PREC_MIXED) {
       if ((rc = dalloc(c, &c->Q32, (int64_t)(g.nv + 1) * g.N))) goto bad;
+      if (gr.ndim == 2 && !getenv("WS_NO_FUSED")) {
+        if ((rc = dalloc(c, &c->Ka, (int64_t)g.nv * g.N)) || (rc = dalloc(c, &c->Kb, (int64_t)g.nv * g.N))) goto bad;
+        if (fused2d_prepare() != cudaSuccess) {
+          rc = fail(c, WS_ECUDA, "cannot enable %d bytes of shared memory for the fused stage", fused2d_smem_bytes());
+          goto bad;
+        }
+        c->fused = true;
+      }
       for (int d = 0; d < gr.ndim; ++d)
         if ((rc = dalloc(c, &c->Fh32[d], (int64_t)g.nv * g.nfaces[d])) ||
             (rc = dalloc(c, &c->us32[d], g.nfaces[d])))

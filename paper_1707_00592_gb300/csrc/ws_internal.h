@@ -52,6 +52,9 @@ struct ws_ctx {
   double* S1 = nullptr;         // RK stage state
   double* Q = nullptr;          // primitives + sound speed, nv+1 fields
   float* Q32 = nullptr;         // mixed precision: FP32 primitives + sound speed
+  float* Ka = nullptr;          // fused 2D: RK increments K0 (stage 0 -> 1)
+  float* Kb = nullptr;          // fused 2D: RK increments K1 (stage 1 -> 2)
+  bool fused = false;           // fused 2D mixed-precision stage kernels in use
   double* Fh[3] = {nullptr, nullptr, nullptr};  // face fluxes per direction (nv fields)
   double* us[3] = {nullptr, nullptr, nullptr};  // face velocities per direction
   float* Fh32[3] = {nullptr, nullptr, nullptr}; // mixed precision face fluxes
@@ -106,6 +109,15 @@ void launch_face_mixed(const GridDev& g, int d, const float* Q, float* Fh, float
 void launch_update_mixed(const GridDev& g, int stage, const double* Un, const double* Us, double* Uout,
                          float* const Fh[3], float* const us[3], const float* Q, const double* dt_dev,
                          unsigned long long* nbad, cudaStream_t s);
+
+void launch_cfl_u(const GridDev& g, const double* U, unsigned long long* lmax, cudaStream_t s);
+
+// ---- fused 2D mixed-precision RK stage (ws_fused2d.cu) ----
+int fused2d_smem_bytes();
+cudaError_t fused2d_prepare();
+void launch_stage2d(const GridDev& g, int stage, const double* Un, double* Ucopy, double* Uout, const float* Kin,
+                    float* Kout, const double* dt_dev, uint8_t* mask_x, uint8_t* mask_y, float eps_rel, int mood,
+                    int weights, unsigned long long* nbad, cudaStream_t s);
 
 // ---- batched tubes (ws_tubes.cu) ----
 void launch_tubes_ghost(const TubesDev& t, double* U, cudaStream_t s);

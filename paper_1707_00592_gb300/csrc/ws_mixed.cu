@@ -46,7 +46,7 @@ __device__ __forceinline__ void cons_to_prim32(const double* U, float* q, float&
   q[1 + NDIM] = p;
   q[2 + NDIM] = Gam;
   q[3 + NDIM] = Pi;
-  c = sqrtf(sound_speed2(rho, p, Gam, Pi));
+  c = fsqrt(sound_speed2(rho, p, Gam, Pi));
 }
 
 template <int NDIM>
@@ -240,7 +240,62 @@ __global__ void k_cfl32(GridDev g, const float* __restrict__ Q, unsigned long lo
   }
 }
 
+// CFL reduction straight from the FP64 state (no primitive cache)
+template <int NDIM>
+__global__ void k_cfl_u(GridDev g, const double* __restrict__ U, unsigned long long* lmax) {
+  constexpr int NV = NDIM + 4;
+  float idx_[3];
+#pragma unroll
+  for (int d = 0; d < NDIM; ++d) idx_[d] = (float)(1.0 / g.dx[d]);
+  float best = 0.0f;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < g.ncell; t += (int64_t)gridDim.x * blockDim.x) {
+    int64_t x = t % g.n[0];
+    int64_t r = t / g.n[0];
+    int64_t y = r % g.n[1];
+    int64_t z = r / g.n[1];
+    int64_t i = (g.G[0] + x) * g.st[0] + (g.G[1] + y) * g.st[1] + (g.G[2] + z) * g.st[2];
+    double u[NV];
+#pragma unroll
+    for (int f = 0; f < NV; ++f) u[f] = U[f * g.N + i];
+    float q[NV], c;
+    cons_to_prim32<NDIM>(u, q, c);
+    float lam = 0.0f;
+#pragma unroll
+    for (int d = 0; d < NDIM; ++d) lam = fmaf(fabsf(q[1 + d]) + c, idx_[d], lam);
+    if (!(lam <= best)) best = lam;
+  }
+  unsigned long long b = (unsigned long long)__double_as_longlong((double)best);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    unsigned long long v = __shfl_xor_sync(0xffffffffu, b, o);
+    b = v > b ? v : b;
+  }
+  __shared__ unsigned long long sm[32];
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) sm[w] = b;
+  __syncthreads();
+  if (w == 0) {
+    b = lane < (int)(blockDim.x >> 5) ? sm[lane] : 0ULL;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      unsigned long long v = __shfl_xor_sync(0xffffffffu, b, o);
+      b = v > b ? v : b;
+    }
+    if (lane == 0) atomicMax(lmax, b);
+  }
+}
+
 }  // namespace
+
+void launch_cfl_u(const GridDev& g, const double* U, unsigned long long* lmax, cudaStream_t s) {
+  int b = blocks_for(g.ncell);
+  if (b > 152 * 8) b = 152 * 8;
+  switch (g.ndim) {
+    case 1: k_cfl_u<1><<<b, BS, 0, s>>>(g, U, lmax); break;
+    case 2: k_cfl_u<2><<<b, BS, 0, s>>>(g, U, lmax); break;
+    default: k_cfl_u<3><<<b, BS, 0, s>>>(g, U, lmax); break;
+  }
+}
 
 void launch_cfl32(const GridDev& g, const float* Q, unsigned long long* lmax, cudaStream_t s) {
   int b = blocks_for(g.ncell);
