@@ -37,6 +37,31 @@ __device__ __forceinline__ float fsqrt(float x) {
 }
 __device__ __forceinline__ float fdiv(float a, float b) { return a * frcp(b); }
 
+// FP64 <-> FP32 conversions on the integer pipe (GB300 runs FP64-pipe
+// instructions at 1/64 of the FP32 rate).  f64_to_f32: round to nearest
+// even for values in the FP32 normal range, +-0 below it (the solver's
+// fields never exceed the FP32 range).  f32_to_f64: exact (+-0 for zero and
+// subnormal inputs).
+__device__ __forceinline__ float f64_to_f32(double x) {
+  unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+  unsigned sign = hi & 0x80000000u, mag = hi & 0x7fffffffu;
+  unsigned f = ((mag - (896u << 20)) << 3) | (lo >> 29);
+  unsigned rb = (lo >> 28) & 1u, sticky = lo & 0x0fffffffu;
+  f += rb & ((sticky != 0u) | (f & 1u));
+  f = mag < (897u << 20) ? 0u : f;
+  return __uint_as_float(sign | f);
+}
+__device__ __forceinline__ double f32_to_f64(float v) {
+  unsigned f = __float_as_uint(v);
+  unsigned mag = f & 0x7fffffffu;
+  unsigned hi = (f & 0x80000000u) | ((mag >> 3) + (896u << 20));
+  unsigned lo = f << 29;
+  hi = mag < 0x00800000u ? (f & 0x80000000u) : hi;
+  lo = mag < 0x00800000u ? 0u : lo;
+  return __longlong_as_double((long long)(((unsigned long long)hi << 32) | lo));
+}
+
 // Sec. 3.3.1-3.3.2: left value at x_{i+1/2} from q_{i-2..i+2}; order 5 or 3.
 __device__ __forceinline__ float weno_is(float qm2, float qm1, float q0, float qp1, float qp2, const WenoParams& P,
                                          int order) {

@@ -200,10 +200,9 @@ int step_device(ws_ctx* c, double* U, double dt) {
     for (int s = 0; s < 3; ++s) {
       uint8_t* mb = c->mask + (int64_t)s * c->nmask;
       KScope k(c, WS_K_FACE);
-      const double* Un = s == 2 ? c->S1 : U;
       const float* Kin = s == 1 ? c->Ka : c->Kb;
       float* Kout = s == 0 ? c->Ka : c->Kb;
-      launch_stage2d(g, s, Un, c->S1, U, Kin, Kout, c->dt_dev, mb + c->mask_off[0], mb + c->mask_off[1],
+      launch_stage2d(g, s, U, c->Q32, Kin, Kout, c->dt_dev, mb + c->mask_off[0], mb + c->mask_off[1],
                      (float)c->opts.eps, c->opts.mood, c->opts.weights, c->nbad, c->stream);
     }
     c->last_stages = 3;

@@ -20,10 +20,11 @@
 //   U1 = U + K0,  K0 = k0
 //   U2 = U + K1/4,  K1 = k0 + k1
 //   U' = U + K1/6 + 2 k2/3
-// The FP64 state U is read in every stage and updated once, in FP64; the
-// increments K (small against U) are FP32.  Stage 0 copies U to scratch so
-// that stage 2 can write U in place while neighbouring tiles still read their
-// halo from the copy; K0 and K1 live in separate buffers for the same reason.
+// The FP64 state U is converted to FP32 once, in stage 0 (E - Pi formed in
+// FP64 first), into a scratch image that stages 1 and 2 read together with
+// the FP32 increments K; stage 2 adds its increment to U in FP64, in place,
+// since no tile reads U's FP64 values after stage 0.  K0 and K1 live in
+// separate buffers because neighbouring tiles read K in their halos.
 #include <cuda_runtime.h>
 
 #include "face_fp32.cuh"
@@ -51,9 +52,8 @@ struct Smem {
 struct StageArgs {
   GridDev g;
   int stage;
-  const double* Un;   // state at t^n (stage 2: the copy made in stage 0)
-  double* Ucopy;      // stage 0: receives a copy of U
-  double* Uout;       // stage 2: new state
+  double* U;          // state at t^n; stage 2 replaces it with t^{n+1}
+  float* U32;         // FP32 image of U^n (rho, m_x, m_y, E - Pi, Gamma, Pi): written in stage 0
   const float* Kin;   // stages 1, 2: accumulated increments
   float* Kout;        // stages 0, 1
   const double* dtp;
@@ -180,18 +180,33 @@ __global__ void __launch_bounds__(NT, 2) k_stage2d(StageArgs a) {
     int mx = map_bc(gx, nx, g.bc[0][0], g.bc[0][1], fx);
     int my = map_bc(gy, ny, g.bc[1][0], g.bc[1][1], fy);
     int64_t i = (int64_t)(NG + my) * P0 + (NG + mx);
-    double E64 = a.Un[3 * N + i], P64 = a.Un[5 * N + i];
-    float rho = (float)a.Un[i], mu = (float)a.Un[N + i], mv = (float)a.Un[2 * N + i];
-    float eint = (float)(E64 - P64);
-    float Gam = (float)a.Un[4 * N + i], Pi = (float)P64;
-    if (a.stage > 0) {
+    float rho, mu, mv, eint, Gam, Pi;
+    if (a.stage == 0) {
+      const double* U = a.U;
+      rho = f64_to_f32(U[i]);
+      mu = f64_to_f32(U[N + i]);
+      mv = f64_to_f32(U[2 * N + i]);
+      eint = f64_to_f32(U[3 * N + i] - U[5 * N + i]);  // E - Pi in FP64
+      Gam = f64_to_f32(U[4 * N + i]);
+      Pi = f64_to_f32(U[5 * N + i]);
+      bool own = hx >= NG && hx < NG + TX && hy >= NG && hy < NG + TY && !outx && !outy;
+      if (own) {
+        a.U32[i] = rho;
+        a.U32[N + i] = mu;
+        a.U32[2 * N + i] = mv;
+        a.U32[3 * N + i] = eint;
+        a.U32[4 * N + i] = Gam;
+        a.U32[5 * N + i] = Pi;
+      }
+    } else {
+      const float* V = a.U32;
       const float* K = a.Kin;
-      rho = fmaf(coef, K[i], rho);
-      mu = fmaf(coef, K[N + i], mu);
-      mv = fmaf(coef, K[2 * N + i], mv);
-      eint = fmaf(coef, K[3 * N + i] - K[5 * N + i], eint);
-      Gam = fmaf(coef, K[4 * N + i], Gam);
-      Pi = fmaf(coef, K[5 * N + i], Pi);
+      rho = fmaf(coef, K[i], V[i]);
+      mu = fmaf(coef, K[N + i], V[N + i]);
+      mv = fmaf(coef, K[2 * N + i], V[2 * N + i]);
+      eint = fmaf(coef, K[3 * N + i] - K[5 * N + i], V[3 * N + i]);
+      Gam = fmaf(coef, K[4 * N + i], V[4 * N + i]);
+      Pi = fmaf(coef, K[5 * N + i], V[5 * N + i]);
     }
     float irho = frcp(rho);
     float u = mu * irho, v = mv * irho;
@@ -328,24 +343,25 @@ __global__ void __launch_bounds__(NT, 2) k_stage2d(StageArgs a) {
     }
     if (a.stage == 0) {
 #pragma unroll
-      for (int m = 0; m < NQ; ++m) {
-        a.Kout[m * N + gi] = inc[m];
-        a.Ucopy[m * N + gi] = a.Un[m * N + gi];
-      }
+      for (int m = 0; m < NQ; ++m) a.Kout[m * N + gi] = inc[m];
     } else if (a.stage == 1) {
 #pragma unroll
       for (int m = 0; m < NQ; ++m) a.Kout[m * N + gi] = a.Kin[m * N + gi] + inc[m];
     } else {
-      double o[NQ];
+      // this cell's U^n is read only here, by this thread, so U is updated in place
+      float d[NQ];
 #pragma unroll
       for (int m = 0; m < NQ; ++m) {
-        float d = fmaf(1.0f / 6.0f, a.Kin[m * N + gi], (2.0f / 3.0f) * inc[m]);
-        o[m] = a.Un[m * N + gi] + (double)d;
-        a.Uout[m * N + gi] = o[m];
+        d[m] = fmaf(1.0f / 6.0f, a.Kin[m * N + gi], (2.0f / 3.0f) * inc[m]);
+        a.U[m * N + gi] = a.U[m * N + gi] + f32_to_f64(d[m]);  // FP64 accumulation
       }
-      // rho > 0, Gamma > 0, (Gamma+1)(rho E - |m|^2/2) - rho Pi > 0
-      double t = fma(o[0], o[3], -0.5 * fma(o[1], o[1], o[2] * o[2]));
-      bool ok = o[0] > 0.0 && o[4] > 0.0 && fma(o[4] + 1.0, t, -o[0] * o[5]) > 0.0;
+      // admissibility of the new state (rho > 0, Gamma > 0, (Gamma+1) p + Pi > 0)
+      // from its FP32 image: a diagnostic, not part of the update
+      const float* V = a.U32;
+      float rho = V[gi] + d[0], mu = V[N + gi] + d[1], mv = V[2 * N + gi] + d[2];
+      float eint = V[3 * N + gi] + (d[3] - d[5]), Gam = V[4 * N + gi] + d[4], Pi = V[5 * N + gi] + d[5];
+      float pe = fmaf(-0.5f, (mu * mu + mv * mv) * frcp(rho), eint);  // Gamma p
+      bool ok = rho > 0.0f && Gam > 0.0f && fmaf(Gam + 1.0f, pe * frcp(Gam), Pi) > 0.0f;
       if (!ok) atomicAdd(a.nbad, 1ULL);
     }
   }
@@ -359,15 +375,14 @@ cudaError_t fused2d_prepare() {
   return cudaFuncSetAttribute(k_stage2d, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
 }
 
-void launch_stage2d(const GridDev& g, int stage, const double* Un, double* Ucopy, double* Uout, const float* Kin,
-                    float* Kout, const double* dt_dev, uint8_t* mask_x, uint8_t* mask_y, float eps_rel, int mood,
-                    int weights, unsigned long long* nbad, cudaStream_t s) {
+void launch_stage2d(const GridDev& g, int stage, double* U, float* U32, const float* Kin, float* Kout,
+                    const double* dt_dev, uint8_t* mask_x, uint8_t* mask_y, float eps_rel, int mood, int weights,
+                    unsigned long long* nbad, cudaStream_t s) {
   StageArgs a;
   a.g = g;
   a.stage = stage;
-  a.Un = Un;
-  a.Ucopy = Ucopy;
-  a.Uout = Uout;
+  a.U = U;
+  a.U32 = U32;
   a.Kin = Kin;
   a.Kout = Kout;
   a.dtp = dt_dev;
