@@ -188,22 +188,15 @@ int step_device(ws_ctx* c, double* U, double dt) {
     return WS_OK;
   }
   if (c->fused) {
-    if (dt <= 0.0) {
-      CK(c, cudaMemsetAsync(c->lmax, 0, sizeof(unsigned long long), c->stream));
-      KScope k(c, WS_K_CFL);
-      launch_cfl_u(g, U, c->lmax, c->stream);
-    }
-    {
-      KScope k(c, WS_K_CFL);
-      launch_set_dt(nullptr, dt, c->opts.cfl, c->lmax, c->dt_dev, 1, c->stream);
-    }
+    // the CFL reduction happens inside stage 0, dt is derived in stage 1
+    CK(c, cudaMemsetAsync(c->lmax, 0, sizeof(unsigned long long), c->stream));
     for (int s = 0; s < 3; ++s) {
       uint8_t* mb = c->mask + (int64_t)s * c->nmask;
       KScope k(c, WS_K_FACE);
       const float* Kin = s == 1 ? c->Ka : c->Kb;
       float* Kout = s == 0 ? c->Ka : c->Kb;
-      launch_stage2d(g, s, U, c->Q32, Kin, Kout, c->dt_dev, mb + c->mask_off[0], mb + c->mask_off[1],
-                     (float)c->opts.eps, c->opts.mood, c->opts.weights, c->nbad, c->stream);
+      launch_stage2d(g, s, U, c->Q32, Kin, Kout, dt, c->opts.cfl, c->lmax, c->dt_dev, mb + c->mask_off[0],
+                     mb + c->mask_off[1], (float)c->opts.eps, c->opts.mood, c->opts.weights, c->nbad, c->stream);
     }
     c->last_stages = 3;
     return check_launch(c, "fused stage");

@@ -15,11 +15,14 @@
 // SM, so one CTA's memory phases overlap the other's arithmetic.
 //
 // The Shu-Osher SSP-RK3 is carried in increment form, algebraically
-// identical to U1 = U + k0, U2 = 3/4 U + 1/4 (U1 + k1),
-// U' = 1/3 U + 2/3 (U2 + k2) with k_s = dt L(U_s):
-//   U1 = U + K0,  K0 = k0
-//   U2 = U + K1/4,  K1 = k0 + k1
-//   U' = U + K1/6 + 2 k2/3
+// identical to U1 = U + dt L0, U2 = 3/4 U + 1/4 (U1 + dt L1),
+// U' = 1/3 U + 2/3 (U2 + dt L2) with L_s = L(U_s):
+//   U1 = U + dt K0,  K0 = L0
+//   U2 = U + dt K1/4,  K1 = L0 + L1
+//   U' = U + dt (K1/6 + 2 L2/3)
+// Stage 0 needs no dt: it also reduces the CFL wave rate max sum_d
+// (|u_d| + c)/dx_d over its cells (atomicMax), and stage 1 derives
+// dt = CFL / max from it, so a step needs no separate CFL kernel.
 // The FP64 state U is converted to FP32 once, in stage 0 (E - Pi formed in
 // FP64 first), into a scratch image that stages 1 and 2 read together with
 // the FP32 increments K; stage 2 adds its increment to U in FP64, in place,
@@ -47,16 +50,21 @@ struct Smem {
   float w[2][NQ][NF];             // [side l/r][variable][face] 5th-order reconstructed characteristics
   float fx[NQ + 1][TY][TX + 1];   // x-face fluxes (global field order) + face velocity
   float fy[NQ + 1][TY + 1][TX];   // y-face fluxes + face velocity
+  unsigned long long red[NT / 32];  // per-warp CFL maxima
 };
 
 struct StageArgs {
   GridDev g;
   int stage;
+  float idx, idy;     // 1/dx, 1/dy
+  float cfl;
+  double dt_fixed;    // > 0: use this step; otherwise CFL
+  unsigned long long* lmax;  // stage 0: max wave rate (FP64 bits)
+  double* dt_out;     // stage 1 (block 0): the dt used
   double* U;          // state at t^n; stage 2 replaces it with t^{n+1}
   float* U32;         // FP32 image of U^n (rho, m_x, m_y, E - Pi, Gamma, Pi): written in stage 0
   const float* Kin;   // stages 1, 2: accumulated increments
   float* Kout;        // stages 0, 1
-  const double* dtp;
   uint8_t* mask_x;    // nullable
   uint8_t* mask_y;
   WenoParams P;
@@ -83,10 +91,19 @@ __device__ __forceinline__ int map_bc(int x, int n, int lo, int hi, bool& flip) 
 
 // halo-tile coordinates of stencil cell k (0..5 = i-2..i+3) of face f, and
 // whether the face is an x face; false if the face lies outside the grid
+// x faces are numbered row by row for tile faces 0..TX-1 (warp = one row,
+// no shared-memory bank conflicts), then the TY right-most faces.
 __device__ __forceinline__ bool face_geom(int f, int x0, int y0, int nx, int ny, bool& isx, int& hx, int& hy,
                                           int& dhx, int& dhy) {
   if (f < NFX) {
-    int j = f / (TX + 1), i = f - j * (TX + 1);
+    int j, i;
+    if (f < TX * TY) {
+      j = f / TX;
+      i = f - j * TX;
+    } else {
+      j = f - TX * TY;
+      i = TX;
+    }
     isx = true;
     hx = i;  // cell k at hx + k
     hy = j + NG;
@@ -168,7 +185,14 @@ __global__ void __launch_bounds__(NT, 2) k_stage2d(StageArgs a) {
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
   const int64_t N = g.N, P0 = g.P[0];
   const int tid = threadIdx.x;
-  const float coef = a.stage == 0 ? 0.0f : (a.stage == 1 ? 1.0f : 0.25f);
+  float dt = 0.0f;
+  if (a.stage > 0) {
+    double d = a.dt_fixed > 0.0 ? a.dt_fixed : a.cfl / __longlong_as_double((long long)*a.lmax);
+    if (a.stage == 1 && blockIdx.x == 0 && blockIdx.y == 0 && tid == 0) *a.dt_out = d;
+    dt = f64_to_f32(d);
+  }
+  const float coef = a.stage == 0 ? 0.0f : (a.stage == 1 ? dt : 0.25f * dt);
+  float lam_max = 0.0f;
 
   // ---- phase A: stage-state primitives of tile + halo ----
   for (int h = tid; h < HX * HY; h += NT) {
@@ -219,9 +243,29 @@ __global__ void __launch_bounds__(NT, 2) k_stage2d(StageArgs a) {
     S.q[3][hy][hx] = p;
     S.q[4][hy][hx] = Gam;
     S.q[5][hy][hx] = Pi;
-    S.q[6][hy][hx] = fsqrt(sound_speed2(rho, p, Gam, Pi));
+    float c = fsqrt(sound_speed2(rho, p, Gam, Pi));
+    S.q[6][hy][hx] = c;
+    if (a.stage == 0 && hx >= NG && hx < NG + TX && hy >= NG && hy < NG + TY && !outx && !outy) {
+      float lam = fmaf(fabsf(u) + c, a.idx, (fabsf(v) + c) * a.idy);
+      if (!(lam <= lam_max)) lam_max = lam;  // NaN propagates
+    }
+  }
+  if (a.stage == 0) {
+    unsigned long long b = (unsigned long long)__double_as_longlong((double)lam_max);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      unsigned long long v = __shfl_xor_sync(0xffffffffu, b, o);
+      b = v > b ? v : b;
+    }
+    if ((tid & 31) == 0) S.red[tid >> 5] = b;
   }
   __syncthreads();
+  if (a.stage == 0 && tid == 0) {
+    unsigned long long b = 0;
+#pragma unroll
+    for (int w = 0; w < NT / 32; ++w) b = S.red[w] > b ? S.red[w] : b;
+    if (b) atomicMax(a.lmax, b);
+  }
 
   // ---- phase B1: WENO-IS per (face, characteristic variable) ----
   {
@@ -325,8 +369,7 @@ __global__ void __launch_bounds__(NT, 2) k_stage2d(StageArgs a) {
   __syncthreads();
 
   // ---- phase C: flux divergence and RK stage ----
-  const float idx = (float)(1.0 / g.dx[0]), idy = (float)(1.0 / g.dx[1]);
-  const float dt = (float)a.dtp[0];
+  const float idx = a.idx, idy = a.idy;
   for (int c = tid; c < TX * TY; c += NT) {
     int j = c / TX, i = c - j * TX;
     int gx = x0 + i, gy = y0 + j;
@@ -339,7 +382,7 @@ __global__ void __launch_bounds__(NT, 2) k_stage2d(StageArgs a) {
       float L = -(S.fx[m][j][i + 1] - S.fx[m][j][i]) * idx;
       L = fmaf(-(S.fy[m][j + 1][i] - S.fy[m][j][i]), idy, L);
       if (m >= 4) L = fmaf(S.q[m][j + NG][i + NG], div_u, L);
-      inc[m] = dt * L;
+      inc[m] = L;
     }
     if (a.stage == 0) {
 #pragma unroll
@@ -352,7 +395,7 @@ __global__ void __launch_bounds__(NT, 2) k_stage2d(StageArgs a) {
       float d[NQ];
 #pragma unroll
       for (int m = 0; m < NQ; ++m) {
-        d[m] = fmaf(1.0f / 6.0f, a.Kin[m * N + gi], (2.0f / 3.0f) * inc[m]);
+        d[m] = dt * fmaf(1.0f / 6.0f, a.Kin[m * N + gi], (2.0f / 3.0f) * inc[m]);
         a.U[m * N + gi] = a.U[m * N + gi] + f32_to_f64(d[m]);  // FP64 accumulation
       }
       // admissibility of the new state (rho > 0, Gamma > 0, (Gamma+1) p + Pi > 0)
@@ -376,16 +419,22 @@ cudaError_t fused2d_prepare() {
 }
 
 void launch_stage2d(const GridDev& g, int stage, double* U, float* U32, const float* Kin, float* Kout,
-                    const double* dt_dev, uint8_t* mask_x, uint8_t* mask_y, float eps_rel, int mood, int weights,
-                    unsigned long long* nbad, cudaStream_t s) {
+                    double dt_fixed, double cfl, unsigned long long* lmax, double* dt_out, uint8_t* mask_x,
+                    uint8_t* mask_y, float eps_rel, int mood, int weights, unsigned long long* nbad,
+                    cudaStream_t s) {
   StageArgs a;
   a.g = g;
   a.stage = stage;
+  a.idx = (float)(1.0 / g.dx[0]);
+  a.idy = (float)(1.0 / g.dx[1]);
+  a.cfl = (float)cfl;
+  a.dt_fixed = dt_fixed;
+  a.lmax = lmax;
+  a.dt_out = dt_out;
   a.U = U;
   a.U32 = U32;
   a.Kin = Kin;
   a.Kout = Kout;
-  a.dtp = dt_dev;
   a.mask_x = mask_x;
   a.mask_y = mask_y;
   a.P = WenoParams{eps_rel, 1e-30f, weights};

@@ -116,8 +116,9 @@ void launch_cfl_u(const GridDev& g, const double* U, unsigned long long* lmax, c
 int fused2d_smem_bytes();
 cudaError_t fused2d_prepare();
 void launch_stage2d(const GridDev& g, int stage, double* U, float* U32, const float* Kin, float* Kout,
-                    const double* dt_dev, uint8_t* mask_x, uint8_t* mask_y, float eps_rel, int mood, int weights,
-                    unsigned long long* nbad, cudaStream_t s);
+                    double dt_fixed, double cfl, unsigned long long* lmax, double* dt_out, uint8_t* mask_x,
+                    uint8_t* mask_y, float eps_rel, int mood, int weights, unsigned long long* nbad,
+                    cudaStream_t s);
 
 // ---- batched tubes (ws_tubes.cu) ----
 void launch_tubes_ghost(const TubesDev& t, double* U, cudaStream_t s);
