@@ -213,6 +213,13 @@ WS_API int ws_peak_probe(int kind, int blocks, double *tflops);
 WS_API int ws_flux_divergence_noalloc(const ws_grid *grid, const ws_opts *opts, void *stream, double *U,
                                       double *L, char *err, int err_len);
 
+/* Applies the mixed-precision kernels' integer-pipe conversions to n DEVICE
+ * doubles: out32[i] = in[i] rounded to FP32 (nearest even; +-0 below the FP32
+ * normal range, +-inf above it, NaN kept), out64[i] = out32[i] widened back
+ * (exact; +-0 for subnormals).  A test hook: the paper has no counterpart.
+ * Runs on the legacy default stream and synchronises the device. */
+WS_API int ws_convert_probe(int64_t n, const double *in, float *out32, double *out64);
+
 /* Message of the last failing call on ctx (never NULL; "" when none). */
 WS_API const char *ws_last_error(const ws_ctx *ctx);
 

@@ -81,6 +81,7 @@ def load():
         "ws_profile": (ctypes.c_int, [vp, ctypes.c_int]),
         "ws_profile_read": (ctypes.c_int, [vp, dp, ctypes.POINTER(ctypes.c_int64)]),
         "ws_peak_probe": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, dp]),
+        "ws_convert_probe": (ctypes.c_int, [ctypes.c_int64, vp, vp, vp]),
         "ws_flux_divergence_noalloc": (ctypes.c_int, [ctypes.POINTER(ws_grid), ctypes.POINTER(ws_opts), vp, vp, vp,
                                                       ctypes.c_char_p, ctypes.c_int]),
     }
@@ -223,6 +224,18 @@ def ws_flux_divergence_noalloc(grid: ws_grid, opts: ws_opts, stream: int, U, L):
                                            _ptr(L), buf, 256)
     if rc != WS_OK:
         raise WsError(rc, buf.value.decode())
+
+
+def ws_convert_probe(x):
+    """(FP32, widened FP64) images of a float64 CUDA tensor under the mixed
+    kernels' integer-pipe conversions."""
+    import torch
+    o32 = torch.empty(x.numel(), dtype=torch.float32, device=x.device)
+    o64 = torch.empty(x.numel(), dtype=torch.float64, device=x.device)
+    rc = load().ws_convert_probe(x.numel(), _ptr(x), _ptr(o32), _ptr(o64))
+    if rc != WS_OK:
+        raise WsError(rc, "convert probe failed")
+    return o32, o64
 
 
 def ws_destroy(ctx):

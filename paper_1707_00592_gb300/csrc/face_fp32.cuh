@@ -39,9 +39,8 @@ __device__ __forceinline__ float fdiv(float a, float b) { return a * frcp(b); }
 
 // FP64 <-> FP32 conversions on the integer pipe (GB300 runs FP64-pipe
 // instructions at 1/64 of the FP32 rate).  f64_to_f32: round to nearest
-// even for values in the FP32 normal range, +-0 below it (the solver's
-// fields never exceed the FP32 range).  f32_to_f64: exact (+-0 for zero and
-// subnormal inputs).
+// even in the FP32 normal range, +-0 below it, +-inf above it, NaN kept.
+// f32_to_f64: exact (+-0 for zero and subnormal inputs; inf and NaN kept).
 __device__ __forceinline__ float f64_to_f32(double x) {
   unsigned long long b = (unsigned long long)__double_as_longlong(x);
   unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
@@ -50,6 +49,8 @@ __device__ __forceinline__ float f64_to_f32(double x) {
   unsigned rb = (lo >> 28) & 1u, sticky = lo & 0x0fffffffu;
   f += rb & ((sticky != 0u) | (f & 1u));
   f = mag < (897u << 20) ? 0u : f;
+  // beyond the FP32 range: +-inf; NaN stays NaN
+  f = mag >= (1151u << 20) ? (0x7f800000u | (mag > 0x7ff00000u || (mag == 0x7ff00000u && lo) ? 0x400000u : 0u)) : f;
   return __uint_as_float(sign | f);
 }
 __device__ __forceinline__ double f32_to_f64(float v) {
@@ -59,6 +60,9 @@ __device__ __forceinline__ double f32_to_f64(float v) {
   unsigned lo = f << 29;
   hi = mag < 0x00800000u ? (f & 0x80000000u) : hi;
   lo = mag < 0x00800000u ? 0u : lo;
+  // +-inf and NaN keep their class
+  hi = mag >= 0x7f800000u ? ((f & 0x80000000u) | 0x7ff00000u | (mag > 0x7f800000u ? 0x80000u : 0u)) : hi;
+  lo = mag >= 0x7f800000u ? 0u : lo;
   return __longlong_as_double((long long)(((unsigned long long)hi << 32) | lo));
 }
 

@@ -51,6 +51,7 @@ struct Smem {
   float fx[NQ + 1][TY][TX + 1];   // x-face fluxes (global field order) + face velocity
   float fy[NQ + 1][TY + 1][TX];   // y-face fluxes + face velocity
   unsigned long long red[NT / 32];  // per-warp CFL maxima
+  float dt;                         // the step, broadcast from thread 0
 };
 
 struct StageArgs {
@@ -185,12 +186,15 @@ __global__ void __launch_bounds__(NT, 2) k_stage2d(StageArgs a) {
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
   const int64_t N = g.N, P0 = g.P[0];
   const int tid = threadIdx.x;
-  float dt = 0.0f;
   if (a.stage > 0) {
-    double d = a.dt_fixed > 0.0 ? a.dt_fixed : a.cfl / __longlong_as_double((long long)*a.lmax);
-    if (a.stage == 1 && blockIdx.x == 0 && blockIdx.y == 0 && tid == 0) *a.dt_out = d;
-    dt = f64_to_f32(d);
+    if (tid == 0) {  // one FP64 division per CTA
+      double d = a.dt_fixed > 0.0 ? a.dt_fixed : (double)a.cfl / __longlong_as_double((long long)*a.lmax);
+      if (a.stage == 1 && blockIdx.x == 0 && blockIdx.y == 0) *a.dt_out = d;
+      S.dt = f64_to_f32(d);
+    }
+    __syncthreads();
   }
+  const float dt = a.stage > 0 ? S.dt : 0.0f;
   const float coef = a.stage == 0 ? 0.0f : (a.stage == 1 ? dt : 0.25f * dt);
   float lam_max = 0.0f;
 
@@ -251,7 +255,7 @@ __global__ void __launch_bounds__(NT, 2) k_stage2d(StageArgs a) {
     }
   }
   if (a.stage == 0) {
-    unsigned long long b = (unsigned long long)__double_as_longlong((double)lam_max);
+    unsigned long long b = (unsigned long long)__double_as_longlong(f32_to_f64(lam_max));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       unsigned long long v = __shfl_xor_sync(0xffffffffu, b, o);

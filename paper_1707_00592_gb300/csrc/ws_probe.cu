@@ -60,3 +60,28 @@ extern "C" WS_API int ws_peak_probe(int kind, int blocks, double* tflops) {
   if (!tflops || (kind != 0 && kind != 1)) return WS_EINVAL;
   return kind == 0 ? probe<double>(blocks, tflops) : probe<float>(blocks, tflops);
 }
+
+// ---- conversion probe: the integer-pipe FP64 <-> FP32 conversions of the
+// mixed-precision kernels, exposed so that tests can compare them with the
+// hardware conversions ----
+#include "face_fp32.cuh"
+
+namespace {
+__global__ void k_convert(int64_t n, const double* __restrict__ in, float* __restrict__ o32,
+                          double* __restrict__ o64) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    float f = ws::fp32::f64_to_f32(in[i]);
+    o32[i] = f;
+    o64[i] = ws::fp32::f32_to_f64(f);
+  }
+}
+}  // namespace
+
+extern "C" WS_API int ws_convert_probe(int64_t n, const double* in, float* out32, double* out64) {
+  if (n < 0 || (n > 0 && (!in || !out32 || !out64))) return WS_EINVAL;
+  if (n == 0) return WS_OK;
+  int64_t b = (n + 255) / 256;
+  if (b > 65535) b = 65535;
+  k_convert<<<(int)b, 256>>>(n, in, out32, out64);
+  return cudaDeviceSynchronize() == cudaSuccess ? WS_OK : WS_ECUDA;
+}

@@ -146,3 +146,27 @@ def test_fused_stage_matches_generic(n, bc, monkeypatch):
         a, b = outs[0][0][sl][f], outs[1][0][sl][f]
         assert np.abs(a - b).max() <= 1e-5 * np.abs(b).max() + 1e-300, f
     assert np.mean(outs[0][1] == outs[1][1]) > 0.99
+
+
+def test_integer_pipe_conversions_match_hardware():
+    """The mixed kernels convert FP64 <-> FP32 on the integer pipe; on normal
+    FP32-range values (including exact rounding ties) the result must equal
+    the hardware round-to-nearest-even cast bit for bit, and widening back
+    must be exact; zero, inf and NaN keep their class."""
+    rng = np.random.default_rng(0)
+    mant = rng.uniform(1.0, 2.0, size=20000)
+    expo = rng.integers(-125, 127, size=20000)
+    x = mant * np.exp2(expo) * rng.choice([-1.0, 1.0], size=20000)
+    f = rng.uniform(1, 2, size=2000).astype(np.float32).astype(np.float64) * np.exp2(rng.integers(-100, 100, 2000))
+    ulp = np.spacing(f.astype(np.float32)).astype(np.float64)
+    ties = f + 0.5 * ulp  # exactly half-way between two floats
+    x = np.concatenate([x, ties, f, [0.0, -0.0, 1.0, -1.0, 3.4e38, 1.2e-38]])
+    o32, o64 = ws.ws_convert_probe(torch.tensor(x, device="cuda"))
+    ref = x.astype(np.float32)
+    assert np.array_equal(o32.cpu().numpy().view(np.uint32), ref.view(np.uint32))
+    assert np.array_equal(o64.cpu().numpy(), ref.astype(np.float64))
+    sp = np.array([np.inf, -np.inf, np.nan, 1e300, 1e-300])
+    s32, s64 = ws.ws_convert_probe(torch.tensor(sp, device="cuda"))
+    s32 = s32.cpu().numpy()
+    assert s32[0] == np.inf and s32[1] == -np.inf and np.isnan(s32[2]) and s32[3] == np.inf and s32[4] == 0.0
+    assert np.isnan(s64.cpu().numpy()[2])
