@@ -183,6 +183,28 @@ def l1_vs_fp64(ws, case, s_mixed, stream, steps):
             "reference": "FP64 path (bit-identical to the FP64 oracle)"}
 
 
+def time_fp64(ws, case, stream, steps):
+    """cell-updates/s of the plain FP64 path (bit-identical to the oracle) on the
+    same workload, timed the same way (L2 flushed between steps)."""
+    import torch
+    s64 = ws.Solver(2, case.n, case.dx, case.bc, precision="fp64", stream=stream)
+    U = s64.prim_to_cons(s64.tensor(case.Q))
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    for _ in range(2):
+        s64.step(U)
+    ms = 0.0
+    for _ in range(steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        s64.step(U)
+        b.record(stream)
+        b.synchronize()
+        ms += a.elapsed_time(b)
+    s64.close()
+    return {"value": case.cells * steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps, "steps": steps}
+
+
 def run_ours(args):
     import torch
     import paper_1707_00592_gb300 as ws
@@ -243,8 +265,11 @@ def run_ours(args):
         state_bytes = s.size * 8
 
         l1 = None
+        fp64_cmp = None
         if args.precision == "mixed" and args.l1_steps > 0:
             l1 = l1_vs_fp64(ws, case, s, stream, args.l1_steps)
+        if args.precision == "mixed" and args.fp64_steps > 0:
+            fp64_cmp = time_fp64(ws, case, stream, args.fp64_steps)
 
     clocks = clk.summary()
     if rank != 0:
@@ -254,7 +279,9 @@ def run_ours(args):
     peaks, which = load_peaks()
     face_ms, face_n = prof["face"]
     per_launch_s = face_ms * 1e-3 / max(face_n, 1)
-    faces_per_launch = (n + 1) * n  # one direction of the 2D grid
+    # the FP64 path launches one face sweep per direction; the mixed path one
+    # fused stage kernel covering both directions' faces
+    faces_per_launch = (n + 1) * n * (1 if args.precision == "fp64" else 2)
     flops = face_flops(2) * faces_per_launch
     achieved = flops / per_launch_s / 1e12
     if args.precision == "fp64":
@@ -262,7 +289,8 @@ def run_ours(args):
         kname, psrc = "face sweep (FP64)", "FP64 FMA chain probe on this GPU (2 flops per DFMA)"
     else:
         peak = args.fp32_peak if args.fp32_peak is not None else ws.ws_peak_probe("fp32")
-        kname, psrc = "face sweep (FP32 mixed)", "FP32 FMA chain probe on this GPU (2 flops per FFMA)"
+        kname, psrc = ("fused RK stage (FP32 mixed: tile load, x and y faces, update)",
+                       "FP32 FMA chain probe on this GPU (2 flops per FFMA)")
     roofline = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
                 "peak_source": psrc,
@@ -288,6 +316,8 @@ def run_ours(args):
         line["clocks"] = clocks
     if l1 is not None:
         line["l1_density_vs_fp64"] = l1
+    if fp64_cmp is not None:
+        line["fp64_plain"] = fp64_cmp
     if ws_size == 1 and not args.no_cpu_baseline:
         cells_c, times, cores = cpu_oracle_rate(n, args.cpu_rows, args.cpu_steps)
         line["cpu_baseline"] = {"kind": "oracle", "value": cells_c * len(times) / sum(times), "unit": UNIT,
@@ -305,7 +335,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
     ap.add_argument("--n", type=int, default=1024)
     ap.add_argument("--cpu-rows", type=int, default=128)
     ap.add_argument("--cpu-steps", type=int, default=3)
@@ -313,7 +343,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-peak", type=float, default=None)
     ap.add_argument("--fp32-peak", type=float, default=None)
-    ap.add_argument("--l1-steps", type=int, default=0)
+    ap.add_argument("--l1-steps", type=int, default=200)
+    ap.add_argument("--fp64-steps", type=int, default=5)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -158,6 +158,15 @@ WS_API int ws_get_mood(ws_ctx *ctx, uint8_t *mask, int64_t counts[9]);
  * ws_step (HOST out).  Synchronises. */
 WS_API int ws_nonphysical(ws_ctx *ctx, int64_t *count);
 
+/* enable != 0: ws_step calls that take the CFL step (dt <= 0) replay one CUDA
+ * graph holding the whole step (CFL reduction and the three RK stages)
+ * instead of launching its kernels one by one; the graph is captured on the
+ * first such call for a given state pointer U (and again when U changes).
+ * Needs a stream other than the legacy default stream; ignored while
+ * ws_profile recording is on.  Results are identical either way.
+ * 0: launch kernels directly (the default). */
+WS_API int ws_set_graph(ws_ctx *ctx, int enable);
+
 /* ---- measurement helpers (not part of the method) ---- */
 
 /* kernel classes for ws_profile_read */

@@ -79,6 +79,7 @@ def load():
         "ws_init_error": (ctypes.c_char_p, []),
         "ws_destroy": (None, [vp]),
         "ws_profile": (ctypes.c_int, [vp, ctypes.c_int]),
+        "ws_set_graph": (ctypes.c_int, [vp, ctypes.c_int]),
         "ws_profile_read": (ctypes.c_int, [vp, dp, ctypes.POINTER(ctypes.c_int64)]),
         "ws_peak_probe": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, dp]),
         "ws_convert_probe": (ctypes.c_int, [ctypes.c_int64, vp, vp, vp]),
@@ -192,6 +193,10 @@ def ws_nonphysical(ctx) -> int:
 
 KERNEL_CLASSES = ["ghost", "prim", "cfl", "face", "update", "other"]
 NKERNEL = 8
+
+
+def ws_set_graph(ctx, enable: bool):
+    _check(ctx, load().ws_set_graph(ctx, int(bool(enable))))
 
 
 def ws_profile(ctx, enable: bool):

@@ -98,6 +98,8 @@ void free_all(ws_ctx* c) {
   cudaFree(c->mask_off_dev);
   for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
   c->ev.clear();
+  if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+  c->graph_exec = nullptr;
 }
 
 bool tubes(const ws_ctx* c) { return c->grid.ntubes > 0; }
@@ -444,9 +446,39 @@ int ws_cfl_dt(ws_ctx* c, double* U, double* dt) {
   return WS_OK;
 }
 
+// one CFL step replayed from a CUDA graph (captured on first use per U)
+int step_graph(ws_ctx* c, double* U) {
+  if (!c->graph_exec || c->graph_U != U) {
+    if (c->graph_exec) {
+      CK(c, cudaGraphExecDestroy(c->graph_exec));
+      c->graph_exec = nullptr;
+    }
+    CK(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    int rc = step_device(c, U, 0.0);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
+    if (rc) {
+      if (graph) cudaGraphDestroy(graph);
+      return rc;
+    }
+    if (e != cudaSuccess) return fail(c, WS_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&c->graph_exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      c->graph_exec = nullptr;
+      return fail(c, WS_ECUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
+    }
+    c->graph_U = U;
+  }
+  CK(c, cudaGraphLaunch(c->graph_exec, c->stream));
+  c->last_stages = 3;
+  return WS_OK;
+}
+
 int ws_step(ws_ctx* c, double* U, double dt, double* dt_used) {
   if (!c || !U) return fail(c, WS_EINVAL, "bad pointers");
-  int rc = step_device(c, U, dt);
+  bool graph = c->graph_on && dt <= 0.0 && c->stream != nullptr && !c->prof_on;
+  int rc = graph ? step_graph(c, U) : step_device(c, U, dt);
   if (rc) return rc;
   if (dt_used) {
     int64_t n = tubes(c) ? c->td.ntubes : 1;
@@ -505,6 +537,12 @@ int ws_nonphysical(ws_ctx* c, int64_t* count) {
   CK(c, cudaMemcpyAsync(&nb, c->nbad, sizeof nb, cudaMemcpyDeviceToHost, c->stream));
   CK(c, cudaStreamSynchronize(c->stream));
   *count = (int64_t)nb;
+  return WS_OK;
+}
+
+int ws_set_graph(ws_ctx* c, int enable) {
+  if (!c) return fail(c, WS_EINVAL, "null context");
+  c->graph_on = enable != 0;
   return WS_OK;
 }
 

@@ -75,6 +75,10 @@ struct ws_ctx {
   std::vector<int> ev_cls;
   size_t ev_used = 0;
   int64_t nlaunch[WS_NKERNEL] = {0};
+  // CUDA graph of one CFL step (ws_set_graph)
+  bool graph_on = false;
+  cudaGraphExec_t graph_exec = nullptr;
+  const double* graph_U = nullptr;
   // ws_get_mood scratch
   unsigned long long* mood_counts = nullptr;
   int64_t* mask_off_dev = nullptr;

@@ -170,3 +170,30 @@ def test_integer_pipe_conversions_match_hardware():
     s32 = s32.cpu().numpy()
     assert s32[0] == np.inf and s32[1] == -np.inf and np.isnan(s32[2]) and s32[3] == np.inf and s32[4] == 0.0
     assert np.isnan(s64.cpu().numpy()[2])
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_graph_replay_identical(precision):
+    """A CFL step replayed from the captured CUDA graph gives the same bits as
+    the directly launched step, over several steps and a change of state buffer."""
+    case = wl.random_state(2, (45, 38), seed=3, kind="two_phase")
+    stream = torch.cuda.Stream()
+    outs = []
+    for graph in (False, True):
+        s = ws.Solver(2, case.n, case.dx, case.bc, precision=precision, stream=stream)
+        ws.ws_set_graph(s.ctx, graph)
+        Uo = oracle.prim_to_cons(2, case.Q)
+        with torch.cuda.stream(stream):
+            U = s.tensor(Uo)
+            V = s.tensor(Uo)
+            for _ in range(4):
+                s.step(U)
+            for _ in range(2):
+                s.step(V)
+            dt = s.step(U, want_dt=True)
+        stream.synchronize()
+        outs.append((U.cpu().numpy(), V.cpu().numpy(), dt))
+        s.close()
+    assert np.array_equal(outs[0][0], outs[1][0])
+    assert np.array_equal(outs[0][1], outs[1][1])
+    assert outs[0][2] == outs[1][2]
