@@ -158,6 +158,73 @@ WS_API int ws_get_mood(ws_ctx *ctx, uint8_t *mask, int64_t counts[9]);
  * ws_step (HOST out).  Synchronises. */
 WS_API int ws_nonphysical(ws_ctx *ctx, int64_t *count);
 
+/* ---- learned smooth-face gate (not in the paper) ----
+ * A 24 -> 32 -> 32 -> 1 MLP (ReLU, ReLU, sigmoid) marks faces whose WENO-IS
+ * value would equal the 5th-order linear-weight value (d = (4,2,3,1)/10 of
+ * Sec. 3.3.1) to 1e-6 of the stencil's range; those faces skip the
+ * smoothness indicators and nonlinear weights.  Inputs of face i+1/2: the
+ * characteristic variables w1, w2, w6 and w_Gamma (Sec. 3.2, Eq.
+ * eigen-vectors) of cells i-2..i+3, each normalised over the stencil as
+ * (w - mean)/(max - min + 1e-30), ordered [variable][cell].
+ * Parameters: WS_MLP_NPARAM FP32 values W1[32][24], b1[32], W2[32][32],
+ * b2[32], W3[32], b3 (DEVICE arrays in the calls below). */
+#define WS_MLP_NPARAM 1889
+#define WS_MLP_NIN 24
+
+/* Training samples from state U (mixed-precision context, grid mode): every
+ * stride-th face of each direction (directions one after another), at most
+ * max_out.  feats (DEVICE, max_out x 24 FP32) and labels (DEVICE, max_out
+ * bytes: 1 = the face needs WENO-IS -- MOOD lowers a side, or WENO-IS and the
+ * linear weights differ by more than 1e-6 of the range for some variable and
+ * side; 0 = smooth).  *count (HOST) receives the number written.  U's ghosts
+ * are filled first.  Synchronises. */
+WS_API int ws_face_samples(ws_ctx *ctx, double *U, int64_t stride, int64_t max_out, float *feats,
+                           uint8_t *labels, int64_t *count);
+
+/* logits[i] (DEVICE, n FP32) of samples X (DEVICE, n x 24 FP32) under params
+ * (FP32 forward pass).  Enqueued on `stream`. */
+WS_API int ws_mlp_forward(const float *params, const float *X, int64_t n, float *logits, void *stream);
+
+/* Gradient (DEVICE, WS_MLP_NPARAM FP32, overwritten) and *loss (DEVICE FP32,
+ * overwritten) of the mean binary cross-entropy over n samples, positives
+ * weighted by pos_weight.  Enqueued on `stream`. */
+WS_API int ws_mlp_grad(const float *params, const float *X, const uint8_t *y, int64_t n, float pos_weight,
+                       float *grad, float *loss, void *stream);
+
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) of params with moment
+ * buffers m, v (DEVICE, WS_MLP_NPARAM FP32 each, zero before step 1); step
+ * counts from 1.  Enqueued on `stream`. */
+WS_API int ws_mlp_adam(float *params, float *m, float *v, const float *grad, int64_t step, float lr, void *stream);
+
+/* Switch the learned gate on for the fused 2D mixed-precision path
+ * (WS_ENOTSUP elsewhere).  params: DEVICE, WS_MLP_NPARAM FP32 values (copied
+ * and converted to BF16 tensor-core fragments); NULL switches the gate off.
+ * A face whose logit is below `threshold` takes the linear weights; every
+ * face still goes through the MOOD cascade (a gated side that fails falls
+ * back to 3rd-order WENO-IS, then 1st order).  Each gated ws_step keeps a
+ * copy of U and, on the device (no host round trip), redoes the step
+ * without the gate if (flags & WS_GATE_REDO_NONPHYS) a cell ends
+ * inadmissible, if (flags & WS_GATE_REDO_DRIFT) on the 1/64 of the tiles
+ * checked that step (rotating) the linear-weight face values differ from
+ * WENO-IS by more than 1e-6 in relative L1, or if (flags &
+ * WS_GATE_REDO_MOOD) any gated face needed the MOOD cascade.  Resets the
+ * statistics of ws_gate_stats. */
+#define WS_GATE_REDO_MOOD 1
+#define WS_GATE_REDO_DRIFT 2
+#define WS_GATE_REDO_NONPHYS 4
+WS_API int ws_set_mlp(ws_ctx *ctx, const float *params, float threshold, int flags);
+
+/* The gate's decisions on state U (DEVICE): smooth (DEVICE, ws_mask_size()
+ * bytes, laid out like one stage of the MOOD mask) receives 1 for faces that
+ * would take the linear weights, 0 otherwise.  Enqueued on the context's
+ * stream. */
+WS_API int ws_gate_eval(ws_ctx *ctx, double *U, uint8_t *smooth);
+
+/* Gate statistics since ws_set_mlp (HOST out[5]): gated steps, steps redone
+ * without the gate, smooth-gated faces, faces examined (both summed over RK
+ * stages), largest drift ratio seen.  Synchronises. */
+WS_API int ws_gate_stats(ws_ctx *ctx, double out[5]);
+
 /* enable != 0: ws_step calls that take the CFL step (dt <= 0) replay one CUDA
  * graph holding the whole step (CFL reduction and the three RK stages)
  * instead of launching its kernels one by one; the graph is captured on the

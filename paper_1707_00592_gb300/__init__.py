@@ -80,6 +80,14 @@ def load():
         "ws_destroy": (None, [vp]),
         "ws_profile": (ctypes.c_int, [vp, ctypes.c_int]),
         "ws_set_graph": (ctypes.c_int, [vp, ctypes.c_int]),
+        "ws_set_mlp": (ctypes.c_int, [vp, vp, ctypes.c_float, ctypes.c_int]),
+        "ws_gate_eval": (ctypes.c_int, [vp, vp, vp]),
+        "ws_gate_stats": (ctypes.c_int, [vp, dp]),
+        "ws_face_samples": (ctypes.c_int, [vp, vp, ctypes.c_int64, ctypes.c_int64, vp, vp,
+                                           ctypes.POINTER(ctypes.c_int64)]),
+        "ws_mlp_forward": (ctypes.c_int, [vp, vp, ctypes.c_int64, vp, vp]),
+        "ws_mlp_grad": (ctypes.c_int, [vp, vp, vp, ctypes.c_int64, ctypes.c_float, vp, vp, vp]),
+        "ws_mlp_adam": (ctypes.c_int, [vp, vp, vp, vp, ctypes.c_int64, ctypes.c_float, vp]),
         "ws_profile_read": (ctypes.c_int, [vp, dp, ctypes.POINTER(ctypes.c_int64)]),
         "ws_peak_probe": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, dp]),
         "ws_convert_probe": (ctypes.c_int, [ctypes.c_int64, vp, vp, vp]),
@@ -193,6 +201,59 @@ def ws_nonphysical(ctx) -> int:
 
 KERNEL_CLASSES = ["ghost", "prim", "cfl", "face", "update", "other"]
 NKERNEL = 8
+
+
+MLP_NPARAM = 1889
+MLP_NIN = 24
+
+
+def ws_face_samples(ctx, U, stride: int, max_out: int, feats, labels) -> int:
+    n = ctypes.c_int64(0)
+    _check(ctx, load().ws_face_samples(ctx, _ptr(U), int(stride), int(max_out), _ptr(feats), _ptr(labels),
+                                       ctypes.byref(n)))
+    return n.value
+
+
+def _stream_ptr(stream):
+    return ctypes.c_void_p(stream.cuda_stream if stream is not None else 0)
+
+
+def ws_mlp_forward(params, X, logits, stream=None):
+    rc = load().ws_mlp_forward(_ptr(params), _ptr(X), X.shape[0], _ptr(logits), _stream_ptr(stream))
+    if rc != WS_OK:
+        raise WsError(rc, "ws_mlp_forward failed")
+
+
+def ws_mlp_grad(params, X, y, pos_weight, grad, loss, stream=None):
+    rc = load().ws_mlp_grad(_ptr(params), _ptr(X), _ptr(y), X.shape[0], ctypes.c_float(pos_weight), _ptr(grad),
+                            _ptr(loss), _stream_ptr(stream))
+    if rc != WS_OK:
+        raise WsError(rc, "ws_mlp_grad failed")
+
+
+def ws_mlp_adam(params, m, v, grad, step, lr, stream=None):
+    rc = load().ws_mlp_adam(_ptr(params), _ptr(m), _ptr(v), _ptr(grad), int(step), ctypes.c_float(lr),
+                            _stream_ptr(stream))
+    if rc != WS_OK:
+        raise WsError(rc, "ws_mlp_adam failed")
+
+
+GATE_REDO_MOOD, GATE_REDO_DRIFT, GATE_REDO_NONPHYS = 1, 2, 4
+
+
+def ws_set_mlp(ctx, params, threshold: float, flags: int = GATE_REDO_DRIFT | GATE_REDO_NONPHYS):
+    _check(ctx, load().ws_set_mlp(ctx, _ptr(params), ctypes.c_float(threshold), int(flags)))
+
+
+def ws_gate_eval(ctx, U, smooth):
+    _check(ctx, load().ws_gate_eval(ctx, _ptr(U), _ptr(smooth)))
+
+
+def ws_gate_stats(ctx) -> dict:
+    out = (ctypes.c_double * 5)()
+    _check(ctx, load().ws_gate_stats(ctx, out))
+    return {"steps": int(out[0]), "redone": int(out[1]), "smooth_faces": out[2], "faces": out[3],
+            "max_drift": out[4]}
 
 
 def ws_set_graph(ctx, enable: bool):

@@ -27,6 +27,7 @@ UNITS = {
     "ws_probe.cu": [],
     "ws_mixed.cu": [],
     "ws_fused2d.cu": [],
+    "ws_learned.cu": [],
     "ws_noalloc.cu": ["-fmad=false"],
 }
 

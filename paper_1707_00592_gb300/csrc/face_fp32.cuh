@@ -158,6 +158,16 @@ __device__ __forceinline__ void weno_is_both(float qm2, float qm1, float q0, flo
   v5 = fmaf(num5, frcp(den5), q0);
 }
 
+// 5th-order reconstruction with the linear weights d = (4,2,3,1)/10, i.e.
+// (2 q_{i-2} - 13 q_{i-1} + 47 q_i + 27 q_{i+1} - 3 q_{i+2})/60, in increment
+// form about q_i (a constant stencil reconstructs exactly)
+__device__ __forceinline__ float linear5(float qm2, float qm1, float q0, float qp1, float qp2) {
+  float t = fmaf(2.0f, qm2 - q0, -13.0f * (qm1 - q0));
+  t = fmaf(27.0f, qp1 - q0, t);
+  t = fmaf(-3.0f, qp2 - q0, t);
+  return fmaf(t, 1.0f / 60.0f, q0);
+}
+
 __device__ __forceinline__ float sound_speed2(float rho, float p, float Gam, float Pi) {
   return fdiv(fmaf(Gam + 1.0f, p, Pi), Gam * rho);
 }

@@ -100,6 +100,11 @@ void free_all(ws_ctx* c) {
   c->ev.clear();
   if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
   c->graph_exec = nullptr;
+  cudaFree(c->mlp_frag);
+  cudaFree(c->mlp_bias);
+  cudaFree(c->lstat);
+  cudaFree(c->gate_redo);
+  cudaFree(c->gate_stats);
 }
 
 bool tubes(const ws_ctx* c) { return c->grid.ntubes > 0; }
@@ -191,17 +196,37 @@ int step_device(ws_ctx* c, double* U, double dt) {
   }
   if (c->fused) {
     // the CFL reduction happens inside stage 0, dt is derived in stage 1
-    CK(c, cudaMemsetAsync(c->lmax, 0, sizeof(unsigned long long), c->stream));
-    for (int s = 0; s < 3; ++s) {
-      uint8_t* mb = c->mask + (int64_t)s * c->nmask;
-      KScope k(c, WS_K_FACE);
-      const float* Kin = s == 1 ? c->Ka : c->Kb;
-      float* Kout = s == 0 ? c->Ka : c->Kb;
-      launch_stage2d(g, s, U, c->Q32, Kin, Kout, dt, c->opts.cfl, c->lmax, c->dt_dev, mb + c->mask_off[0],
-                     mb + c->mask_off[1], (float)c->opts.eps, c->opts.mood, c->opts.weights, c->nbad, c->stream);
+    auto run3 = [&](const GateArgs* gate, const int* run_if) -> int {
+      if (!run_if) CK(c, cudaMemsetAsync(c->lmax, 0, sizeof(unsigned long long), c->stream));
+      for (int s = 0; s < 3; ++s) {
+        uint8_t* mb = c->mask + (int64_t)s * c->nmask;
+        KScope k(c, WS_K_FACE);
+        const float* Kin = s == 1 ? c->Ka : c->Kb;
+        float* Kout = s == 0 ? c->Ka : c->Kb;
+        launch_stage2d(g, s, U, c->Q32, Kin, Kout, dt, c->opts.cfl, c->lmax, c->dt_dev, mb + c->mask_off[0],
+                       mb + c->mask_off[1], (float)c->opts.eps, c->opts.mood, c->opts.weights, c->nbad, gate,
+                       run_if, c->stream);
+      }
+      return check_launch(c, "fused stage");
+    };
+    if (!c->learned_on) {
+      if ((rc = run3(nullptr, nullptr))) return rc;
+    } else {
+      // gated step, then on the device: keep or redo it without the gate
+      // (restored from the backup taken in stage 0), with no host round trip
+      GateArgs ga{c->mlp_frag, c->mlp_bias, c->mlp_thr, (int)(c->gate_steps & 63), c->S1, c->lstat};
+      CK(c, cudaMemsetAsync(c->lstat, 0, 8 * sizeof(float), c->stream));
+      if ((rc = run3(&ga, nullptr))) return rc;
+      {
+        KScope k(c, WS_K_OTHER, 2);
+        launch_gate_decide(c->lstat, c->nbad, c->lmax, c->gate_flags, c->gate_redo, c->gate_stats, c->stream);
+        launch_restore(c->gate_redo, c->S1, U, c->nstate, c->stream);
+      }
+      if ((rc = run3(nullptr, c->gate_redo))) return rc;
+      c->gate_steps++;
     }
     c->last_stages = 3;
-    return check_launch(c, "fused stage");
+    return WS_OK;
   }
   for (int s = 0; s < 3; ++s) {
     double* Us = s == 0 ? U : c->S1;
@@ -477,7 +502,7 @@ int step_graph(ws_ctx* c, double* U) {
 
 int ws_step(ws_ctx* c, double* U, double dt, double* dt_used) {
   if (!c || !U) return fail(c, WS_EINVAL, "bad pointers");
-  bool graph = c->graph_on && dt <= 0.0 && c->stream != nullptr && !c->prof_on;
+  bool graph = c->graph_on && dt <= 0.0 && c->stream != nullptr && !c->prof_on && !c->learned_on;
   int rc = graph ? step_graph(c, U) : step_device(c, U, dt);
   if (rc) return rc;
   if (dt_used) {
@@ -537,6 +562,114 @@ int ws_nonphysical(ws_ctx* c, int64_t* count) {
   CK(c, cudaMemcpyAsync(&nb, c->nbad, sizeof nb, cudaMemcpyDeviceToHost, c->stream));
   CK(c, cudaStreamSynchronize(c->stream));
   *count = (int64_t)nb;
+  return WS_OK;
+}
+
+int ws_face_samples(ws_ctx* c, double* U, int64_t stride, int64_t max_out, float* feats, uint8_t* labels,
+                    int64_t* count) {
+  if (!c || !U || !count || stride < 1 || max_out < 0 || (max_out > 0 && (!feats || !labels)))
+    return fail(c, WS_EINVAL, "bad arguments");
+  if (tubes(c) || !mixed(c)) return fail(c, WS_ENOTSUP, "face samples need a mixed-precision grid context");
+  const GridDev& g = c->gd;
+  for (int d = 0; d < g.ndim; ++d) launch_ghost(g, U, d, c->stream);
+  launch_prim32(g, U, c->Q32, c->stream);
+  int64_t out = 0;
+  for (int d = 0; d < g.ndim && out < max_out; ++d) {
+    launch_face_samples(g, d, c->Q32, stride, out, max_out, feats, labels, (float)c->opts.eps, c->opts.weights,
+                        c->stream);
+    out += (g.nfaces[d] + stride - 1) / stride;
+  }
+  *count = out < max_out ? out : max_out;
+  int rc = check_launch(c, "face samples");
+  if (rc) return rc;
+  CK(c, cudaStreamSynchronize(c->stream));
+  return WS_OK;
+}
+
+// BF16 m16n8k16 B fragments of the gate MLP: for k-step ks and n-tile nt, lane
+// (g = lane/4, t = lane%4) holds B[16ks+2t .. +1][8nt+g] and B[16ks+2t+8 .. +9][8nt+g]
+// with B[k][n] = W[n][k]; entries outside W are zero
+static uint32_t bf16_bits(float v) {
+  uint32_t u;
+  memcpy(&u, &v, 4);
+  if ((u & 0x7fffffffu) > 0x7f800000u) return 0x7fc0u;
+  u += 0x7fffu + ((u >> 16) & 1u);  // round to nearest even
+  return u >> 16;
+}
+
+static void build_frags(const float* W, int nout, int nin, int ksteps, int ntiles, uint32_t* out /* [ks][nt][32][2] */) {
+  for (int ks = 0; ks < ksteps; ++ks)
+    for (int nt = 0; nt < ntiles; ++nt)
+      for (int lane = 0; lane < 32; ++lane) {
+        int g = lane >> 2, t = lane & 3, n = nt * 8 + g;
+        auto B = [&](int k) -> float { return (n < nout && k < nin) ? W[n * nin + k] : 0.0f; };
+        int k0 = ks * 16 + 2 * t;
+        uint32_t lo = bf16_bits(B(k0)) | (bf16_bits(B(k0 + 1)) << 16);
+        uint32_t hi = bf16_bits(B(k0 + 8)) | (bf16_bits(B(k0 + 9)) << 16);
+        uint32_t* o = out + (((size_t)(ks * ntiles + nt) * 32 + lane) * 2);
+        o[0] = lo;
+        o[1] = hi;
+      }
+}
+
+int ws_set_mlp(ws_ctx* c, const float* params, float threshold, int flags) {
+  if (!c) return fail(c, WS_EINVAL, "null context");
+  if (!params) {
+    c->learned_on = false;
+    return WS_OK;
+  }
+  if (!c->fused) return fail(c, WS_ENOTSUP, "the learned gate runs in the fused 2D mixed-precision path only");
+  std::vector<float> P(WS_MLP_NPARAM);
+  CK(c, cudaMemcpy(P.data(), params, sizeof(float) * WS_MLP_NPARAM, cudaMemcpyDeviceToHost));
+  const float* W1 = P.data();
+  const float* b1 = W1 + 32 * 24;
+  const float* W2 = b1 + 32;
+  const float* b2 = W2 + 32 * 32;
+  const float* W3 = b2 + 32;
+  const float* b3 = W3 + 32;
+  std::vector<uint32_t> F(18 * 32 * 2);
+  build_frags(W1, 32, 24, 2, 4, F.data());
+  build_frags(W2, 32, 32, 2, 4, F.data() + 8 * 64);
+  build_frags(W3, 1, 32, 2, 1, F.data() + 16 * 64);
+  std::vector<float> B(65);
+  for (int i = 0; i < 32; ++i) {
+    B[i] = b1[i];
+    B[32 + i] = b2[i];
+  }
+  B[64] = b3[0];
+  int rc;
+  if (!c->mlp_frag) {
+    if ((rc = dalloc(c, &c->mlp_frag, 18 * 32)) || (rc = dalloc(c, &c->mlp_bias, 65)) ||
+        (rc = dalloc(c, &c->lstat, 8)) || (rc = dalloc(c, &c->gate_redo, 1)) || (rc = dalloc(c, &c->gate_stats, 5)))
+      return rc;
+  }
+  CK(c, cudaMemset(c->gate_stats, 0, 5 * sizeof(double)));
+  CK(c, cudaMemcpy(c->mlp_frag, F.data(), F.size() * 4, cudaMemcpyHostToDevice));
+  CK(c, cudaMemcpy(c->mlp_bias, B.data(), 65 * sizeof(float), cudaMemcpyHostToDevice));
+  c->mlp_thr = threshold;
+  c->gate_flags = flags;
+  c->learned_on = true;
+  c->gate_steps = 0;
+  return WS_OK;
+}
+
+int ws_gate_eval(ws_ctx* c, double* U, uint8_t* smooth) {
+  if (!c || !U || !smooth) return fail(c, WS_EINVAL, "bad pointers");
+  if (!c->learned_on) return fail(c, WS_EINVAL, "no gate set (ws_set_mlp)");
+  GateArgs ga{c->mlp_frag, c->mlp_bias, c->mlp_thr, -1, c->S1, c->lstat};
+  CK(c, cudaMemsetAsync(smooth, 0, (size_t)c->nmask, c->stream));
+  launch_stage2d(c->gd, 3, U, c->Q32, c->Ka, c->Kb, 0.0, c->opts.cfl, c->lmax, c->dt_dev, smooth,
+                 smooth + c->mask_off[1], (float)c->opts.eps, c->opts.mood, c->opts.weights, c->nbad, &ga, nullptr,
+                 c->stream);
+  return check_launch(c, "gate eval");
+}
+
+int ws_gate_stats(ws_ctx* c, double out[5]) {
+  if (!c || !out) return fail(c, WS_EINVAL, "bad pointers");
+  for (int i = 0; i < 5; ++i) out[i] = 0.0;
+  if (!c->gate_stats) return WS_OK;
+  CK(c, cudaMemcpyAsync(out, c->gate_stats, 5 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
   return WS_OK;
 }
 

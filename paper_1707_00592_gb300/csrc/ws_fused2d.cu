@@ -30,6 +30,8 @@
 // separate buffers because neighbouring tiles read K in their halos.
 #include <cuda_runtime.h>
 
+#include <cuda_bf16.h>
+
 #include "face_fp32.cuh"
 #include "ws_internal.h"
 
@@ -45,13 +47,28 @@ constexpr int NQ = 6;  // rho, u, v, p, Gamma, Pi
 constexpr int NFX = (TX + 1) * TY, NFY = TX * (TY + 1), NF = NFX + NFY;
 constexpr int NT = 512;
 
+// learned gate: BF16 MMA fragments of the MLP weights (m16n8k16, 32 lanes)
+constexpr int NFRAG1 = 2 * 4, NFRAG2 = 2 * 4, NFRAG3 = 2;  // (k-step, n-tile) pairs per layer
+constexpr int NFRAG = NFRAG1 + NFRAG2 + NFRAG3;
+constexpr int NMT = (NF + 15) / 16;  // 16-face M tiles
+
 struct Smem {
   float q[NQ + 1][HY][HX];        // primitives + sound speed of tile and halo
-  float w[2][NQ][NF];             // [side l/r][variable][face] 5th-order reconstructed characteristics
+  union {
+    float w[2][NQ][NF];           // [side l/r][variable][face] 5th-order reconstructed characteristics
+    __nv_bfloat16 feat[NF][24];   // learned gate inputs (before the reconstruction)
+  };
   float fx[NQ + 1][TY][TX + 1];   // x-face fluxes (global field order) + face velocity
   float fy[NQ + 1][TY + 1][TX];   // y-face fluxes + face velocity
   unsigned long long red[NT / 32];  // per-warp CFL maxima
   float dt;                         // the step, broadcast from thread 0
+};
+
+struct SmemGate {
+  uint2 frag[NFRAG][32];            // weight fragments
+  float b1[32], b2[32], b3;         // biases
+  uint8_t smooth[NF];               // 1: the face takes the linear weights
+  float red[4][NT / 32];             // per-warp sums: |linear - WENO-IS|, |WENO-IS|, smooth faces, faces
 };
 
 struct StageArgs {
@@ -71,6 +88,15 @@ struct StageArgs {
   WenoParams P;
   int mood;
   unsigned long long* nbad;
+  // learned gate
+  const uint2* mlp_frag;   // NFRAG x 32 fragments, then biases (as floats) -- see ws_set_mlp
+  const float* mlp_bias;   // b1[32], b2[32], b3
+  float thr;               // logit threshold: smooth when logit < thr
+  int drift_tile;          // tiles with (tile id % 64) == drift_tile run the drift check
+  double* Ubackup;         // stage 0: copy of U (for a plain redo)
+  float* lstat;            // [0] gated faces failing MOOD, [1] drift |lin - full|, [2] drift |full|,
+                           // [3] smooth-gated faces, [4] gated faces examined
+  const int* run_if;       // nullable: the CTA returns at once when *run_if == 0
 };
 
 // interior index along an axis of n cells for a (possibly out-of-range)
@@ -178,15 +204,79 @@ __device__ __noinline__ void weno_side3(const float* qb, int side, const WenoPar
 // the (at most FPT) faces a thread owns in phase B1
 constexpr int FPT = (NF + NT - 1) / NT;
 
+__device__ __forceinline__ void mma16816(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                         uint2 b) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b.x), "r"(b.y));
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<uint32_t*>(&v);
+}
+
+// gate inputs of one face: w1, w2, w6, w_Gamma of the six stencil cells, each
+// normalised over the stencil (zero for a stencil flat to 1e-6)
+template <int D>
+__device__ __forceinline__ void gate_features(const float* qb, __nv_bfloat16* out) {
+  constexpr int ST = D == 0 ? 1 : HX;
+  constexpr int FS = HY * HX;
+  constexpr int UN = D == 0 ? 1 : 2;
+  float rho_bar = 0.5f * (qb[2 * ST] + qb[3 * ST]);
+  float c_bar = 0.5f * (qb[6 * FS + 2 * ST] + qb[6 * FS + 3 * ST]);
+  float rc = rho_bar * c_bar, mic2 = -frcp(c_bar * c_bar);
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    float w[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      float p = qb[3 * FS + k * ST];
+      if (v == 0) w[k] = 0.5f * fmaf(-rc, qb[UN * FS + k * ST], p);
+      else if (v == 1) w[k] = fmaf(mic2, p, qb[k * ST]);
+      else if (v == 2) w[k] = 0.5f * fmaf(rc, qb[UN * FS + k * ST], p);
+      else w[k] = qb[4 * FS + k * ST];
+    }
+    float mn = w[0], mx = w[0], sum = w[0];
+#pragma unroll
+    for (int k = 1; k < 6; ++k) {
+      mn = fminf(mn, w[k]);
+      mx = fmaxf(mx, w[k]);
+      sum += w[k];
+    }
+    float mean = sum * (1.0f / 6.0f);
+    float inv = (mx - mn) > 1e-6f * fmaxf(fabsf(mx), fabsf(mn)) ? frcp((mx - mn) + 1e-30f) : 0.0f;
+#pragma unroll
+    for (int k = 0; k < 6; k += 2) {
+      __nv_bfloat162 pr = __floats2bfloat162_rn((w[k] - mean) * inv, (w[k + 1] - mean) * inv);
+      *reinterpret_cast<__nv_bfloat162*>(&out[v * 6 + k]) = pr;
+    }
+  }
+}
+
+// 5th-order linear-weight reconstruction of variable R on both sides
+template <int D, int R>
+__device__ __forceinline__ void linear_item(const float* qb, float& l5, float& r5) {
+  float w[6];
+  project6<D, R>(qb, w);
+  l5 = linear5(w[0], w[1], w[2], w[3], w[4]);
+  r5 = linear5(w[5], w[4], w[3], w[2], w[1]);
+}
+
+template <bool LEARNED>
 __global__ void __launch_bounds__(NT, 2) k_stage2d(StageArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Smem& S = *reinterpret_cast<Smem*>(smem_raw);
+  SmemGate& SG = *reinterpret_cast<SmemGate*>(smem_raw + sizeof(Smem));
+  if (a.run_if && *a.run_if == 0) return;  // a conditional redo that is not needed
   const GridDev& g = a.g;
   const int nx = g.n[0], ny = g.n[1];
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
   const int64_t N = g.N, P0 = g.P[0];
   const int tid = threadIdx.x;
-  if (a.stage > 0) {
+  if (a.stage == 1 || a.stage == 2) {
     if (tid == 0) {  // one FP64 division per CTA
       double d = a.dt_fixed > 0.0 ? a.dt_fixed : (double)a.cfl / __longlong_as_double((long long)*a.lmax);
       if (a.stage == 1 && blockIdx.x == 0 && blockIdx.y == 0) *a.dt_out = d;
@@ -194,7 +284,7 @@ __global__ void __launch_bounds__(NT, 2) k_stage2d(StageArgs a) {
     }
     __syncthreads();
   }
-  const float dt = a.stage > 0 ? S.dt : 0.0f;
+  const float dt = (a.stage == 1 || a.stage == 2) ? S.dt : 0.0f;
   const float coef = a.stage == 0 ? 0.0f : (a.stage == 1 ? dt : 0.25f * dt);
   float lam_max = 0.0f;
 
@@ -209,7 +299,7 @@ __global__ void __launch_bounds__(NT, 2) k_stage2d(StageArgs a) {
     int my = map_bc(gy, ny, g.bc[1][0], g.bc[1][1], fy);
     int64_t i = (int64_t)(NG + my) * P0 + (NG + mx);
     float rho, mu, mv, eint, Gam, Pi;
-    if (a.stage == 0) {
+    if (a.stage == 0 || a.stage == 3) {
       const double* U = a.U;
       rho = f64_to_f32(U[i]);
       mu = f64_to_f32(U[N + i]);
@@ -217,7 +307,11 @@ __global__ void __launch_bounds__(NT, 2) k_stage2d(StageArgs a) {
       eint = f64_to_f32(U[3 * N + i] - U[5 * N + i]);  // E - Pi in FP64
       Gam = f64_to_f32(U[4 * N + i]);
       Pi = f64_to_f32(U[5 * N + i]);
-      bool own = hx >= NG && hx < NG + TX && hy >= NG && hy < NG + TY && !outx && !outy;
+      bool own = a.stage == 0 && hx >= NG && hx < NG + TX && hy >= NG && hy < NG + TY && !outx && !outy;
+      if (LEARNED && own) {
+#pragma unroll
+        for (int m = 0; m < NQ; ++m) a.Ubackup[m * N + i] = U[m * N + i];
+      }
       if (own) {
         a.U32[i] = rho;
         a.U32[N + i] = mu;
@@ -271,7 +365,92 @@ __global__ void __launch_bounds__(NT, 2) k_stage2d(StageArgs a) {
     if (b) atomicMax(a.lmax, b);
   }
 
+  // ---- phases G1, G2 (learned gate): features, then the BF16 tensor-core MLP ----
+  if (LEARNED) {
+    for (int i = tid; i < NFRAG * 32; i += NT) SG.frag[i / 32][i % 32] = a.mlp_frag[i];
+    for (int i = tid; i < 65; i += NT) {
+      float b = a.mlp_bias[i];
+      if (i < 32) SG.b1[i] = b;
+      else if (i < 64) SG.b2[i - 32] = b;
+      else SG.b3 = b;
+    }
+    for (int f = tid; f < NF; f += NT) {
+      bool isx;
+      int hx, hy, dhx, dhy;
+      SG.smooth[f] = 0;
+      if (!face_geom(f, x0, y0, nx, ny, isx, hx, hy, dhx, dhy)) continue;
+      const float* qb = &S.q[0][hy][hx];
+      if (isx)
+        gate_features<0>(qb, S.feat[f]);
+      else
+        gate_features<1>(qb, S.feat[f]);
+    }
+    __syncthreads();
+    const int lane = tid & 31, warp = tid >> 5, g8 = lane >> 2, t4 = lane & 3;
+    for (int mt = warp; mt < NMT; mt += NT / 32) {
+      int r0 = min(mt * 16 + g8, NF - 1), r1 = min(mt * 16 + g8 + 8, NF - 1);
+      const uint32_t* x0p = reinterpret_cast<const uint32_t*>(S.feat[r0]);
+      const uint32_t* x1p = reinterpret_cast<const uint32_t*>(S.feat[r1]);
+      // layer 1: [16 x 24(32)] x [24(32) x 32]
+      float h[4][4];
+#pragma unroll
+      for (int nt = 0; nt < 4; ++nt) {
+        h[nt][0] = h[nt][1] = h[nt][2] = h[nt][3] = 0.0f;
+        mma16816(h[nt], x0p[t4], x1p[t4], x0p[t4 + 4], x1p[t4 + 4], SG.frag[nt][lane]);
+        mma16816(h[nt], x0p[t4 + 8], x1p[t4 + 8], 0u, 0u, SG.frag[4 + nt][lane]);
+      }
+      uint32_t A[2][4];
+#pragma unroll
+      for (int nt = 0; nt < 4; ++nt) {
+        float b0 = SG.b1[nt * 8 + 2 * t4], b1 = SG.b1[nt * 8 + 2 * t4 + 1];
+        uint32_t lo = pack_bf16(fmaxf(h[nt][0] + b0, 0.0f), fmaxf(h[nt][1] + b1, 0.0f));
+        uint32_t hi = pack_bf16(fmaxf(h[nt][2] + b0, 0.0f), fmaxf(h[nt][3] + b1, 0.0f));
+        A[nt >> 1][(nt & 1) * 2 + 0] = lo;
+        A[nt >> 1][(nt & 1) * 2 + 1] = hi;
+      }
+      // layer 2: [16 x 32] x [32 x 32]
+#pragma unroll
+      for (int nt = 0; nt < 4; ++nt) {
+        h[nt][0] = h[nt][1] = h[nt][2] = h[nt][3] = 0.0f;
+        mma16816(h[nt], A[0][0], A[0][1], A[0][2], A[0][3], SG.frag[NFRAG1 + nt][lane]);
+        mma16816(h[nt], A[1][0], A[1][1], A[1][2], A[1][3], SG.frag[NFRAG1 + 4 + nt][lane]);
+      }
+#pragma unroll
+      for (int nt = 0; nt < 4; ++nt) {
+        float b0 = SG.b2[nt * 8 + 2 * t4], b1 = SG.b2[nt * 8 + 2 * t4 + 1];
+        uint32_t lo = pack_bf16(fmaxf(h[nt][0] + b0, 0.0f), fmaxf(h[nt][1] + b1, 0.0f));
+        uint32_t hi = pack_bf16(fmaxf(h[nt][2] + b0, 0.0f), fmaxf(h[nt][3] + b1, 0.0f));
+        A[nt >> 1][(nt & 1) * 2 + 0] = lo;
+        A[nt >> 1][(nt & 1) * 2 + 1] = hi;
+      }
+      // layer 3: [16 x 32] x [32 x 1 (8)]
+      float z[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+      mma16816(z, A[0][0], A[0][1], A[0][2], A[0][3], SG.frag[NFRAG1 + NFRAG2][lane]);
+      mma16816(z, A[1][0], A[1][1], A[1][2], A[1][3], SG.frag[NFRAG1 + NFRAG2 + 1][lane]);
+      if (t4 == 0) {
+        int f0 = mt * 16 + g8, f1 = f0 + 8;
+        if (f0 < NF && (z[0] + SG.b3) < a.thr) SG.smooth[f0] = 1;
+        if (f1 < NF && (z[2] + SG.b3) < a.thr) SG.smooth[f1] = 1;
+      }
+    }
+    __syncthreads();
+    if (a.stage == 3) {  // gate evaluation only: the decisions go to the mask arrays
+      for (int f = tid; f < NF; f += NT) {
+        bool isx;
+        int hx, hy, dhx, dhy;
+        if (!face_geom(f, x0, y0, nx, ny, isx, hx, hy, dhx, dhy)) continue;
+        if (isx)
+          a.mask_x[(int64_t)(y0 + hy - NG) * (nx + 1) + (x0 + hx)] = SG.smooth[f];
+        else
+          a.mask_y[(int64_t)(y0 + hy) * nx + (x0 + hx - NG)] = SG.smooth[f];
+      }
+      return;
+    }
+  }
+
   // ---- phase B1: WENO-IS per (face, characteristic variable) ----
+  const bool drift = LEARNED && ((int)((blockIdx.y * gridDim.x + blockIdx.x) & 63) == a.drift_tile);
+  float dnum = 0.0f, dden = 0.0f, nsm = 0.0f, nval = 0.0f;
   {
     int fo[FPT];       // face index, or -1
     int qo[FPT];       // offset of stencil cell 0 in the halo tile
@@ -285,16 +464,37 @@ __global__ void __launch_bounds__(NT, 2) k_stage2d(StageArgs a) {
       fo[t] = ok ? f : -1;
       qo[t] = hy * HX + hx;
       fxd[t] = isx;
+      if (LEARNED && ok) {
+        nval += 1.0f;
+        nsm += SG.smooth[f] ? 1.0f : 0.0f;
+      }
     }
     const float* q0 = &S.q[0][0][0];
 #define WS_B1(R)                                                              \
     _Pragma("unroll") for (int t = 0; t < FPT; ++t) {                         \
       if (fo[t] < 0) continue;                                                \
       float l5, r5;                                                           \
-      if (fxd[t])                                                             \
-        weno_item<0, R>(q0 + qo[t], a.P, l5, r5);                             \
-      else                                                                    \
-        weno_item<1, R>(q0 + qo[t], a.P, l5, r5);                             \
+      bool lin = LEARNED && R != 2 && SG.smooth[fo[t]]; /* shear: WENO-IS */ \
+      if (lin) {                                                              \
+        if (fxd[t])                                                           \
+          linear_item<0, R>(q0 + qo[t], l5, r5);                              \
+        else                                                                  \
+          linear_item<1, R>(q0 + qo[t], l5, r5);                              \
+      }                                                                       \
+      if (!lin || drift) {                                                    \
+        float fl, fr;                                                         \
+        if (fxd[t])                                                           \
+          weno_item<0, R>(q0 + qo[t], a.P, fl, fr);                           \
+        else                                                                  \
+          weno_item<1, R>(q0 + qo[t], a.P, fl, fr);                           \
+        if (lin) {                                                            \
+          dnum += fabsf(l5 - fl) + fabsf(r5 - fr);                            \
+          dden += fabsf(fl) + fabsf(fr);                                      \
+        } else {                                                              \
+          l5 = fl;                                                            \
+          r5 = fr;                                                            \
+        }                                                                     \
+      }                                                                       \
       S.w[0][R][fo[t]] = l5;                                                  \
       S.w[1][R][fo[t]] = r5;                                                  \
     }
@@ -306,7 +506,27 @@ __global__ void __launch_bounds__(NT, 2) k_stage2d(StageArgs a) {
     WS_B1(5)
 #undef WS_B1
   }
+  if (LEARNED) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      dnum += __shfl_xor_sync(0xffffffffu, dnum, o);
+      dden += __shfl_xor_sync(0xffffffffu, dden, o);
+      nsm += __shfl_xor_sync(0xffffffffu, nsm, o);
+      nval += __shfl_xor_sync(0xffffffffu, nval, o);
+    }
+    if ((tid & 31) == 0) {
+      SG.red[0][tid >> 5] = dnum;
+      SG.red[1][tid >> 5] = dden;
+      SG.red[2][tid >> 5] = nsm;
+      SG.red[3][tid >> 5] = nval;
+    }
+  }
   __syncthreads();
+  if (LEARNED && tid < 4) {
+    float sum = 0.0f;
+    for (int w = 0; w < NT / 32; ++w) sum += SG.red[tid][w];
+    if (tid >= 2 || drift) atomicAdd(&a.lstat[1 + tid], sum);
+  }
 
   // ---- phase B2: back-projection, MOOD, HLLC per face ----
   for (int f = tid; f < NF; f += NT) {
@@ -330,6 +550,7 @@ __global__ void __launch_bounds__(NT, 2) k_stage2d(StageArgs a) {
       back_project<NQ>(wt, ic2, irc, q[side]);
       code[side] = 0;
       if (a.mood && !admissible<NQ>(q[side])) {
+        if (LEARNED && SG.smooth[f]) atomicAdd(&a.lstat[0], 1.0f);
         const float* qb = &S.q[0][hy][hx];
         if (isx)
           weno_side3<0>(qb, side, a.P, wt);
@@ -416,16 +637,57 @@ __global__ void __launch_bounds__(NT, 2) k_stage2d(StageArgs a) {
 
 }  // namespace
 
-int fused2d_smem_bytes() { return (int)sizeof(Smem); }
+// After a gated step: decide on the device whether to redo it without the gate
+// (no host round trip), and keep the gate statistics.
+static __global__ void k_gate_decide(const float* __restrict__ lstat, unsigned long long* nbad, unsigned long long* lmax,
+                              int flags, int* redo, double* stats) {
+  bool r = false;
+  double drift = lstat[2] > 0.0f ? (double)lstat[1] / (double)lstat[2] : 0.0;
+  if ((flags & WS_GATE_REDO_MOOD) && lstat[0] > 0.0f) r = true;
+  if ((flags & WS_GATE_REDO_DRIFT) && drift > 1e-6) r = true;
+  if ((flags & WS_GATE_REDO_NONPHYS) && *nbad > 0ULL) r = true;
+  *redo = r ? 1 : 0;
+  stats[0] += 1.0;
+  stats[1] += r ? 1.0 : 0.0;
+  stats[2] += lstat[3];
+  stats[3] += lstat[4];
+  stats[4] = drift > stats[4] ? drift : stats[4];
+  if (r) {
+    *nbad = 0ULL;
+    *lmax = 0ULL;
+  }
+}
+
+static __global__ void k_restore(const int* __restrict__ redo, const double* __restrict__ src, double* __restrict__ dst,
+                          int64_t n) {
+  if (*redo == 0) return;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = src[i];
+}
+
+void launch_gate_decide(const float* lstat, unsigned long long* nbad, unsigned long long* lmax, int flags, int* redo,
+                        double* stats, cudaStream_t s) {
+  k_gate_decide<<<1, 1, 0, s>>>(lstat, nbad, lmax, flags, redo, stats);
+}
+
+void launch_restore(const int* redo, const double* src, double* dst, int64_t n, cudaStream_t s) {
+  k_restore<<<152 * 4, 256, 0, s>>>(redo, src, dst, n);
+}
+
+int fused2d_smem_bytes() { return (int)(sizeof(Smem) + sizeof(SmemGate)); }
 
 cudaError_t fused2d_prepare() {
-  return cudaFuncSetAttribute(k_stage2d, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
+  cudaError_t e = cudaFuncSetAttribute(k_stage2d<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)sizeof(Smem));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_stage2d<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)(sizeof(Smem) + sizeof(SmemGate)));
 }
 
 void launch_stage2d(const GridDev& g, int stage, double* U, float* U32, const float* Kin, float* Kout,
                     double dt_fixed, double cfl, unsigned long long* lmax, double* dt_out, uint8_t* mask_x,
                     uint8_t* mask_y, float eps_rel, int mood, int weights, unsigned long long* nbad,
-                    cudaStream_t s) {
+                    const GateArgs* gate, const int* run_if, cudaStream_t s) {
   StageArgs a;
   a.g = g;
   a.stage = stage;
@@ -445,7 +707,24 @@ void launch_stage2d(const GridDev& g, int stage, double* U, float* U32, const fl
   a.mood = mood;
   a.nbad = nbad;
   dim3 grid((g.n[0] + TX - 1) / TX, (g.n[1] + TY - 1) / TY);
-  k_stage2d<<<grid, NT, sizeof(Smem), s>>>(a);
+  a.run_if = run_if;
+  if (gate) {
+    a.mlp_frag = gate->frag;
+    a.mlp_bias = gate->bias;
+    a.thr = gate->thr;
+    a.drift_tile = gate->drift_tile;
+    a.Ubackup = gate->Ubackup;
+    a.lstat = gate->lstat;
+    k_stage2d<true><<<grid, NT, sizeof(Smem) + sizeof(SmemGate), s>>>(a);
+  } else {
+    a.mlp_frag = nullptr;
+    a.mlp_bias = nullptr;
+    a.thr = 0.0f;
+    a.drift_tile = -1;
+    a.Ubackup = nullptr;
+    a.lstat = nullptr;
+    k_stage2d<false><<<grid, NT, sizeof(Smem), s>>>(a);
+  }
 }
 
 }  // namespace ws

@@ -75,6 +75,16 @@ struct ws_ctx {
   std::vector<int> ev_cls;
   size_t ev_used = 0;
   int64_t nlaunch[WS_NKERNEL] = {0};
+  // learned smooth-face gate (ws_set_mlp)
+  bool learned_on = false;
+  uint2* mlp_frag = nullptr;     // device, 18 x 32
+  float* mlp_bias = nullptr;     // device, 65
+  float mlp_thr = 0.0f;
+  int gate_flags = 6;
+  float* lstat = nullptr;        // device gate statistics of the current step
+  int* gate_redo = nullptr;      // device: redo flag of the current step
+  double* gate_stats = nullptr;  // device: steps, redone, smooth faces, faces, max drift
+  int64_t gate_steps = 0;        // host step counter (drift-check tile rotation)
   // CUDA graph of one CFL step (ws_set_graph)
   bool graph_on = false;
   cudaGraphExec_t graph_exec = nullptr;
@@ -117,12 +127,27 @@ void launch_update_mixed(const GridDev& g, int stage, const double* Un, const do
 void launch_cfl_u(const GridDev& g, const double* U, unsigned long long* lmax, cudaStream_t s);
 
 // ---- fused 2D mixed-precision RK stage (ws_fused2d.cu) ----
+struct GateArgs {
+  const uint2* frag;   // BF16 MMA fragments of W1, W2, W3 (18 x 32 lanes)
+  const float* bias;   // b1[32], b2[32], b3
+  float thr;           // logit threshold (smooth when below)
+  int drift_tile;      // tile residue (mod 64) of this step's drift check
+  double* Ubackup;     // stage 0 copies U here
+  float* lstat;        // gate statistics, see k_stage2d
+};
 int fused2d_smem_bytes();
 cudaError_t fused2d_prepare();
 void launch_stage2d(const GridDev& g, int stage, double* U, float* U32, const float* Kin, float* Kout,
                     double dt_fixed, double cfl, unsigned long long* lmax, double* dt_out, uint8_t* mask_x,
                     uint8_t* mask_y, float eps_rel, int mood, int weights, unsigned long long* nbad,
-                    cudaStream_t s);
+                    const GateArgs* gate, const int* run_if, cudaStream_t s);
+void launch_gate_decide(const float* lstat, unsigned long long* nbad, unsigned long long* lmax, int flags, int* redo,
+                        double* stats, cudaStream_t s);
+void launch_restore(const int* redo, const double* src, double* dst, int64_t n, cudaStream_t s);
+
+// ---- learned gate (ws_learned.cu) ----
+void launch_face_samples(const GridDev& g, int d, const float* Q, int64_t stride, int64_t out0, int64_t max_out,
+                         float* feats, uint8_t* labels, float eps_rel, int weights, cudaStream_t s);
 
 // ---- batched tubes (ws_tubes.cu) ----
 void launch_tubes_ghost(const TubesDev& t, double* U, cudaStream_t s);

@@ -1,0 +1,233 @@
+"""Learned smooth-face gate: the GPU training kernels against the FP64 MLP
+oracle, and the face sampler's features and labels against the FP64 scheme
+oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import mlp_oracle as mo
+from paper_1707_00592_gb300 import workloads as wl
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("needs a GPU", allow_module_level=True)
+
+import paper_1707_00592_gb300 as ws  # noqa: E402
+
+
+def cuda(a, dtype):
+    return torch.tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
+
+
+def test_forward_matches_oracle():
+    rng = np.random.default_rng(0)
+    p = mo.init(3)
+    X = rng.normal(size=(3000, mo.NIN))
+    logits = torch.empty(3000, dtype=torch.float32, device="cuda")
+    ws.ws_mlp_forward(cuda(p, torch.float32), cuda(X, torch.float32), logits)
+    torch.cuda.synchronize()
+    z, _ = mo.forward(p.astype(np.float32).astype(np.float64), X.astype(np.float32).astype(np.float64))
+    np.testing.assert_allclose(logits.cpu().numpy(), z, rtol=1e-4, atol=1e-4 * np.abs(z).max())
+
+
+def test_gradient_matches_oracle():
+    """FP32 gradient of the weighted BCE against the FP64 back-propagation
+    (itself pinned by finite differences)."""
+    rng = np.random.default_rng(1)
+    p = mo.init(4)
+    X = rng.normal(size=(5000, mo.NIN))
+    y = (rng.random(5000) < 0.3).astype(np.uint8)
+    grad = torch.empty(mo.NPARAM, dtype=torch.float32, device="cuda")
+    loss = torch.empty(1, dtype=torch.float32, device="cuda")
+    ws.ws_mlp_grad(cuda(p, torch.float32), cuda(X, torch.float32), cuda(y, torch.uint8), 2.5, grad, loss)
+    torch.cuda.synchronize()
+    p32 = p.astype(np.float32).astype(np.float64)
+    X32 = X.astype(np.float32).astype(np.float64)
+    g = mo.grad(p32, X32, y, 2.5)
+    gg = grad.cpu().numpy()
+    assert np.abs(gg - g).max() <= 2e-4 * np.abs(g).max()
+    assert loss.item() == pytest.approx(mo.loss(p32, X32, y, 2.5), rel=1e-4)
+
+
+def test_adam_step():
+    rng = np.random.default_rng(2)
+    p = rng.normal(size=mo.NPARAM)
+    g = rng.normal(size=mo.NPARAM)
+    P, M, V = cuda(p, torch.float32), torch.zeros(mo.NPARAM, device="cuda"), torch.zeros(mo.NPARAM, device="cuda")
+    ws.ws_mlp_adam(P, M, V, cuda(g, torch.float32), 1, 1e-3)
+    torch.cuda.synchronize()
+    # step 1 of Adam: m_hat = g, v_hat = g^2, so p -= lr g / (|g| + eps)
+    expect = p - 1e-3 * g / (np.abs(g) + 1e-8)
+    np.testing.assert_allclose(P.cpu().numpy(), expect, rtol=1e-5, atol=1e-6)
+
+
+def oracle_face_features(qc, cc):
+    """FP64 features and label of one face from the oracle's own functions."""
+    nq = qc.shape[1]
+    rho_bar = 0.5 * (qc[2, 0] + qc[3, 0])
+    c_bar = 0.5 * (cc[2] + cc[3])
+    Lm, Rm = oracle.char_matrices(nq, rho_bar, c_bar)
+    w = qc @ Lm.T
+    feats = []
+    rough = False
+    full = np.zeros((2, nq))
+    flat_gamma = False
+    for r in range(nq):
+        col = w[:, r]
+        rng_ = col.max() - col.min() + 1e-30
+        flat_r = col.max() - col.min() <= 1e-6 * max(abs(col.max()), abs(col.min()))
+        if r == nq - 3:
+            flat_gamma = flat_r
+        for side in range(2):
+            v = col[0:5] if side == 0 else col[5:0:-1]
+            f, _ = oracle.weno_is(v)
+            lin = v[2] + (2 * (v[0] - v[2]) - 13 * (v[1] - v[2]) + 27 * (v[3] - v[2]) - 3 * (v[4] - v[2])) / 60.0
+            flat = flat_r or (r == nq - 2 and flat_gamma)
+            shear = 2 <= r < nq - 3
+            if not shear and not flat and abs(f - lin) > 1e-6 * rng_:
+                rough = True
+            full[side, r] = f
+    cond = []
+    for r in (0, 1, nq - 1, nq - 3):
+        col = w[:, r]
+        span = col.max() - col.min()
+        mag = max(abs(col.max()), abs(col.min()))
+        inv = 1.0 / (span + 1e-30) if span > 1e-6 * mag else 0.0
+        feats.append((col - col.mean()) * inv)
+        cond.append(np.full(6, span > 1e-3 * mag or span == 0.0))
+    for side in range(2):
+        q = Rm @ full[side]
+        if not (q[0] > 0 and q[-2] > 0 and (q[-2] + 1) * q[-3] + q[-1] > 0):
+            rough = True
+    return np.concatenate(feats), int(rough), np.concatenate(cond)
+
+
+def test_face_samples_match_oracle():
+    case = wl.random_state(2, (64, 48), seed=6, kind="two_phase")
+    s = ws.Solver(2, case.n, case.dx, case.bc, precision="mixed")
+    Uo = oracle.prim_to_cons(2, case.Q)
+    U = s.tensor(Uo)
+    stride = 7
+    nmax = 2000
+    feats = torch.empty((nmax, 24), dtype=torch.float32, device="cuda")
+    labels = torch.empty(nmax, dtype=torch.uint8, device="cuda")
+    n = ws.ws_face_samples(s.ctx, U, stride, nmax, feats, labels)
+    F = feats.cpu().numpy()[:n]
+    Lb = labels.cpu().numpy()[:n]
+    Uf = oracle.fill_ghosts(oracle.Grid(2, case.n, case.dx, case.bc), Uo)
+    Q = oracle.cons_to_prim(2, Uf)
+    nx, ny = case.n[0], case.n[1]
+    agree = 0
+    checked = 0
+    out = 0
+    for d in range(2):
+        fe = [nx + (d == 0), ny + (d == 1)]
+        nf = fe[0] * fe[1]
+        for sidx in range((nf + stride - 1) // stride):
+            f = sidx * stride
+            fx, fy = f % fe[0], f // fe[0]
+            c = [fx, fy]
+            c[d] -= 1
+            cells = []
+            for j in range(6):
+                cc_ = [3 + c[0], 3 + c[1]]
+                cc_[d] += j - 2
+                cells.append(Q[:, 0, cc_[1], cc_[0]])
+            cells = np.array(cells)
+            perm = [0, 1 + d, 2 - d, 3, 4, 5]
+            qc = cells[:, perm]
+            cc = np.array([oracle.sound_speed(q[0], q[3], q[4], q[5]) for q in qc])
+            feat, lab, cond = oracle_face_features(qc, cc)
+            # features of stencils flat to < 1e-3 of their magnitude carry FP32 noise
+            np.testing.assert_allclose(F[out][cond], feat[cond], atol=2e-3)
+            agree += int(Lb[out] == lab)
+            checked += 1
+            out += 1
+    assert out == n
+    assert agree >= 0.97 * checked
+
+
+def _shock_bubble_state(n):
+    case = wl.shock_bubble_2d(n)
+    s = ws.Solver(2, case.n, case.dx, case.bc, precision="mixed")
+    U = s.prim_to_cons(s.tensor(case.Q))
+    for _ in range(15):  # let the shock enter the bubble
+        s.step(U)
+    return case, s, U
+
+
+def test_tensor_core_gate_matches_fp32_mlp():
+    """The gate's decisions inside the fused stage kernel (BF16 features and
+    weights on the tensor cores) agree with the FP32 MLP on the same faces,
+    except for faces whose logit lies within BF16 rounding of the threshold."""
+    from paper_1707_00592_gb300 import learned
+    case, s, U = _shock_bubble_state(96)
+    P = torch.tensor(learned.init_params(7), dtype=torch.float32, device="cuda")
+    nf = s.nmask
+    feats = torch.empty((nf, 24), dtype=torch.float32, device="cuda")
+    labels = torch.empty(nf, dtype=torch.uint8, device="cuda")
+    n = ws.ws_face_samples(s.ctx, U, 1, nf, feats, labels)
+    assert n == nf
+    z = learned.logits(P, feats).cpu().numpy()
+    thr = float(np.median(z))
+    ws.ws_set_mlp(s.ctx, P, thr)
+    smooth = torch.empty(nf, dtype=torch.uint8, device="cuda")
+    ws.ws_gate_eval(s.ctx, U, smooth)
+    torch.cuda.synchronize()
+    got = smooth.cpu().numpy().astype(bool)
+    expect = z < thr
+    bad = got != expect
+    assert bad.mean() < 0.01
+    assert np.all(np.abs(z[bad] - thr) < 0.05 * (np.abs(z).max() + 1e-30))
+    s.close()
+
+
+def test_gate_closed_equals_plain_step_bitwise():
+    """With a threshold no logit falls below, every face keeps WENO-IS and the
+    gated kernel reproduces the plain fused kernel bit for bit."""
+    from paper_1707_00592_gb300 import learned
+    case = wl.random_state(2, (70, 47), seed=8, kind="two_phase")
+    Uo = oracle.prim_to_cons(2, case.Q)
+    outs = []
+    for gated in (False, True):
+        s = ws.Solver(2, case.n, case.dx, case.bc, precision="mixed")
+        if gated:
+            P = torch.tensor(learned.init_params(1), dtype=torch.float32, device="cuda")
+            ws.ws_set_mlp(s.ctx, P, -1e30)
+        U = s.tensor(Uo)
+        for _ in range(3):
+            s.step(U)
+        outs.append(U.cpu().numpy())
+        if gated:
+            st = ws.ws_gate_stats(s.ctx)
+            assert st["steps"] == 3 and st["smooth_faces"] == 0 and st["redone"] == 0
+        s.close()
+    assert np.array_equal(outs[0], outs[1])
+
+
+def test_gate_open_without_redo_runs_linear_weights():
+    """Threshold above every logit, no redo: every face takes the linear
+    weights for all but the shear variable (MOOD still applies).  On a smooth
+    periodic wave the result stays within 1e-5 (L1) of the plain WENO-IS step."""
+    from paper_1707_00592_gb300 import learned
+    case = wl.entropy_wave(64, 2, amp=0.2, kind="sine")
+    Uo = oracle.prim_to_cons(2, case.Q)
+    outs = []
+    for gated in (False, True):
+        s = ws.Solver(2, case.n, case.dx, case.bc, precision="mixed")
+        if gated:
+            P = torch.tensor(learned.init_params(1), dtype=torch.float32, device="cuda")
+            ws.ws_set_mlp(s.ctx, P, 1e30, 0)
+        U = s.tensor(Uo)
+        for _ in range(10):
+            s.step(U)
+        outs.append(U.cpu().numpy())
+        if gated:
+            st = ws.ws_gate_stats(s.ctx)
+            assert st["smooth_faces"] == st["faces"] > 0 and st["redone"] == 0
+        s.close()
+    sl = wl.interior(2, case.n)
+    a, b = outs[1][sl][0], outs[0][sl][0]
+    assert np.abs(a - b).sum() / np.abs(b).sum() < 1e-5
