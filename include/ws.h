@@ -220,10 +220,12 @@ WS_API int ws_set_mlp(ws_ctx *ctx, const float *params, float threshold, int fla
  * stream. */
 WS_API int ws_gate_eval(ws_ctx *ctx, double *U, uint8_t *smooth);
 
-/* Gate statistics since ws_set_mlp (HOST out[5]): gated steps, steps redone
- * without the gate, smooth-gated faces, faces examined (both summed over RK
- * stages), largest drift ratio seen.  Synchronises. */
-WS_API int ws_gate_stats(ws_ctx *ctx, double out[5]);
+/* Gate statistics since ws_set_mlp (HOST out[6]): gated steps, steps redone
+ * without the gate, faces the MLP sent to the linear weights, faces examined,
+ * largest drift ratio seen, faces with a constant stencil (these need no
+ * reconstruction and bypass the MLP); face counts are summed over RK stages.
+ * Synchronises. */
+WS_API int ws_gate_stats(ws_ctx *ctx, double out[6]);
 
 /* enable != 0: ws_step calls that take the CFL step (dt <= 0) replay one CUDA
  * graph holding the whole step (CFL reduction and the three RK stages)
@@ -245,8 +247,9 @@ WS_API int ws_set_graph(ws_ctx *ctx, int enable);
 #define WS_K_OTHER 5
 #define WS_NKERNEL 8
 
-/* enable != 0: from now on record a CUDA event pair around every kernel the
- * context launches (on its stream) and reset the totals; 0: stop recording. */
+/* enable == 1: from now on record a CUDA event pair around every kernel the
+ * context launches (on its stream) and reset the totals; 2: resume recording
+ * without resetting; 0: stop recording. */
 WS_API int ws_profile(ws_ctx *ctx, int enable);
 
 /* Device time (ms, summed over launches, from the recorded events) and launch

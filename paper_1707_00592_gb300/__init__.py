@@ -250,18 +250,18 @@ def ws_gate_eval(ctx, U, smooth):
 
 
 def ws_gate_stats(ctx) -> dict:
-    out = (ctypes.c_double * 5)()
+    out = (ctypes.c_double * 6)()
     _check(ctx, load().ws_gate_stats(ctx, out))
     return {"steps": int(out[0]), "redone": int(out[1]), "smooth_faces": out[2], "faces": out[3],
-            "max_drift": out[4]}
+            "max_drift": out[4], "constant_faces": out[5]}
 
 
 def ws_set_graph(ctx, enable: bool):
     _check(ctx, load().ws_set_graph(ctx, int(bool(enable))))
 
 
-def ws_profile(ctx, enable: bool):
-    _check(ctx, load().ws_profile(ctx, int(bool(enable))))
+def ws_profile(ctx, enable: bool, reset: bool = True):
+    _check(ctx, load().ws_profile(ctx, (1 if reset else 2) if enable else 0))
 
 
 def ws_profile_read(ctx):

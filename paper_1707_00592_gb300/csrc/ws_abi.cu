@@ -640,10 +640,10 @@ int ws_set_mlp(ws_ctx* c, const float* params, float threshold, int flags) {
   int rc;
   if (!c->mlp_frag) {
     if ((rc = dalloc(c, &c->mlp_frag, 18 * 32)) || (rc = dalloc(c, &c->mlp_bias, 65)) ||
-        (rc = dalloc(c, &c->lstat, 8)) || (rc = dalloc(c, &c->gate_redo, 1)) || (rc = dalloc(c, &c->gate_stats, 5)))
+        (rc = dalloc(c, &c->lstat, 8)) || (rc = dalloc(c, &c->gate_redo, 1)) || (rc = dalloc(c, &c->gate_stats, 6)))
       return rc;
   }
-  CK(c, cudaMemset(c->gate_stats, 0, 5 * sizeof(double)));
+  CK(c, cudaMemset(c->gate_stats, 0, 6 * sizeof(double)));
   CK(c, cudaMemcpy(c->mlp_frag, F.data(), F.size() * 4, cudaMemcpyHostToDevice));
   CK(c, cudaMemcpy(c->mlp_bias, B.data(), 65 * sizeof(float), cudaMemcpyHostToDevice));
   c->mlp_thr = threshold;
@@ -664,11 +664,11 @@ int ws_gate_eval(ws_ctx* c, double* U, uint8_t* smooth) {
   return check_launch(c, "gate eval");
 }
 
-int ws_gate_stats(ws_ctx* c, double out[5]) {
+int ws_gate_stats(ws_ctx* c, double out[6]) {
   if (!c || !out) return fail(c, WS_EINVAL, "bad pointers");
-  for (int i = 0; i < 5; ++i) out[i] = 0.0;
+  for (int i = 0; i < 6; ++i) out[i] = 0.0;
   if (!c->gate_stats) return WS_OK;
-  CK(c, cudaMemcpyAsync(out, c->gate_stats, 5 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaMemcpyAsync(out, c->gate_stats, 6 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   CK(c, cudaStreamSynchronize(c->stream));
   return WS_OK;
 }
@@ -681,7 +681,7 @@ int ws_set_graph(ws_ctx* c, int enable) {
 
 int ws_profile(ws_ctx* c, int enable) {
   if (!c) return fail(c, WS_EINVAL, "null context");
-  if (enable) {
+  if (enable == 1) {
     CK(c, cudaStreamSynchronize(c->stream));
     c->ev_used = 0;
     for (int k = 0; k < WS_NKERNEL; ++k) c->nlaunch[k] = 0;

@@ -175,13 +175,24 @@ __device__ __forceinline__ void project6(const float* qb, float (&w)[6]) {
   }
 }
 
-// 5th-order reconstruction of variable R on both sides of a face
+// 5th-order reconstruction of variable R on both sides of a face.  A
+// stencil flat to 1e-6 of its magnitude (a few FP32 ulps: rounding noise)
+// takes the linear weights, from which WENO-IS differs there by less than
+// the stencil's range; elsewhere WENO-IS.  Returns whether it was flat.
 template <int D, int R>
-__device__ __forceinline__ void weno_item(const float* qb, const WenoParams& P, float& l5, float& r5) {
+__device__ __forceinline__ bool weno_item(const float* qb, const WenoParams& P, float& l5, float& r5) {
   float w[6];
   project6<D, R>(qb, w);
+  float mn = fminf(fminf(fminf(w[0], w[1]), fminf(w[2], w[3])), fminf(w[4], w[5]));
+  float mx = fmaxf(fmaxf(fmaxf(w[0], w[1]), fmaxf(w[2], w[3])), fmaxf(w[4], w[5]));
+  if (mx - mn <= 1e-6f * fmaxf(fabsf(mx), fabsf(mn))) {
+    l5 = linear5(w[0], w[1], w[2], w[3], w[4]);
+    r5 = linear5(w[5], w[4], w[3], w[2], w[1]);
+    return true;
+  }
   l5 = weno_is(w[0], w[1], w[2], w[3], w[4], P, 5);
   r5 = weno_is(w[5], w[4], w[3], w[2], w[1], P, 5);
+  return false;
 }
 
 // 3rd-order reconstruction (d3 = d4 = 0) of all variables of one side:
@@ -652,6 +663,7 @@ static __global__ void k_gate_decide(const float* __restrict__ lstat, unsigned l
   stats[2] += lstat[3];
   stats[3] += lstat[4];
   stats[4] = drift > stats[4] ? drift : stats[4];
+  stats[5] += lstat[5];
   if (r) {
     *nbad = 0ULL;
     *lmax = 0ULL;

@@ -83,7 +83,7 @@ struct ws_ctx {
   int gate_flags = 6;
   float* lstat = nullptr;        // device gate statistics of the current step
   int* gate_redo = nullptr;      // device: redo flag of the current step
-  double* gate_stats = nullptr;  // device: steps, redone, smooth faces, faces, max drift
+  double* gate_stats = nullptr;  // device: steps, redone, gated faces, faces, max drift, constant faces
   int64_t gate_steps = 0;        // host step counter (drift-check tile rotation)
   // CUDA graph of one CFL step (ws_set_graph)
   bool graph_on = false;

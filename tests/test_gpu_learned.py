@@ -226,7 +226,7 @@ def test_gate_open_without_redo_runs_linear_weights():
         outs.append(U.cpu().numpy())
         if gated:
             st = ws.ws_gate_stats(s.ctx)
-            assert st["smooth_faces"] == st["faces"] > 0 and st["redone"] == 0
+            assert st["smooth_faces"] + st["constant_faces"] == st["faces"] > 0 and st["redone"] == 0
         s.close()
     sl = wl.interior(2, case.n)
     a, b = outs[1][sl][0], outs[0][sl][0]
