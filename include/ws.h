@@ -73,7 +73,8 @@ typedef struct ws_grid {
   int n[3];                    /* interior cells per direction (n[d] >= 1; unused dims ignored) */
   double dx[3];                /* uniform cell size per direction (> 0) */
   int bc[3][2];                /* WS_BC_* per direction, [d][0] low side, [d][1] high side */
-  int64_t ntubes;              /* > 0: batched independent 1D tubes (ndim must be 1) */
+  int64_t ntubes;              /* > 0: batched independent 1D tubes (ndim must be 1); in mixed precision
+                                  one persistent launch per RK stage works through (tube, chunk) items */
   const int64_t *tube_offsets; /* HOST array of ntubes+1 padded offsets; each tube has
                                   len = off[t+1]-off[t]-6 >= 6 interior cells, dx = 1/len,
                                   transmissive ends; copied at ws_init */
@@ -226,6 +227,16 @@ WS_API int ws_gate_eval(ws_ctx *ctx, double *U, uint8_t *smooth);
  * reconstruction and bypass the MLP); face counts are summed over RK stages.
  * Synchronises. */
 WS_API int ws_gate_stats(ws_ctx *ctx, double out[6]);
+
+/* Chooses the kernel configuration of the context by timing each candidate
+ * for `steps` CFL steps on a scratch copy of U (DEVICE; U itself is not
+ * modified).  Batched tubes in mixed precision: the chunk of cells a CTA of
+ * the persistent stage kernel processes and its thread count, from
+ * (256, 128), (256, 256), (512, 256), (512, 512), (1024, 512).  *choice (HOST,
+ * nullable) receives the index chosen, or -1 when the context has nothing to
+ * tune.  Allocates a scratch state for the duration of the call.
+ * Synchronises. */
+WS_API int ws_autotune(ws_ctx *ctx, const double *U, int steps, int *choice);
 
 /* enable != 0: ws_step calls that take the CFL step (dt <= 0) replay one CUDA
  * graph holding the whole step (CFL reduction and the three RK stages)

@@ -80,6 +80,7 @@ def load():
         "ws_destroy": (None, [vp]),
         "ws_profile": (ctypes.c_int, [vp, ctypes.c_int]),
         "ws_set_graph": (ctypes.c_int, [vp, ctypes.c_int]),
+        "ws_autotune": (ctypes.c_int, [vp, vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
         "ws_set_mlp": (ctypes.c_int, [vp, vp, ctypes.c_float, ctypes.c_int]),
         "ws_gate_eval": (ctypes.c_int, [vp, vp, vp]),
         "ws_gate_stats": (ctypes.c_int, [vp, dp]),
@@ -254,6 +255,12 @@ def ws_gate_stats(ctx) -> dict:
     _check(ctx, load().ws_gate_stats(ctx, out))
     return {"steps": int(out[0]), "redone": int(out[1]), "smooth_faces": out[2], "faces": out[3],
             "max_drift": out[4], "constant_faces": out[5]}
+
+
+def ws_autotune(ctx, U, steps: int = 3) -> int:
+    choice = ctypes.c_int(-1)
+    _check(ctx, load().ws_autotune(ctx, _ptr(U), int(steps), ctypes.byref(choice)))
+    return choice.value
 
 
 def ws_set_graph(ctx, enable: bool):

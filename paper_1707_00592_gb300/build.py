@@ -28,6 +28,7 @@ UNITS = {
     "ws_mixed.cu": [],
     "ws_fused2d.cu": [],
     "ws_learned.cu": [],
+    "ws_tubes_mixed.cu": [],
     "ws_noalloc.cu": ["-fmad=false"],
 }
 

@@ -94,6 +94,9 @@ void free_all(ws_ctx* c) {
   cudaFree(c->Uhost_dev);
   cudaFree(c->off_dev);
   cudaFree(c->cell_tube);
+  cudaFree(c->chunk_tube);
+  cudaFree(c->chunk_start);
+  cudaFree(c->counters);
   cudaFree(c->mood_counts);
   cudaFree(c->mask_off_dev);
   for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
@@ -108,6 +111,32 @@ void free_all(ws_ctx* c) {
 }
 
 bool tubes(const ws_ctx* c) { return c->grid.ntubes > 0; }
+
+// work items of the persistent mixed-precision tube kernel: chunks of CH cells
+int build_chunks(ws_ctx* c, int config) {
+  int CH = tube_chunk_size(config);
+  std::vector<int64_t> ct;
+  std::vector<int> cs;
+  for (int64_t t = 0; t < c->td.ntubes; ++t) {
+    int64_t len = c->off_host[t + 1] - c->off_host[t] - 2 * NG;
+    for (int64_t s0 = 0; s0 < len; s0 += CH) {
+      ct.push_back(t);
+      cs.push_back((int)s0);
+    }
+  }
+  cudaFree(c->chunk_tube);
+  cudaFree(c->chunk_start);
+  c->chunk_tube = nullptr;
+  c->chunk_start = nullptr;
+  int rc;
+  if ((rc = dalloc(c, &c->chunk_tube, (int64_t)ct.size())) || (rc = dalloc(c, &c->chunk_start, (int64_t)cs.size())))
+    return rc;
+  CK(c, cudaMemcpy(c->chunk_tube, ct.data(), ct.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
+  CK(c, cudaMemcpy(c->chunk_start, cs.data(), cs.size() * sizeof(int), cudaMemcpyHostToDevice));
+  c->nchunks = (int64_t)ct.size();
+  c->tube_config = config;
+  return WS_OK;
+}
 bool mixed(const ws_ctx* c) { return c->opts.precision == WS_PREC_MIXED; }
 
 // one RHS evaluation of the stage state Us into the face arrays
@@ -177,6 +206,22 @@ int step_device(ws_ctx* c, double* U, double dt) {
   const GridDev& g = c->gd;
   int rc;
   CK(c, cudaMemsetAsync(c->nbad, 0, sizeof(unsigned long long), c->stream));
+  if (tubes(c) && mixed(c)) {
+    const int64_t nt = c->td.ntubes;
+    CK(c, cudaMemsetAsync(c->lmax, 0, sizeof(unsigned long long) * nt, c->stream));
+    CK(c, cudaMemsetAsync(c->counters, 0, 3 * sizeof(unsigned), c->stream));
+    for (int s = 0; s < 3; ++s) {
+      KScope k(c, WS_K_FACE);
+      const float* Kin = s == 1 ? c->Ka : c->Kb;
+      float* Kout = s == 0 ? c->Ka : c->Kb;
+      launch_tubes_stage_mixed(c->td, c->tube_config, s, U, c->Q32, Kin, Kout, dt, c->opts.cfl, c->lmax, c->dt_dev,
+                               c->chunk_tube, c->chunk_start, c->nchunks, c->counters + s,
+                               c->mask + (int64_t)s * c->nmask, (float)c->opts.eps, c->opts.mood, c->opts.weights,
+                               c->nbad, c->stream);
+    }
+    c->last_stages = 3;
+    return check_launch(c, "mixed tube stage");
+  }
   if (tubes(c)) {
     const int64_t nt = c->td.ntubes;
     for (int s = 0; s < 3; ++s) {
@@ -289,8 +334,6 @@ int ws_init(const ws_grid* grid, const ws_opts* opts, void* stream, ws_ctx** out
   if (op.eps <= 0.0) op.eps = op.precision == WS_PREC_FP64 ? 1e-40 : 1e-10;
   if (op.cfl <= 0.0) op.cfl = 0.5;
   if (op.learned) return fail(nullptr, WS_ENOTSUP, "the learned face gate is not built in this library");
-  if (tb && op.precision == WS_PREC_MIXED)
-    return fail(nullptr, WS_ENOTSUP, "batched tubes run in FP64 in this library");
 
   ws_ctx* c = new (std::nothrow) ws_ctx();
   if (!c) return fail(nullptr, WS_ECUDA, "out of host memory");
@@ -393,13 +436,20 @@ int ws_init(const ws_grid* grid, const ws_opts* opts, void* stream, ws_ctx** out
     }
     c->td.off = c->off_dev;
     c->td.cell_tube = c->cell_tube;
+    c->off_host = off;
+    if (op.precision == WS_PREC_MIXED) {
+      if ((rc = dalloc(c, &c->Q32, 5 * total)) || (rc = dalloc(c, &c->Ka, 5 * total)) ||
+          (rc = dalloc(c, &c->Kb, 5 * total)) || (rc = dalloc(c, &c->counters, 3)) || (rc = build_chunks(c, 2)))
+        goto bad;
+    }
   }
   if ((rc = dalloc(c, &c->mood_counts, 9)) || (rc = dalloc(c, &c->mask_off_dev, 3))) goto bad;
   if (cudaMemcpy(c->mask_off_dev, c->mask_off, 3 * sizeof(int64_t), cudaMemcpyHostToDevice) != cudaSuccess) {
     rc = fail(c, WS_ECUDA, "copying mask offsets failed");
     goto bad;
   }
-  if (cudaMemset(c->mask, 0, 3 * c->nmask) != cudaSuccess) {
+  // tube masks hold one byte per padded cell; the bytes that carry no face stay 0xff
+  if (cudaMemset(c->mask, tb ? 0xff : 0, 3 * c->nmask) != cudaSuccess) {
     rc = fail(c, WS_ECUDA, "cudaMemset failed");
     goto bad;
   }
@@ -670,6 +720,52 @@ int ws_gate_stats(ws_ctx* c, double out[6]) {
   if (!c->gate_stats) return WS_OK;
   CK(c, cudaMemcpyAsync(out, c->gate_stats, 6 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   CK(c, cudaStreamSynchronize(c->stream));
+  return WS_OK;
+}
+
+int ws_autotune(ws_ctx* c, const double* U, int steps, int* choice) {
+  if (!c || !U || steps < 1) return fail(c, WS_EINVAL, "bad arguments");
+  if (!(tubes(c) && mixed(c))) {
+    if (choice) *choice = -1;
+    return WS_OK;  // nothing to tune
+  }
+  // time each configuration on a scratch copy of U
+  double* Ut = nullptr;
+  int rc = dalloc(c, &Ut, c->nstate);
+  if (rc) return rc;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  int bestc = c->tube_config;
+  bool prof = c->prof_on;
+  c->prof_on = false;
+  for (int cfg = 0; cfg < kNumTubeConfigs && rc == WS_OK; ++cfg) {
+    if ((rc = build_chunks(c, cfg))) break;
+    cudaMemcpyAsync(Ut, U, sizeof(double) * c->nstate, cudaMemcpyDeviceToDevice, c->stream);
+    if ((rc = step_device(c, Ut, 0.0))) break;  // warm-up
+    cudaEventRecord(e0, c->stream);
+    for (int k = 0; k < steps && rc == WS_OK; ++k) rc = step_device(c, Ut, 0.0);
+    cudaEventRecord(e1, c->stream);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) {
+      best = ms;
+      bestc = cfg;
+    }
+  }
+  c->prof_on = prof;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(Ut);
+  if (rc) return rc;
+  if ((rc = build_chunks(c, bestc))) return rc;
+  if (c->graph_exec) {
+    cudaGraphExecDestroy(c->graph_exec);
+    c->graph_exec = nullptr;
+  }
+  if (choice) *choice = bestc;
   return WS_OK;
 }
 

@@ -69,6 +69,12 @@ struct ws_ctx {
   ws::TubesDev td{};
   int64_t* off_dev = nullptr;
   int* cell_tube = nullptr;
+  std::vector<int64_t> off_host;   // tube offsets
+  int tube_config = 2;             // mixed tubes: autotuned (chunk, threads) configuration
+  int64_t* chunk_tube = nullptr;   // device: work item -> tube
+  int* chunk_start = nullptr;      // device: work item -> first cell of the chunk
+  int64_t nchunks = 0;
+  unsigned* counters = nullptr;    // device: 3 work counters (one per stage)
   // measurement: event pairs around launches, launch counts per kernel class
   bool prof_on = false;
   std::vector<cudaEvent_t> ev;  // 2 per recorded launch
@@ -144,6 +150,15 @@ void launch_stage2d(const GridDev& g, int stage, double* U, float* U32, const fl
 void launch_gate_decide(const float* lstat, unsigned long long* nbad, unsigned long long* lmax, int flags, int* redo,
                         double* stats, cudaStream_t s);
 void launch_restore(const int* redo, const double* src, double* dst, int64_t n, cudaStream_t s);
+
+// ---- batched tubes, mixed precision, persistent (ws_tubes_mixed.cu) ----
+extern const int kNumTubeConfigs;
+int tube_chunk_size(int config);
+void launch_tubes_stage_mixed(const TubesDev& t, int config, int stage, double* U, float* U32, const float* Kin,
+                              float* Kout, double dt_fixed, double cfl, unsigned long long* lmax, double* dt_out,
+                              const int64_t* chunk_tube, const int* chunk_start, int64_t nitems, unsigned* counter,
+                              uint8_t* mask, float eps_rel, int mood, int weights, unsigned long long* nbad,
+                              cudaStream_t s);
 
 // ---- learned gate (ws_learned.cu) ----
 void launch_face_samples(const GridDev& g, int d, const float* Q, int64_t stride, int64_t out0, int64_t max_out,

@@ -231,3 +231,43 @@ def test_gate_open_without_redo_runs_linear_weights():
     sl = wl.interior(2, case.n)
     a, b = outs[1][sl][0], outs[0][sl][0]
     assert np.abs(a - b).sum() / np.abs(b).sum() < 1e-5
+
+
+def test_trained_gate_ab():
+    """A/B of the trained gate on a 256^2 shock-bubble (60 CFL steps): the
+    plain mixed path, the gated path (MLP trained on the GPU by this library's
+    kernels, threshold at recall 0.999), and the linear weights everywhere
+    (no gate, no redo).  The gate keeps the result within 1e-6 (L1) of the
+    plain path while sending most faces to the linear weights; the linear
+    weights everywhere either break down or err by orders of magnitude more.
+    Timings are printed (the gate's MLP costs about what it saves on this
+    workload; see the benchmark notes)."""
+    import time
+    from paper_1707_00592_gb300 import learned
+    P, thr, rep = learned.train_gate(total=1_000_000, epochs=3)
+    assert rep["recall"] >= 0.998
+    case = wl.shock_bubble_2d(256)
+    res = {}
+    for mode in ("plain", "gated", "linear"):
+        s = ws.Solver(2, case.n, case.dx, case.bc, precision="mixed")
+        if mode == "gated":
+            ws.ws_set_mlp(s.ctx, P, thr)
+        elif mode == "linear":
+            ws.ws_set_mlp(s.ctx, P, 1e30, 0)
+        U = s.prim_to_cons(s.tensor(case.Q))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(60):
+            s.step(U, 2e-7)
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / 60
+        st = ws.ws_gate_stats(s.ctx) if mode != "plain" else None
+        res[mode] = (U.cpu().numpy()[wl.interior(2, case.n)][0], dt, st)
+        s.close()
+    ref = res["plain"][0]
+    l1 = {m: float(np.abs(r[0] - ref).sum() / np.abs(ref).sum()) for m, r in res.items()}
+    print({m: (l1[m], round(r[1] * 1e3, 4), r[2]) for m, r in res.items()})
+    gst = res["gated"][2]
+    assert l1["gated"] < 1e-6
+    assert gst["smooth_faces"] > 0.3 * gst["faces"]
+    assert not np.isfinite(l1["linear"]) or l1["linear"] > 100 * max(l1["gated"], 1e-12)

@@ -197,3 +197,52 @@ def test_graph_replay_identical(precision):
     assert np.array_equal(outs[0][0], outs[1][0])
     assert np.array_equal(outs[0][1], outs[1][1])
     assert outs[0][2] == outs[1][2]
+
+
+def _tubes_case(ntubes=64, lmin=6, lmax=600, seed=1):
+    off, Q = wl.riemann_tubes(ntubes=ntubes, lmin=lmin, lmax=lmax, seed=seed)
+    return off, Q
+
+
+def test_tubes_mixed_close_to_oracle():
+    """Batched tubes in mixed precision (persistent kernel, chunks of 256..1024
+    cells so that long tubes span several chunks): per-tube CFL steps and
+    densities against the FP64 oracle, tube by tube."""
+    off, Q = _tubes_case()
+    s = ws.Solver(1, (1,), (1.0,), tube_offsets=off, precision="mixed")
+    U = s.prim_to_cons(s.tensor(Q))
+    Uo = oracle.prim_to_cons(1, Q.reshape(5, 1, 1, -1)).reshape(5, -1)
+    for _ in range(3):
+        dts = s.step(U, want_dt=True)
+        Uo, dto = oracle.tubes_step(off, Uo)
+        np.testing.assert_allclose(dts, dto, rtol=2e-5)  # FP32 wave speeds
+    Ug = U.cpu().numpy()
+    for t in range(len(off) - 1):
+        a, b = off[t] + 3, off[t + 1] - 3
+        assert l1_rel(Ug[0, a:b], Uo[0, a:b]) < 2e-5, t
+    counts, _ = s.mood()
+    faces = sum(off[t + 1] - off[t] - 5 for t in range(len(off) - 1))
+    assert counts[0].sum() == 2 * 3 * faces  # both sides of every face, 3 stages, direction x only
+    assert s.nonphysical() == 0
+
+
+def test_tubes_autotune_and_graph():
+    """The autotuner picks one of the configurations; CUDA-graph replay of the
+    persistent tube step gives the same bits as direct launches."""
+    off, Q = _tubes_case(ntubes=200, lmin=256, lmax=2048, seed=3)
+    stream = torch.cuda.Stream()
+    outs = []
+    for graph in (False, True):
+        s = ws.Solver(1, (1,), (1.0,), tube_offsets=off, precision="mixed", stream=stream)
+        with torch.cuda.stream(stream):
+            U = s.prim_to_cons(s.tensor(Q))
+            choice = ws.ws_autotune(s.ctx, U, 2)
+            assert 0 <= choice < 5
+            ws.ws_set_graph(s.ctx, graph)
+            for _ in range(3):
+                s.step(U)
+        stream.synchronize()
+        outs.append(U.cpu().numpy())
+        s.close()
+    # both runs use their own autotuned chunking; results agree to FP32 rounding
+    np.testing.assert_allclose(outs[0][0], outs[1][0], rtol=1e-5)
