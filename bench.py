@@ -205,6 +205,77 @@ def time_fp64(ws, case, stream, steps):
     return {"value": case.cells * steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps, "steps": steps}
 
 
+def time_tubes(ws, stream, steps, seed=0):
+    """The batched configuration: 4096 independent 1D Riemann tubes of 256..8192
+    cells (log-uniform) in one persistent launch per RK stage, mixed precision,
+    per-tube CFL steps, autotuned chunking, CUDA-graph replay."""
+    import torch
+    off, Q = wl.riemann_tubes(ntubes=4096, lmin=256, lmax=8192, seed=seed)
+    s = ws.Solver(1, (1,), (1.0,), tube_offsets=off, precision="mixed", stream=stream)
+    cells = int(sum(off[t + 1] - off[t] - 6 for t in range(len(off) - 1)))
+    with torch.cuda.stream(stream):
+        U = s.prim_to_cons(s.tensor(Q))
+        choice = ws.ws_autotune(s.ctx, U, 2)
+        ws.ws_set_graph(s.ctx, True)
+        for _ in range(3):
+            s.step(U)
+        flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+        ms = 0.0
+        for _ in range(steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            s.step(U)
+            b.record(stream)
+            b.synchronize()
+            ms += a.elapsed_time(b)
+        bad = s.nonphysical()
+    s.close()
+    return {"value": cells * steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps, "tubes": 4096,
+            "cells": cells, "chunk_config": choice, "graph": True, "nonphysical_cells": bad,
+            "workload": "4096 Riemann tubes, lengths log-uniform in [256, 8192], per-tube CFL, mixed precision"}
+
+
+def time_learned(ws, case, stream, steps, run_steps, warmup):
+    """The learned smooth-face gate on the same run: trained on the GPU by the
+    library's kernels, then timed like the plain mixed path, with its L1 density
+    difference from the plain mixed path after the timed run."""
+    import torch
+    from paper_1707_00592_gb300 import learned
+    P, thr, rep = learned.train_gate(total=2_000_000, epochs=4)
+    outs = {}
+    for mode in ("plain", "gated"):
+        s = ws.Solver(2, case.n, case.dx, case.bc, precision="mixed", stream=stream)
+        if mode == "gated":
+            ws.ws_set_mlp(s.ctx, P, thr)
+        with torch.cuda.stream(stream):
+            U = s.prim_to_cons(s.tensor(case.Q))
+            for _ in range(warmup):
+                s.step(U, 5e-8)
+            gap = max(0, (run_steps - warmup - steps) // max(steps, 1))
+            flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+            ms = 0.0
+            for _ in range(steps):
+                for _ in range(gap):
+                    s.step(U, 5e-8)
+                flush.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                s.step(U, 5e-8)
+                b.record(stream)
+                b.synchronize()
+                ms += a.elapsed_time(b)
+            stats = ws.ws_gate_stats(s.ctx) if mode == "gated" else None
+        outs[mode] = (U[wl.interior(2, case.n)][0].double(), ms / steps, stats)
+        s.close()
+    a, b = outs["gated"][0], outs["plain"][0]
+    st = outs["gated"][2]
+    return {"value": case.cells / (outs["gated"][1] * 1e-3), "unit": UNIT, "ms_per_step": outs["gated"][1],
+            "plain_ms_per_step": outs["plain"][1], "l1_density_vs_plain_mixed": float((a - b).abs().sum() / b.abs().sum()),
+            "gated_face_fraction": st["smooth_faces"] / max(st["faces"], 1.0), "steps_redone": st["redone"],
+            "training": rep, "dt": "fixed 5e-8 for both runs (same trajectory)"}
+
+
 def run_ours(args):
     import torch
     import paper_1707_00592_gb300 as ws
@@ -278,6 +349,9 @@ def run_ours(args):
             l1 = l1_vs_fp64(ws, case, s, stream, args.l1_steps)
         if args.precision == "mixed" and args.fp64_steps > 0:
             fp64_cmp = time_fp64(ws, case, stream, args.fp64_steps)
+        tubes = time_tubes(ws, stream, args.tube_steps) if args.tube_steps > 0 else None
+        gate = (time_learned(ws, case, stream, args.steps, args.run_steps, args.warmup)
+                if args.learned and args.precision == "mixed" else None)
 
     clocks = clk.summary()
     if rank != 0:
@@ -329,6 +403,10 @@ def run_ours(args):
         line["l1_density_vs_fp64"] = l1
     if fp64_cmp is not None:
         line["fp64_plain"] = fp64_cmp
+    if tubes is not None:
+        line["batched_tubes"] = tubes
+    if gate is not None:
+        line["learned_gate"] = gate
     if ws_size == 1 and not args.no_cpu_baseline:
         cells_c, times, cores = cpu_oracle_rate(n, args.cpu_rows, args.cpu_steps)
         line["cpu_baseline"] = {"kind": "oracle", "value": cells_c * len(times) / sum(times), "unit": UNIT,
@@ -356,6 +434,8 @@ def main():
     ap.add_argument("--fp32-peak", type=float, default=None)
     ap.add_argument("--l1-steps", type=int, default=200)
     ap.add_argument("--run-steps", type=int, default=2000)
+    ap.add_argument("--tube-steps", type=int, default=10)
+    ap.add_argument("--learned", type=int, default=1)
     ap.add_argument("--fp64-steps", type=int, default=5)
     args = ap.parse_args()
     if args.warmup < 3:

@@ -264,9 +264,9 @@ WS_API int ws_set_graph(ws_ctx *ctx, int enable);
 WS_API int ws_profile(ws_ctx *ctx, int enable);
 
 /* Device time (ms, summed over launches, from the recorded events) and launch
- * count per kernel class since the last ws_profile(ctx, 1).  ms and launches
- * are HOST arrays of WS_NKERNEL entries (either may be NULL).  Launch counts
- * are kept even when recording is off.  Synchronises. */
+ * count per kernel class, over the launches made while recording was on since
+ * the last ws_profile(ctx, 1).  ms and launches are HOST arrays of WS_NKERNEL
+ * entries (either may be NULL).  Synchronises. */
 WS_API int ws_profile_read(ws_ctx *ctx, double ms[WS_NKERNEL], int64_t launches[WS_NKERNEL]);
 
 /* Throughput of dependent fused multiply-add chains on the current device:

@@ -47,8 +47,8 @@ int dalloc(ws_ctx* c, T** p, int64_t count) {
   return WS_OK;
 }
 
-// Records an event pair around the launches of its scope when profiling is on,
-// and counts the kernel launches of its class.
+// Records an event pair around the launches of its scope and counts the kernel
+// launches of its class, while profiling is on.
 struct KScope {
   ws_ctx* c;
   int cls;
@@ -70,7 +70,7 @@ struct KScope {
     cudaEventRecord(c->ev[slot], c->stream);
   }
   ~KScope() {
-    c->nlaunch[cls] += n;
+    if (c->prof_on) c->nlaunch[cls] += n;
     if (slot != (size_t)-1) cudaEventRecord(c->ev[slot + 1], c->stream);
   }
 };
