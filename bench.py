@@ -115,6 +115,23 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def reduce_max_ms(ms: float, device=None) -> float:
+    """Slowest rank's timed-region duration (ms); identity on a single process."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return ms
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(cells_per_rank: int, steps: int, world: int, max_ms: float) -> float:
+    """Whole-job rate: every rank advances its own replica, so the cells
+    updated by all ranks over the slowest rank's time."""
+    return world * cells_per_rank * steps / (max_ms * 1e-3)
+
+
 def dist_setup():
     ws_size = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -324,12 +341,9 @@ def run_ours(args):
         prof = ws.ws_profile_read(s.ctx)
         ws.ws_profile(s.ctx, False)
         ms = sum(a.elapsed_time(b) for a, b in ev)
-        if ws_size > 1:
-            t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = reduce_max_ms(ms, device="cuda")
         cells = case.cells
-        value = ws_size * cells * args.steps / (ms * 1e-3)
+        value = aggregate_rate(cells, args.steps, ws_size, ms)
         launches = int(sum(v[1] for v in prof.values()))
 
         # end to end through the public C ABI with host buffers: H2D of the

@@ -246,3 +246,60 @@ def test_tubes_autotune_and_graph():
         s.close()
     # both runs use their own autotuned chunking; results agree to FP32 rounding
     np.testing.assert_allclose(outs[0][0], outs[1][0], rtol=1e-5)
+
+
+def _sub_batch(off, U, tubes):
+    """The padded segments of the chosen tubes, concatenated, with their offsets."""
+    segs = [U[:, off[t]:off[t + 1]] for t in tubes]
+    sub_off = np.zeros(len(tubes) + 1, dtype=np.int64)
+    sub_off[1:] = np.cumsum([sg.shape[1] for sg in segs])
+    return sub_off, np.ascontiguousarray(np.concatenate(segs, axis=1))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_tubes_full_size_sampled(precision):
+    """The full batched configuration (4096 tubes of 256..8192 cells, 9.3M
+    cells), launched as the benchmark launches it (autotuned, CUDA graph);
+    32 sampled tubes are recomputed by the oracle one by one: bit-exact in
+    FP64, within FP32 tolerances in mixed precision."""
+    off, Q = wl.riemann_tubes(ntubes=4096, lmin=256, lmax=8192, seed=0)
+    stream = torch.cuda.Stream()
+    s = ws.Solver(1, (1,), (1.0,), tube_offsets=off, precision=precision, stream=stream)
+    with torch.cuda.stream(stream):
+        U = s.prim_to_cons(s.tensor(Q))
+        ws.ws_autotune(s.ctx, U, 1)
+        ws.ws_set_graph(s.ctx, True)
+        U0 = U.cpu().numpy()
+        s.step(U)
+    stream.synchronize()
+    Ug = U.cpu().numpy()
+    rng = np.random.default_rng(1)
+    pick = np.sort(rng.choice(4096, size=32, replace=False))
+    sub_off, sub_U = _sub_batch(off, U0, pick)
+    Uo, _ = oracle.tubes_step(sub_off, sub_U)
+    for k, t in enumerate(pick):
+        g = Ug[:, off[t] + 3:off[t + 1] - 3]
+        o = Uo[:, sub_off[k] + 3:sub_off[k + 1] - 3]
+        if precision == "fp64":
+            assert np.array_equal(g, o), t
+        else:
+            assert l1_rel(g[0], o[0]) < 2e-5, t
+    s.close()
+
+
+def test_drop_3d_mixed_close_to_oracle():
+    """3D periodic water drop with density noise (24^3), 4 CFL steps of the
+    generic mixed kernels against the FP64 oracle."""
+    case = wl.drop_3d(24, seed=0)
+    s = solver_for(case)
+    g = ogrid(case)
+    Uo = oracle.prim_to_cons(3, case.Q)
+    U = s.tensor(Uo)
+    for _ in range(4):
+        dt = oracle.cfl_dt(g, Uo)
+        s.step(U, dt)
+        Uo, _, _ = oracle.step(g, Uo, dt=dt)
+    sl = wl.interior(3, case.n)
+    assert l1_rel(U.cpu().numpy()[sl][0], Uo[sl][0]) < 1e-5
+    Q = s.cons_to_prim(U).cpu().numpy()[sl]
+    assert np.abs(Q[4] / 1e5 - 1.0).max() < 5e-3  # pressure equilibrium at FP32 resolution of E - Pi
