@@ -168,6 +168,70 @@ __device__ __forceinline__ float linear5(float qm2, float qm1, float q0, float q
   return fmaf(t, 1.0f / 60.0f, q0);
 }
 
+// Paired FP32 arithmetic: one sm_100-family instruction computes both lanes,
+// each rounded exactly as its scalar counterpart.  The two sides of a face
+// run the same WENO-IS arithmetic on mirrored stencils, so a face
+// reconstructs both as one float2 (x: left state, y: right state), which
+// halves the issued FP32 instructions of the reconstruction.
+__device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, f2(-1.0f), a); }  // exact -b
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 rcp2(float2 a) { return make_float2(frcp(a.x), frcp(a.y)); }
+
+// weno_is(..., 5) on both lanes.  Factors of 1/2 and 4 are moved between
+// products where the scaling is exact (powers of two), and 3 (1 + r3) is
+// formed as one fused multiply-add.
+__device__ __forceinline__ float2 weno5_pair(float2 qm2, float2 qm1, float2 q0, float2 qp1, float2 qp2,
+                                             const WenoParams& P) {
+  const float2 c13 = f2(13.0f / 12.0f), one = f2(1.0f), half = f2(0.5f);
+  float2 dp1 = sub2(qp1, q0), dm1 = sub2(q0, qm1);
+  float2 beta1 = mul2(dp1, dp1);
+  float2 beta2 = mul2(dm1, dm1);
+  float2 a = add2(fma2(q0, f2(-2.0f), qm1), qp1);  // (q_{i-1} - 2 q_i) + q_{i+1}
+  float2 b = mul2(sub2(qm1, qp1), half);
+  float2 beta12 = fma2(c13, mul2(a, a), mul2(b, b));
+  a = mul2(sub2(fma2(qm1, f2(2.0f), fma2(qp1, f2(-2.0f), qp2)), qm2), half);
+  b = add2(fma2(qm1, f2(-4.0f), fma2(q0, f2(6.0f), fma2(qp1, f2(-4.0f), qp2))), qm2);
+  float2 tau5 = fma2(a, a, mul2(c13, mul2(b, b)));  // a holds half the scalar form's a
+  float2 eps = fma2(f2(P.eps_rel), add2(add2(beta1, beta2), tau5), f2(P.eps_abs));
+  float2 r1 = mul2(tau5, rcp2(add2(beta1, eps)));
+  float2 r2 = mul2(tau5, rcp2(add2(beta2, eps)));
+  float2 alpha1, alpha2;
+  if (P.weights == WS_W_MODIFIED) {
+    float2 r12 = mul2(tau5, rcp2(add2(beta12, eps)));
+    alpha1 = fma2(mul2(r1, f2(4.0f)), r12, f2(4.0f));  // 4 (1 + r1 r12)
+    alpha2 = fma2(add2(r2, r2), r12, f2(2.0f));        // 2 (1 + r2 r12)
+  } else {
+    alpha1 = fma2(r1, f2(4.0f), f2(4.0f));
+    alpha2 = fma2(r2, f2(2.0f), f2(2.0f));
+  }
+  float2 num = mul2(fma2(alpha1, dp1, mul2(alpha2, dm1)), half);  // alpha1 delta1 + alpha2 delta2
+  float2 den = add2(alpha1, alpha2);
+  float2 delta3 = fma2(f2(5.0f / 6.0f), dp1, mul2(f2(-1.0f / 6.0f), sub2(qp2, q0)));
+  float2 delta4 = fma2(f2(1.0f / 3.0f), sub2(qm2, q0), mul2(f2(7.0f / 6.0f), dm1));
+  a = add2(fma2(qp1, f2(-2.0f), q0), qp2);
+  b = mul2(add2(fma2(qp1, f2(-4.0f), mul2(f2(3.0f), q0)), qp2), half);
+  float2 beta3 = fma2(c13, mul2(a, a), mul2(b, b));
+  a = add2(fma2(qm1, f2(-2.0f), qm2), q0);
+  b = mul2(fma2(q0, f2(3.0f), fma2(qm1, f2(-4.0f), qm2)), half);
+  float2 beta4 = fma2(c13, mul2(a, a), mul2(b, b));
+  float2 alpha3 = fma2(mul2(tau5, rcp2(add2(beta3, eps))), f2(3.0f), f2(3.0f));
+  float2 alpha4 = fma2(tau5, rcp2(add2(beta4, eps)), one);
+  num = fma2(alpha3, delta3, fma2(alpha4, delta4, num));
+  den = add2(add2(den, alpha3), alpha4);
+  return fma2(num, rcp2(den), q0);
+}
+
+// linear5 on both lanes
+__device__ __forceinline__ float2 linear5_pair(float2 qm2, float2 qm1, float2 q0, float2 qp1, float2 qp2) {
+  float2 t = fma2(f2(2.0f), sub2(qm2, q0), mul2(f2(-13.0f), sub2(qm1, q0)));
+  t = fma2(f2(27.0f), sub2(qp1, q0), t);
+  t = fma2(f2(-3.0f), sub2(qp2, q0), t);
+  return fma2(t, f2(1.0f / 60.0f), q0);
+}
+
 __device__ __forceinline__ float sound_speed2(float rho, float p, float Gam, float Pi) {
   return fdiv(fmaf(Gam + 1.0f, p, Pi), Gam * rho);
 }

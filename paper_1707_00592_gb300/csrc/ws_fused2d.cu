@@ -54,10 +54,7 @@ constexpr int NMT = (NF + 15) / 16;  // 16-face M tiles
 
 struct Smem {
   float q[NQ + 1][HY][HX];        // primitives + sound speed of tile and halo
-  union {
-    float w[2][NQ][NF];           // [side l/r][variable][face] 5th-order reconstructed characteristics
-    __nv_bfloat16 feat[NF][24];   // learned gate inputs (before the reconstruction)
-  };
+  __nv_bfloat16 feat[NF][24];     // learned gate inputs (read before the reconstruction)
   float fx[NQ + 1][TY][TX + 1];   // x-face fluxes (global field order) + face velocity
   float fy[NQ + 1][TY + 1][TX];   // y-face fluxes + face velocity
   unsigned long long red[NT / 32];  // per-warp CFL maxima
@@ -175,24 +172,48 @@ __device__ __forceinline__ void project6(const float* qb, float (&w)[6]) {
   }
 }
 
+// Characteristic variable R of the six stencil cells as mirrored pairs
+// p[k] = (w_k, w_{5-k}), k = 0..4: the .x lanes are the left stencil
+// w_0..w_4, the .y lanes the right stencil w_5..w_1.
+template <int D, int R>
+__device__ __forceinline__ void project_pairs(const float* qb, float2 (&p)[5]) {
+  constexpr int ST = D == 0 ? 1 : HX;
+  constexpr int FS = HY * HX;
+  constexpr int UN = D == 0 ? 1 : 2, UT = D == 0 ? 2 : 1;
+  auto cell = [&](int F, int k) { return make_float2(qb[F * FS + k * ST], qb[F * FS + (5 - k) * ST]); };
+  if (R == 0 || R == NQ - 1) {
+    float rho_bar = 0.5f * (qb[2 * ST] + qb[3 * ST]);
+    float c_bar = 0.5f * (qb[6 * FS + 2 * ST] + qb[6 * FS + 3 * ST]);
+    float2 rc = f2(R == 0 ? -(rho_bar * c_bar) : rho_bar * c_bar);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) p[k] = mul2(f2(0.5f), fma2(rc, cell(UN, k), cell(3, k)));
+  } else if (R == 1) {
+    float c_bar = 0.5f * (qb[6 * FS + 2 * ST] + qb[6 * FS + 3 * ST]);
+    float2 mic2 = f2(-frcp(c_bar * c_bar));
+#pragma unroll
+    for (int k = 0; k < 5; ++k) p[k] = fma2(mic2, cell(3, k), cell(0, k));
+  } else {
+    constexpr int F = R == 2 ? UT : R + 1;  // shear, Gamma, Pi
+#pragma unroll
+    for (int k = 0; k < 5; ++k) p[k] = cell(F, k);
+  }
+}
+
 // 5th-order reconstruction of variable R on both sides of a face.  A
 // stencil flat to 1e-6 of its magnitude (a few FP32 ulps: rounding noise)
 // takes the linear weights, from which WENO-IS differs there by less than
 // the stencil's range; elsewhere WENO-IS.  Returns whether it was flat.
 template <int D, int R>
 __device__ __forceinline__ bool weno_item(const float* qb, const WenoParams& P, float& l5, float& r5) {
-  float w[6];
-  project6<D, R>(qb, w);
-  float mn = fminf(fminf(fminf(w[0], w[1]), fminf(w[2], w[3])), fminf(w[4], w[5]));
-  float mx = fmaxf(fmaxf(fmaxf(w[0], w[1]), fmaxf(w[2], w[3])), fmaxf(w[4], w[5]));
-  if (mx - mn <= 1e-6f * fmaxf(fabsf(mx), fabsf(mn))) {
-    l5 = linear5(w[0], w[1], w[2], w[3], w[4]);
-    r5 = linear5(w[5], w[4], w[3], w[2], w[1]);
-    return true;
-  }
-  l5 = weno_is(w[0], w[1], w[2], w[3], w[4], P, 5);
-  r5 = weno_is(w[5], w[4], w[3], w[2], w[1], P, 5);
-  return false;
+  float2 p[5];
+  project_pairs<D, R>(qb, p);
+  float mn = fminf(fminf(fminf(p[0].x, p[1].x), fminf(p[2].x, p[2].y)), fminf(p[1].y, p[0].y));
+  float mx = fmaxf(fmaxf(fmaxf(p[0].x, p[1].x), fmaxf(p[2].x, p[2].y)), fmaxf(p[1].y, p[0].y));
+  bool flat = mx - mn <= 1e-6f * fmaxf(fabsf(mx), fabsf(mn));
+  float2 v = flat ? linear5_pair(p[0], p[1], p[2], p[3], p[4]) : weno5_pair(p[0], p[1], p[2], p[3], p[4], P);
+  l5 = v.x;
+  r5 = v.y;
+  return flat;
 }
 
 // 3rd-order reconstruction (d3 = d4 = 0) of all variables of one side:
@@ -212,8 +233,8 @@ __device__ __noinline__ void weno_side3(const float* qb, int side, const WenoPar
 #undef WS_SIDE3
 }
 
-// the (at most FPT) faces a thread owns in phase B1
-constexpr int FPT = (NF + NT - 1) / NT;
+// the (at most HPT) halo cells a thread owns in phase A
+constexpr int HPT = (HX * HY + NT - 1) / NT;
 
 __device__ __forceinline__ void mma16816(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
                                          uint2 b) {
@@ -270,10 +291,11 @@ __device__ __forceinline__ void gate_features(const float* qb, __nv_bfloat16* ou
 // 5th-order linear-weight reconstruction of variable R on both sides
 template <int D, int R>
 __device__ __forceinline__ void linear_item(const float* qb, float& l5, float& r5) {
-  float w[6];
-  project6<D, R>(qb, w);
-  l5 = linear5(w[0], w[1], w[2], w[3], w[4]);
-  r5 = linear5(w[5], w[4], w[3], w[2], w[1]);
+  float2 p[5];
+  project_pairs<D, R>(qb, p);
+  float2 v = linear5_pair(p[0], p[1], p[2], p[3], p[4]);
+  l5 = v.x;
+  r5 = v.y;
 }
 
 template <bool LEARNED>
@@ -300,63 +322,77 @@ __global__ void __launch_bounds__(NT, 2) k_stage2d(StageArgs a) {
   float lam_max = 0.0f;
 
   // ---- phase A: stage-state primitives of tile + halo ----
-  for (int h = tid; h < HX * HY; h += NT) {
-    int hy = h / HX, hx = h - hy * HX;
-    int gx = x0 + hx - NG, gy = y0 + hy - NG;
-    bool outx = gx < 0 || gx >= nx, outy = gy < 0 || gy >= ny;
-    if (outx && outy) continue;  // corners are never read
-    bool fx = false, fy = false;
-    int mx = map_bc(gx, nx, g.bc[0][0], g.bc[0][1], fx);
-    int my = map_bc(gy, ny, g.bc[1][0], g.bc[1][1], fy);
-    int64_t i = (int64_t)(NG + my) * P0 + (NG + mx);
-    float rho, mu, mv, eint, Gam, Pi;
-    if (a.stage == 0 || a.stage == 3) {
-      const double* U = a.U;
-      rho = f64_to_f32(U[i]);
-      mu = f64_to_f32(U[N + i]);
-      mv = f64_to_f32(U[2 * N + i]);
-      eint = f64_to_f32(U[3 * N + i] - U[5 * N + i]);  // E - Pi in FP64
-      Gam = f64_to_f32(U[4 * N + i]);
-      Pi = f64_to_f32(U[5 * N + i]);
-      bool own = a.stage == 0 && hx >= NG && hx < NG + TX && hy >= NG && hy < NG + TY && !outx && !outy;
-      if (LEARNED && own) {
+  // A thread owns up to HPT halo cells; all their global loads are issued
+  // before any of them is used, so that a CTA has its whole halo in flight.
+  {
+    float ld[HPT][NQ];
+    int hh[HPT];
+    bool flx[HPT], fly[HPT];
 #pragma unroll
-        for (int m = 0; m < NQ; ++m) a.Ubackup[m * N + i] = U[m * N + i];
+    for (int t = 0; t < HPT; ++t) {
+      int h = tid + t * NT;
+      int hy = h / HX, hx = h - hy * HX;
+      int gx = x0 + hx - NG, gy = y0 + hy - NG;
+      bool outx = gx < 0 || gx >= nx, outy = gy < 0 || gy >= ny;
+      hh[t] = (h < HX * HY && !(outx && outy)) ? h : -1;  // corners are never read
+      if (hh[t] < 0) continue;
+      bool fx = false, fy = false;
+      int mx = map_bc(gx, nx, g.bc[0][0], g.bc[0][1], fx);
+      int my = map_bc(gy, ny, g.bc[1][0], g.bc[1][1], fy);
+      flx[t] = fx;
+      fly[t] = fy;
+      int64_t i = (int64_t)(NG + my) * P0 + (NG + mx);
+      if (a.stage == 0 || a.stage == 3) {
+        const double* U = a.U;
+        ld[t][0] = f64_to_f32(U[i]);
+        ld[t][1] = f64_to_f32(U[N + i]);
+        ld[t][2] = f64_to_f32(U[2 * N + i]);
+        ld[t][3] = f64_to_f32(U[3 * N + i] - U[5 * N + i]);  // E - Pi in FP64
+        ld[t][4] = f64_to_f32(U[4 * N + i]);
+        ld[t][5] = f64_to_f32(U[5 * N + i]);
+        bool own = a.stage == 0 && hx >= NG && hx < NG + TX && hy >= NG && hy < NG + TY && !outx && !outy;
+        if (LEARNED && own) {
+#pragma unroll
+          for (int m = 0; m < NQ; ++m) a.Ubackup[m * N + i] = U[m * N + i];
+        }
+        if (own) {
+#pragma unroll
+          for (int m = 0; m < NQ; ++m) a.U32[m * N + i] = ld[t][m];
+        }
+      } else {
+        const float* V = a.U32;
+        const float* K = a.Kin;
+        ld[t][0] = fmaf(coef, K[i], V[i]);
+        ld[t][1] = fmaf(coef, K[N + i], V[N + i]);
+        ld[t][2] = fmaf(coef, K[2 * N + i], V[2 * N + i]);
+        ld[t][3] = fmaf(coef, K[3 * N + i] - K[5 * N + i], V[3 * N + i]);
+        ld[t][4] = fmaf(coef, K[4 * N + i], V[4 * N + i]);
+        ld[t][5] = fmaf(coef, K[5 * N + i], V[5 * N + i]);
       }
-      if (own) {
-        a.U32[i] = rho;
-        a.U32[N + i] = mu;
-        a.U32[2 * N + i] = mv;
-        a.U32[3 * N + i] = eint;
-        a.U32[4 * N + i] = Gam;
-        a.U32[5 * N + i] = Pi;
-      }
-    } else {
-      const float* V = a.U32;
-      const float* K = a.Kin;
-      rho = fmaf(coef, K[i], V[i]);
-      mu = fmaf(coef, K[N + i], V[N + i]);
-      mv = fmaf(coef, K[2 * N + i], V[2 * N + i]);
-      eint = fmaf(coef, K[3 * N + i] - K[5 * N + i], V[3 * N + i]);
-      Gam = fmaf(coef, K[4 * N + i], V[4 * N + i]);
-      Pi = fmaf(coef, K[5 * N + i], V[5 * N + i]);
     }
-    float irho = frcp(rho);
-    float u = mu * irho, v = mv * irho;
-    if (fx) u = -u;
-    if (fy) v = -v;
-    float p = fmaf(-0.5f * rho, fmaf(u, u, v * v), eint) * frcp(Gam);
-    S.q[0][hy][hx] = rho;
-    S.q[1][hy][hx] = u;
-    S.q[2][hy][hx] = v;
-    S.q[3][hy][hx] = p;
-    S.q[4][hy][hx] = Gam;
-    S.q[5][hy][hx] = Pi;
-    float c = fsqrt(sound_speed2(rho, p, Gam, Pi));
-    S.q[6][hy][hx] = c;
-    if (a.stage == 0 && hx >= NG && hx < NG + TX && hy >= NG && hy < NG + TY && !outx && !outy) {
-      float lam = fmaf(fabsf(u) + c, a.idx, (fabsf(v) + c) * a.idy);
-      if (!(lam <= lam_max)) lam_max = lam;  // NaN propagates
+#pragma unroll
+    for (int t = 0; t < HPT; ++t) {
+      if (hh[t] < 0) continue;
+      int hy = hh[t] / HX, hx = hh[t] - hy * HX;
+      float rho = ld[t][0], eint = ld[t][3], Gam = ld[t][4], Pi = ld[t][5];
+      float irho = frcp(rho);
+      float u = ld[t][1] * irho, v = ld[t][2] * irho;
+      if (flx[t]) u = -u;
+      if (fly[t]) v = -v;
+      float p = fmaf(-0.5f * rho, fmaf(u, u, v * v), eint) * frcp(Gam);
+      S.q[0][hy][hx] = rho;
+      S.q[1][hy][hx] = u;
+      S.q[2][hy][hx] = v;
+      S.q[3][hy][hx] = p;
+      S.q[4][hy][hx] = Gam;
+      S.q[5][hy][hx] = Pi;
+      float c = fsqrt(sound_speed2(rho, p, Gam, Pi));
+      S.q[6][hy][hx] = c;
+      int gx = x0 + hx - NG, gy = y0 + hy - NG;
+      if (a.stage == 0 && hx >= NG && hx < NG + TX && hy >= NG && hy < NG + TY && gx < nx && gy < ny) {
+        float lam = fmaf(fabsf(u) + c, a.idx, (fabsf(v) + c) * a.idy);
+        if (!(lam <= lam_max)) lam_max = lam;  // NaN propagates
+      }
     }
   }
   if (a.stage == 0) {
@@ -459,55 +495,51 @@ __global__ void __launch_bounds__(NT, 2) k_stage2d(StageArgs a) {
     }
   }
 
-  // ---- phase B1: WENO-IS per (face, characteristic variable) ----
+  // ---- phase B: per face, WENO-IS per characteristic variable (B1), then
+  // back-projection, MOOD and HLLC (B2).  The thread that reconstructs a face
+  // also solves its Riemann problem, so no barrier separates the two and the
+  // reconstructed characteristics stay in registers.
   const bool drift = LEARNED && ((int)((blockIdx.y * gridDim.x + blockIdx.x) & 63) == a.drift_tile);
   float dnum = 0.0f, dden = 0.0f, nsm = 0.0f, nval = 0.0f;
-  {
-    int fo[FPT];       // face index, or -1
-    int qo[FPT];       // offset of stencil cell 0 in the halo tile
-    bool fxd[FPT];     // x face?
-#pragma unroll
-    for (int t = 0; t < FPT; ++t) {
-      int f = tid + t * NT;
-      bool isx = false;
-      int hx = 0, hy = 0, dhx, dhy;
-      bool ok = f < NF && face_geom(f, x0, y0, nx, ny, isx, hx, hy, dhx, dhy);
-      fo[t] = ok ? f : -1;
-      qo[t] = hy * HX + hx;
-      fxd[t] = isx;
-      if (LEARNED && ok) {
-        nval += 1.0f;
-        nsm += SG.smooth[f] ? 1.0f : 0.0f;
-      }
+  const float* q0 = &S.q[0][0][0];
+#pragma unroll 1
+  for (int f = tid; f < NF; f += NT) {
+    bool isx;
+    int hx, hy, dhx, dhy;
+    if (!face_geom(f, x0, y0, nx, ny, isx, hx, hy, dhx, dhy)) continue;
+    const int qo = hy * HX + hx;  // stencil cell 0 in the halo tile
+    const bool sm = LEARNED && SG.smooth[f];
+    float wl[NQ], wr[NQ];  // reconstructed characteristics, left and right
+    if (LEARNED) {
+      nval += 1.0f;
+      nsm += sm ? 1.0f : 0.0f;
     }
-    const float* q0 = &S.q[0][0][0];
-#define WS_B1(R)                                                              \
-    _Pragma("unroll") for (int t = 0; t < FPT; ++t) {                         \
-      if (fo[t] < 0) continue;                                                \
-      float l5, r5;                                                           \
-      bool lin = LEARNED && R != 2 && SG.smooth[fo[t]]; /* shear: WENO-IS */ \
-      if (lin) {                                                              \
-        if (fxd[t])                                                           \
-          linear_item<0, R>(q0 + qo[t], l5, r5);                              \
-        else                                                                  \
-          linear_item<1, R>(q0 + qo[t], l5, r5);                              \
-      }                                                                       \
-      if (!lin || drift) {                                                    \
-        float fl, fr;                                                         \
-        if (fxd[t])                                                           \
-          weno_item<0, R>(q0 + qo[t], a.P, fl, fr);                           \
-        else                                                                  \
-          weno_item<1, R>(q0 + qo[t], a.P, fl, fr);                           \
-        if (lin) {                                                            \
-          dnum += fabsf(l5 - fl) + fabsf(r5 - fr);                            \
-          dden += fabsf(fl) + fabsf(fr);                                      \
-        } else {                                                              \
-          l5 = fl;                                                            \
-          r5 = fr;                                                            \
-        }                                                                     \
-      }                                                                       \
-      S.w[0][R][fo[t]] = l5;                                                  \
-      S.w[1][R][fo[t]] = r5;                                                  \
+#define WS_B1(R)                                                          \
+    {                                                                     \
+      float l5, r5;                                                       \
+      bool lin = LEARNED && R != 2 && sm; /* shear: always WENO-IS */     \
+      if (lin) {                                                          \
+        if (isx)                                                          \
+          linear_item<0, R>(q0 + qo, l5, r5);                             \
+        else                                                              \
+          linear_item<1, R>(q0 + qo, l5, r5);                             \
+      }                                                                   \
+      if (!lin || drift) {                                                \
+        float fl, fr;                                                     \
+        if (isx)                                                          \
+          weno_item<0, R>(q0 + qo, a.P, fl, fr);                          \
+        else                                                              \
+          weno_item<1, R>(q0 + qo, a.P, fl, fr);                          \
+        if (lin) {                                                        \
+          dnum += fabsf(l5 - fl) + fabsf(r5 - fr);                        \
+          dden += fabsf(fl) + fabsf(fr);                                  \
+        } else {                                                          \
+          l5 = fl;                                                        \
+          r5 = fr;                                                        \
+        }                                                                 \
+      }                                                                   \
+      wl[R] = l5;                                                         \
+      wr[R] = r5;                                                         \
     }
     WS_B1(0)
     WS_B1(1)
@@ -516,34 +548,7 @@ __global__ void __launch_bounds__(NT, 2) k_stage2d(StageArgs a) {
     WS_B1(4)
     WS_B1(5)
 #undef WS_B1
-  }
-  if (LEARNED) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      dnum += __shfl_xor_sync(0xffffffffu, dnum, o);
-      dden += __shfl_xor_sync(0xffffffffu, dden, o);
-      nsm += __shfl_xor_sync(0xffffffffu, nsm, o);
-      nval += __shfl_xor_sync(0xffffffffu, nval, o);
-    }
-    if ((tid & 31) == 0) {
-      SG.red[0][tid >> 5] = dnum;
-      SG.red[1][tid >> 5] = dden;
-      SG.red[2][tid >> 5] = nsm;
-      SG.red[3][tid >> 5] = nval;
-    }
-  }
-  __syncthreads();
-  if (LEARNED && tid < 4) {
-    float sum = 0.0f;
-    for (int w = 0; w < NT / 32; ++w) sum += SG.red[tid][w];
-    if (tid >= 2 || drift) atomicAdd(&a.lstat[1 + tid], sum);
-  }
 
-  // ---- phase B2: back-projection, MOOD, HLLC per face ----
-  for (int f = tid; f < NF; f += NT) {
-    bool isx;
-    int hx, hy, dhx, dhy;
-    if (!face_geom(f, x0, y0, nx, ny, isx, hx, hy, dhx, dhy)) continue;
     const int un = isx ? 1 : 2, ut = isx ? 2 : 1;
     int ya = hy + 2 * dhy, xa = hx + 2 * dhx, yb = hy + 3 * dhy, xb = hx + 3 * dhx;
     float rho_bar = 0.5f * (S.q[0][ya][xa] + S.q[0][yb][xb]);
@@ -557,11 +562,11 @@ __global__ void __launch_bounds__(NT, 2) k_stage2d(StageArgs a) {
     for (int side = 0; side < 2; ++side) {
       float wt[NQ];
 #pragma unroll
-      for (int r = 0; r < NQ; ++r) wt[r] = S.w[side][r][f];
+      for (int r = 0; r < NQ; ++r) wt[r] = side == 0 ? wl[r] : wr[r];
       back_project<NQ>(wt, ic2, irc, q[side]);
       code[side] = 0;
       if (a.mood && !admissible<NQ>(q[side])) {
-        if (LEARNED && SG.smooth[f]) atomicAdd(&a.lstat[0], 1.0f);
+        if (LEARNED && sm) atomicAdd(&a.lstat[0], 1.0f);
         const float* qb = &S.q[0][hy][hx];
         if (isx)
           weno_side3<0>(qb, side, a.P, wt);
@@ -602,7 +607,27 @@ __global__ void __launch_bounds__(NT, 2) k_stage2d(StageArgs a) {
       if (a.mask_y) a.mask_y[(int64_t)(y0 + j) * nx + (x0 + i)] = mb;
     }
   }
+  if (LEARNED) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      dnum += __shfl_xor_sync(0xffffffffu, dnum, o);
+      dden += __shfl_xor_sync(0xffffffffu, dden, o);
+      nsm += __shfl_xor_sync(0xffffffffu, nsm, o);
+      nval += __shfl_xor_sync(0xffffffffu, nval, o);
+    }
+    if ((tid & 31) == 0) {
+      SG.red[0][tid >> 5] = dnum;
+      SG.red[1][tid >> 5] = dden;
+      SG.red[2][tid >> 5] = nsm;
+      SG.red[3][tid >> 5] = nval;
+    }
+  }
   __syncthreads();
+  if (LEARNED && tid < 4) {
+    float sum = 0.0f;
+    for (int w = 0; w < NT / 32; ++w) sum += SG.red[tid][w];
+    if (tid >= 2 || drift) atomicAdd(&a.lstat[1 + tid], sum);
+  }
 
   // ---- phase C: flux divergence and RK stage ----
   const float idx = a.idx, idy = a.idy;
