@@ -353,6 +353,85 @@ __device__ __forceinline__ void hllc(const float* ql, const float* qr, float* Fh
   ustar = fmaf(wl, us[0], wr * us[1]);
 }
 
+// three-operand minimum and maximum (sm_100 family; NaN operands are
+// ignored as by fminf / fmaxf)
+__device__ __forceinline__ float fmin3(float a, float b, float c) {
+  float r;
+  asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
+}
+__device__ __forceinline__ float fmax3(float a, float b, float c) {
+  float r;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
+}
+
+// back_project<6> of both sides at once: W[r] = (left, right) characteristic r
+__device__ __forceinline__ void back_project_pair(const float2 (&W)[6], float ic2, float irc, float2 (&Q)[6]) {
+  float2 s05 = add2(W[0], W[5]);
+  Q[0] = fma2(f2(ic2), s05, W[1]);
+  Q[1] = mul2(f2(irc), sub2(W[5], W[0]));
+  Q[2] = W[2];
+  Q[3] = s05;
+  Q[4] = W[3];
+  Q[5] = W[4];
+}
+
+// hllc<6> (two dimensions: rho, u_n, u_t, p, Gamma, Pi) with the states of
+// both sides in the lanes of Q (x: left, y: right).  The per-side quantities
+// (conserved state, physical flux, sound speed, star flux) are computed for
+// both sides in paired instructions; the wave-speed estimates and the
+// contact speed are scalar.
+__device__ __forceinline__ void hllc_pair(const float2 (&Q)[6], float* Fhat, float& ustar) {
+  const float2 rho = Q[0], un = Q[1], ut = Q[2], p = Q[3], Gam = Q[4], Pi = Q[5];
+  float2 usq = fma2(ut, ut, mul2(un, un));
+  float2 E = fma2(mul2(f2(0.5f), rho), usq, fma2(Gam, p, Pi));
+  float2 mn = mul2(rho, un);
+  float2 U[6] = {rho, mn, mul2(rho, ut), E, Gam, Pi};
+  float2 F[6] = {mn, fma2(mn, un, p), mul2(mn, ut), mul2(add2(E, p), un), mul2(Gam, un), mul2(Pi, un)};
+  float2 c2 = mul2(fma2(add2(Gam, f2(1.0f)), p, Pi), rcp2(mul2(Gam, rho)));
+  float2 cc = make_float2(fsqrt(c2.x), fsqrt(c2.y));
+  float sl = fsqrt(rho.x), sr = fsqrt(rho.y);
+  float iden = frcp(sl + sr);
+  float ubar = fmaf(sl, un.x, sr * un.y) * iden;
+  float du = un.y - un.x;
+  float c2bar = fmaf(sl, c2.x, sr * c2.y) * iden + (0.5f * (sl * sr) * (iden * iden)) * (du * du);
+  float cbar = fsqrt(c2bar);
+  float Sl = fmin3(ubar - cbar, un.x - cc.x, 0.0f);
+  float Sr = fmax3(ubar + cbar, un.y + cc.y, 0.0f);
+  float2 S = make_float2(Sl, Sr);
+  float2 Sm = sub2(S, un);
+  float2 m = mul2(rho, Sm);
+  float Ss = fdiv(fmaf(m.x, un.x, p.y - p.x) - m.y * un.y, m.x - m.y);
+  float s = (Ss > 0.0f) ? 1.0f : ((Ss < 0.0f) ? -1.0f : 0.0f);
+  float wl = 0.5f * (1.0f + s), wr = 0.5f * (1.0f - s);
+  const float2 SS = f2(Ss);
+  float2 Pk = fma2(m, sub2(SS, un), p);
+  float2 SP = mul2(S, Pk);
+  float2 idS = rcp2(sub2(S, SS));
+  float2 Fs[6];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    float2 t = mul2(SS, fma2(S, U[k], mul2(F[k], f2(-1.0f))));
+    if (k == 1) t = add2(t, SP);
+    if (k == 3) t = fma2(SP, SS, t);
+    Fs[k] = mul2(t, idS);
+  }
+  float2 us = mul2(mul2(SS, Sm), idS);
+  if (Sl == Ss || Sr == Ss) {  // a wave speed equal to the contact: that side's flux is its physical flux
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      if (Sl == Ss) Fs[k].x = F[k].x;
+      if (Sr == Ss) Fs[k].y = F[k].y;
+    }
+    if (Sl == Ss) us.x = un.x;
+    if (Sr == Ss) us.y = un.y;
+  }
+#pragma unroll
+  for (int k = 0; k < 6; ++k) Fhat[k] = fmaf(wl, Fs[k].x, wr * Fs[k].y);
+  ustar = fmaf(wl, us.x, wr * us.y);
+}
+
 // One face from sweep-frame FP32 primitives of cells i-2..i+3 and their sound
 // speeds.  code_l / code_r: 0, 1, 2 for 5th, 3rd, 1st order.
 template <int NQ>

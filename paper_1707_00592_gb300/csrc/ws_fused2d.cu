@@ -207,8 +207,8 @@ template <int D, int R>
 __device__ __forceinline__ bool weno_item(const float* qb, const WenoParams& P, float& l5, float& r5) {
   float2 p[5];
   project_pairs<D, R>(qb, p);
-  float mn = fminf(fminf(fminf(p[0].x, p[1].x), fminf(p[2].x, p[2].y)), fminf(p[1].y, p[0].y));
-  float mx = fmaxf(fmaxf(fmaxf(p[0].x, p[1].x), fmaxf(p[2].x, p[2].y)), fmaxf(p[1].y, p[0].y));
+  float mn = fminf(fmin3(p[0].x, p[1].x, p[2].x), fmin3(p[2].y, p[1].y, p[0].y));
+  float mx = fmaxf(fmax3(p[0].x, p[1].x, p[2].x), fmax3(p[2].y, p[1].y, p[0].y));
   bool flat = mx - mn <= 1e-6f * fmaxf(fabsf(mx), fabsf(mn));
   float2 v = flat ? linear5_pair(p[0], p[1], p[2], p[3], p[4]) : weno5_pair(p[0], p[1], p[2], p[3], p[4], P);
   l5 = v.x;
@@ -556,38 +556,55 @@ __global__ void __launch_bounds__(NT, 2) k_stage2d(StageArgs a) {
     float c2 = c_bar * c_bar, rc = rho_bar * c_bar;
     float inv = frcp(c2 * rc);
     float ic2 = rc * inv, irc = c2 * inv;
-    float q[2][NQ];
-    int code[2];
+    float2 W[NQ], Q[NQ];  // (left, right) characteristics, then primitives
 #pragma unroll
-    for (int side = 0; side < 2; ++side) {
-      float wt[NQ];
+    for (int r = 0; r < NQ; ++r) W[r] = make_float2(wl[r], wr[r]);
+    back_project_pair(W, ic2, irc, Q);
+    int code[2] = {0, 0};
+    if (a.mood) {
+      float qs[2][NQ];
 #pragma unroll
-      for (int r = 0; r < NQ; ++r) wt[r] = side == 0 ? wl[r] : wr[r];
-      back_project<NQ>(wt, ic2, irc, q[side]);
-      code[side] = 0;
-      if (a.mood && !admissible<NQ>(q[side])) {
-        if (LEARNED && sm) atomicAdd(&a.lstat[0], 1.0f);
-        const float* qb = &S.q[0][hy][hx];
-        if (isx)
-          weno_side3<0>(qb, side, a.P, wt);
-        else
-          weno_side3<1>(qb, side, a.P, wt);
-        back_project<NQ>(wt, ic2, irc, q[side]);
-        code[side] = 1;
-        if (!admissible<NQ>(q[side])) {
-          int yy = side == 0 ? ya : yb, xx = side == 0 ? xa : xb;
-          q[side][0] = S.q[0][yy][xx];
-          q[side][1] = S.q[un][yy][xx];
-          q[side][2] = S.q[ut][yy][xx];
-          q[side][3] = S.q[3][yy][xx];
-          q[side][4] = S.q[4][yy][xx];
-          q[side][5] = S.q[5][yy][xx];
-          code[side] = 2;
+      for (int r = 0; r < NQ; ++r) {
+        qs[0][r] = Q[r].x;
+        qs[1][r] = Q[r].y;
+      }
+      const bool ok0 = admissible<NQ>(qs[0]), ok1 = admissible<NQ>(qs[1]);
+      if (!ok0 || !ok1) {  // MOOD cascade of the failing side(s): rare
+#pragma unroll 1
+        for (int side = 0; side < 2; ++side) {
+          if (side == 0 ? ok0 : ok1) continue;
+          if (LEARNED && sm) atomicAdd(&a.lstat[0], 1.0f);
+          float wt[NQ];
+          const float* qb = &S.q[0][hy][hx];
+          if (isx)
+            weno_side3<0>(qb, side, a.P, wt);
+          else
+            weno_side3<1>(qb, side, a.P, wt);
+          float q3[NQ];
+          back_project<NQ>(wt, ic2, irc, q3);
+          code[side] = 1;
+          if (!admissible<NQ>(q3)) {
+            int yy = side == 0 ? ya : yb, xx = side == 0 ? xa : xb;
+            q3[0] = S.q[0][yy][xx];
+            q3[1] = S.q[un][yy][xx];
+            q3[2] = S.q[ut][yy][xx];
+            q3[3] = S.q[3][yy][xx];
+            q3[4] = S.q[4][yy][xx];
+            q3[5] = S.q[5][yy][xx];
+            code[side] = 2;
+          }
+#pragma unroll
+          for (int r = 0; r < NQ; ++r) {
+            if (side == 0)
+              Q[r].x = q3[r];
+            else
+              Q[r].y = q3[r];
+          }
         }
       }
     }
     float Fh[NQ], us;
-    hllc<NQ>(q[0], q[1], Fh, us);
+    hllc_pair(Q, Fh, us);
     uint8_t mb = (uint8_t)(code[0] | (code[1] << 2));
     if (isx) {
       int j = hy - NG, i = hx;
