@@ -52,11 +52,19 @@ constexpr int NFRAG1 = 2 * 4, NFRAG2 = 2 * 4, NFRAG3 = 2;  // (k-step, n-tile) p
 constexpr int NFRAG = NFRAG1 + NFRAG2 + NFRAG3;
 constexpr int NMT = (NF + 15) / 16;  // 16-face M tiles
 
+template <bool LEARNED>
 struct Smem {
   float q[NQ + 1][HY][HX];        // primitives + sound speed of tile and halo
-  __nv_bfloat16 feat[NF][24];     // learned gate inputs (read before the reconstruction)
   float fx[NQ + 1][TY][TX + 1];   // x-face fluxes (global field order) + face velocity
   float fy[NQ + 1][TY + 1][TX];   // y-face fluxes + face velocity
+  union {
+    struct {                      // plain kernel: this tile's own cells, for phase C
+      double u[NQ][TY][TX];       // stage 2: FP64 state, copied in asynchronously from the start
+      float k[NQ][TY][TX];        // stages 1, 2: accumulated increments (kept from the phase-A loads)
+      float v[NQ][TY][TX];        // stage 2: FP32 image of U^n (kept from the phase-A loads)
+    } own;
+    __nv_bfloat16 feat[NF][24];   // learned kernel: gate inputs (read before the reconstruction)
+  };
   unsigned long long red[NT / 32];  // per-warp CFL maxima
   float dt;                         // the step, broadcast from thread 0
 };
@@ -172,26 +180,29 @@ __device__ __forceinline__ void project6(const float* qb, float (&w)[6]) {
   }
 }
 
+// Per-face averages of the characteristic projection: rho c and -1/c^2 at
+// the face (arithmetic means of cells i and i+1), shared by all variables.
+struct FaceAvg {
+  float rc;    // rho_bar c_bar
+  float mic2;  // -1 / c_bar^2
+};
+
 // Characteristic variable R of the six stencil cells as mirrored pairs
 // p[k] = (w_k, w_{5-k}), k = 0..4: the .x lanes are the left stencil
 // w_0..w_4, the .y lanes the right stencil w_5..w_1.
 template <int D, int R>
-__device__ __forceinline__ void project_pairs(const float* qb, float2 (&p)[5]) {
+__device__ __forceinline__ void project_pairs(const float* qb, const FaceAvg& fa, float2 (&p)[5]) {
   constexpr int ST = D == 0 ? 1 : HX;
   constexpr int FS = HY * HX;
   constexpr int UN = D == 0 ? 1 : 2, UT = D == 0 ? 2 : 1;
   auto cell = [&](int F, int k) { return make_float2(qb[F * FS + k * ST], qb[F * FS + (5 - k) * ST]); };
   if (R == 0 || R == NQ - 1) {
-    float rho_bar = 0.5f * (qb[2 * ST] + qb[3 * ST]);
-    float c_bar = 0.5f * (qb[6 * FS + 2 * ST] + qb[6 * FS + 3 * ST]);
-    float2 rc = f2(R == 0 ? -(rho_bar * c_bar) : rho_bar * c_bar);
+    float2 rc = f2(R == 0 ? -fa.rc : fa.rc);
 #pragma unroll
     for (int k = 0; k < 5; ++k) p[k] = mul2(f2(0.5f), fma2(rc, cell(UN, k), cell(3, k)));
   } else if (R == 1) {
-    float c_bar = 0.5f * (qb[6 * FS + 2 * ST] + qb[6 * FS + 3 * ST]);
-    float2 mic2 = f2(-frcp(c_bar * c_bar));
 #pragma unroll
-    for (int k = 0; k < 5; ++k) p[k] = fma2(mic2, cell(3, k), cell(0, k));
+    for (int k = 0; k < 5; ++k) p[k] = fma2(f2(fa.mic2), cell(3, k), cell(0, k));
   } else {
     constexpr int F = R == 2 ? UT : R + 1;  // shear, Gamma, Pi
 #pragma unroll
@@ -202,18 +213,21 @@ __device__ __forceinline__ void project_pairs(const float* qb, float2 (&p)[5]) {
 // 5th-order reconstruction of variable R on both sides of a face.  A
 // stencil flat to 1e-6 of its magnitude (a few FP32 ulps: rounding noise)
 // takes the linear weights, from which WENO-IS differs there by less than
-// the stencil's range; elsewhere WENO-IS.  Returns whether it was flat.
+// the stencil's range; elsewhere WENO-IS.
 template <int D, int R>
-__device__ __forceinline__ bool weno_item(const float* qb, const WenoParams& P, float& l5, float& r5) {
+__device__ __forceinline__ void weno_item(const float* qb, const FaceAvg& fa, const WenoParams& P, float& l5,
+                                          float& r5) {
   float2 p[5];
-  project_pairs<D, R>(qb, p);
+  project_pairs<D, R>(qb, fa, p);
   float mn = fminf(fmin3(p[0].x, p[1].x, p[2].x), fmin3(p[2].y, p[1].y, p[0].y));
   float mx = fmaxf(fmax3(p[0].x, p[1].x, p[2].x), fmax3(p[2].y, p[1].y, p[0].y));
-  bool flat = mx - mn <= 1e-6f * fmaxf(fabsf(mx), fabsf(mn));
-  float2 v = flat ? linear5_pair(p[0], p[1], p[2], p[3], p[4]) : weno5_pair(p[0], p[1], p[2], p[3], p[4], P);
+  float2 v;
+  if (mx - mn <= 1e-6f * fmaxf(fabsf(mx), fabsf(mn)))
+    v = linear5_pair(p[0], p[1], p[2], p[3], p[4]);
+  else
+    v = weno5_pair(p[0], p[1], p[2], p[3], p[4], P);
   l5 = v.x;
   r5 = v.y;
-  return flat;
 }
 
 // 3rd-order reconstruction (d3 = d4 = 0) of all variables of one side:
@@ -290,19 +304,27 @@ __device__ __forceinline__ void gate_features(const float* qb, __nv_bfloat16* ou
 
 // 5th-order linear-weight reconstruction of variable R on both sides
 template <int D, int R>
-__device__ __forceinline__ void linear_item(const float* qb, float& l5, float& r5) {
+__device__ __forceinline__ void linear_item(const float* qb, const FaceAvg& fa, float& l5, float& r5) {
   float2 p[5];
-  project_pairs<D, R>(qb, p);
+  project_pairs<D, R>(qb, fa, p);
   float2 v = linear5_pair(p[0], p[1], p[2], p[3], p[4]);
   l5 = v.x;
   r5 = v.y;
 }
 
+// Asynchronous 8-byte global -> shared copy (holds no register while in flight)
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+  unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 template <bool LEARNED>
 __global__ void __launch_bounds__(NT, 2) k_stage2d(StageArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  Smem& S = *reinterpret_cast<Smem*>(smem_raw);
-  SmemGate& SG = *reinterpret_cast<SmemGate*>(smem_raw + sizeof(Smem));
+  Smem<LEARNED>& S = *reinterpret_cast<Smem<LEARNED>*>(smem_raw);
+  SmemGate& SG = *reinterpret_cast<SmemGate*>(smem_raw + sizeof(Smem<LEARNED>));
   if (a.run_if && *a.run_if == 0) return;  // a conditional redo that is not needed
   const GridDev& g = a.g;
   const int nx = g.n[0], ny = g.n[1];
@@ -317,6 +339,19 @@ __global__ void __launch_bounds__(NT, 2) k_stage2d(StageArgs a) {
     }
     __syncthreads();
   }
+  // plain kernel, stage 2: the own cells' FP64 state, needed only in phase C,
+  // is copied into shared memory while phases A and B run
+  constexpr bool CACHE = !LEARNED;
+  if (CACHE && a.stage == 2) {
+    for (int c = tid; c < TX * TY; c += NT) {
+      int j = c / TX, i = c - j * TX;
+      if (x0 + i >= nx || y0 + j >= ny) continue;
+      int64_t gi = (int64_t)(NG + y0 + j) * P0 + (NG + x0 + i);
+#pragma unroll
+      for (int m = 0; m < NQ; ++m) cp_async8(&S.own.u[m][j][i], &a.U[m * N + gi]);
+    }
+    cp_async_commit();
+  }
   const float dt = (a.stage == 1 || a.stage == 2) ? S.dt : 0.0f;
   const float coef = a.stage == 0 ? 0.0f : (a.stage == 1 ? dt : 0.25f * dt);
   float lam_max = 0.0f;
@@ -326,8 +361,9 @@ __global__ void __launch_bounds__(NT, 2) k_stage2d(StageArgs a) {
   // before any of them is used, so that a CTA has its whole halo in flight.
   {
     float ld[HPT][NQ];
+    float rk[HPT][NQ], rv[HPT][NQ];  // stages 1, 2: increment and FP32 image as loaded
     int hh[HPT];
-    bool flx[HPT], fly[HPT];
+    bool flx[HPT], fly[HPT], own[HPT];
 #pragma unroll
     for (int t = 0; t < HPT; ++t) {
       int h = tid + t * NT;
@@ -350,24 +386,42 @@ __global__ void __launch_bounds__(NT, 2) k_stage2d(StageArgs a) {
         ld[t][3] = f64_to_f32(U[3 * N + i] - U[5 * N + i]);  // E - Pi in FP64
         ld[t][4] = f64_to_f32(U[4 * N + i]);
         ld[t][5] = f64_to_f32(U[5 * N + i]);
-        bool own = a.stage == 0 && hx >= NG && hx < NG + TX && hy >= NG && hy < NG + TY && !outx && !outy;
-        if (LEARNED && own) {
+        own[t] = a.stage == 0 && hx >= NG && hx < NG + TX && hy >= NG && hy < NG + TY && !outx && !outy;
+        if (LEARNED && own[t]) {
 #pragma unroll
           for (int m = 0; m < NQ; ++m) a.Ubackup[m * N + i] = U[m * N + i];
         }
-        if (own) {
+        if (own[t]) {
 #pragma unroll
           for (int m = 0; m < NQ; ++m) a.U32[m * N + i] = ld[t][m];
         }
       } else {
-        const float* V = a.U32;
-        const float* K = a.Kin;
-        ld[t][0] = fmaf(coef, K[i], V[i]);
-        ld[t][1] = fmaf(coef, K[N + i], V[N + i]);
-        ld[t][2] = fmaf(coef, K[2 * N + i], V[2 * N + i]);
-        ld[t][3] = fmaf(coef, K[3 * N + i] - K[5 * N + i], V[3 * N + i]);
-        ld[t][4] = fmaf(coef, K[4 * N + i], V[4 * N + i]);
-        ld[t][5] = fmaf(coef, K[5 * N + i], V[5 * N + i]);
+        own[t] = hx >= NG && hx < NG + TX && hy >= NG && hy < NG + TY && !outx && !outy;
+#pragma unroll
+        for (int m = 0; m < NQ; ++m) {
+          rk[t][m] = __ldg(&a.Kin[m * N + i]);
+          rv[t][m] = __ldg(&a.U32[m * N + i]);
+        }
+      }
+    }
+    if (a.stage == 1 || a.stage == 2) {
+#pragma unroll
+      for (int t = 0; t < HPT; ++t) {
+        if (hh[t] < 0) continue;
+        ld[t][0] = fmaf(coef, rk[t][0], rv[t][0]);
+        ld[t][1] = fmaf(coef, rk[t][1], rv[t][1]);
+        ld[t][2] = fmaf(coef, rk[t][2], rv[t][2]);
+        ld[t][3] = fmaf(coef, rk[t][3] - rk[t][5], rv[t][3]);
+        ld[t][4] = fmaf(coef, rk[t][4], rv[t][4]);
+        ld[t][5] = fmaf(coef, rk[t][5], rv[t][5]);
+        if (CACHE && own[t]) {  // phase C reads these instead of global memory
+          int j = hh[t] / HX - NG, i = hh[t] % HX - NG;
+#pragma unroll
+          for (int m = 0; m < NQ; ++m) {
+            S.own.k[m][j][i] = rk[t][m];
+            if (a.stage == 2) S.own.v[m][j][i] = rv[t][m];
+          }
+        }
       }
     }
 #pragma unroll
@@ -510,6 +564,14 @@ __global__ void __launch_bounds__(NT, 2) k_stage2d(StageArgs a) {
     const int qo = hy * HX + hx;  // stencil cell 0 in the halo tile
     const bool sm = LEARNED && SG.smooth[f];
     float wl[NQ], wr[NQ];  // reconstructed characteristics, left and right
+    const int un = isx ? 1 : 2, ut = isx ? 2 : 1;
+    int ya = hy + 2 * dhy, xa = hx + 2 * dhx, yb = hy + 3 * dhy, xb = hx + 3 * dhx;
+    float rho_bar = 0.5f * (S.q[0][ya][xa] + S.q[0][yb][xb]);
+    float c_bar = 0.5f * (S.q[6][ya][xa] + S.q[6][yb][xb]);
+    float c2 = c_bar * c_bar, rc = rho_bar * c_bar;
+    float inv = frcp(c2 * rc);
+    float ic2 = rc * inv, irc = c2 * inv;  // 1/c^2, 1/(rho c)
+    const FaceAvg fa{rc, -ic2};
     if (LEARNED) {
       nval += 1.0f;
       nsm += sm ? 1.0f : 0.0f;
@@ -520,16 +582,16 @@ __global__ void __launch_bounds__(NT, 2) k_stage2d(StageArgs a) {
       bool lin = LEARNED && R != 2 && sm; /* shear: always WENO-IS */     \
       if (lin) {                                                          \
         if (isx)                                                          \
-          linear_item<0, R>(q0 + qo, l5, r5);                             \
+          linear_item<0, R>(q0 + qo, fa, l5, r5);                             \
         else                                                              \
-          linear_item<1, R>(q0 + qo, l5, r5);                             \
+          linear_item<1, R>(q0 + qo, fa, l5, r5);                             \
       }                                                                   \
       if (!lin || drift) {                                                \
         float fl, fr;                                                     \
         if (isx)                                                          \
-          weno_item<0, R>(q0 + qo, a.P, fl, fr);                          \
+          weno_item<0, R>(q0 + qo, fa, a.P, fl, fr);                          \
         else                                                              \
-          weno_item<1, R>(q0 + qo, a.P, fl, fr);                          \
+          weno_item<1, R>(q0 + qo, fa, a.P, fl, fr);                          \
         if (lin) {                                                        \
           dnum += fabsf(l5 - fl) + fabsf(r5 - fr);                        \
           dden += fabsf(fl) + fabsf(fr);                                  \
@@ -549,13 +611,6 @@ __global__ void __launch_bounds__(NT, 2) k_stage2d(StageArgs a) {
     WS_B1(5)
 #undef WS_B1
 
-    const int un = isx ? 1 : 2, ut = isx ? 2 : 1;
-    int ya = hy + 2 * dhy, xa = hx + 2 * dhx, yb = hy + 3 * dhy, xb = hx + 3 * dhx;
-    float rho_bar = 0.5f * (S.q[0][ya][xa] + S.q[0][yb][xb]);
-    float c_bar = 0.5f * (S.q[6][ya][xa] + S.q[6][yb][xb]);
-    float c2 = c_bar * c_bar, rc = rho_bar * c_bar;
-    float inv = frcp(c2 * rc);
-    float ic2 = rc * inv, irc = c2 * inv;
     float2 W[NQ], Q[NQ];  // (left, right) characteristics, then primitives
 #pragma unroll
     for (int r = 0; r < NQ; ++r) W[r] = make_float2(wl[r], wr[r]);
@@ -639,6 +694,7 @@ __global__ void __launch_bounds__(NT, 2) k_stage2d(StageArgs a) {
       SG.red[3][tid >> 5] = nval;
     }
   }
+  if (CACHE && a.stage == 2) cp_async_wait_all();  // own FP64 state, visible after the barrier
   __syncthreads();
   if (LEARNED && tid < 4) {
     float sum = 0.0f;
@@ -646,41 +702,59 @@ __global__ void __launch_bounds__(NT, 2) k_stage2d(StageArgs a) {
     if (tid >= 2 || drift) atomicAdd(&a.lstat[1 + tid], sum);
   }
 
-  // ---- phase C: flux divergence and RK stage ----
-  const float idx = a.idx, idy = a.idy;
+  // ---- phase C: flux divergence and RK stage (variables in pairs) ----
+  const float2 idx = f2(a.idx), idy = f2(a.idy);
   for (int c = tid; c < TX * TY; c += NT) {
     int j = c / TX, i = c - j * TX;
     int gx = x0 + i, gy = y0 + j;
     if (gx >= nx || gy >= ny) continue;
     int64_t gi = (int64_t)(NG + gy) * P0 + (NG + gx);
-    float div_u = (S.fx[NQ][j][i + 1] - S.fx[NQ][j][i]) * idx + (S.fy[NQ][j + 1][i] - S.fy[NQ][j][i]) * idy;
-    float inc[NQ];
+    float div_u = (S.fx[NQ][j][i + 1] - S.fx[NQ][j][i]) * a.idx + (S.fy[NQ][j + 1][i] - S.fy[NQ][j][i]) * a.idy;
+    float2 inc[NQ / 2];
 #pragma unroll
-    for (int m = 0; m < NQ; ++m) {
-      float L = -(S.fx[m][j][i + 1] - S.fx[m][j][i]) * idx;
-      L = fmaf(-(S.fy[m][j + 1][i] - S.fy[m][j][i]), idy, L);
-      if (m >= 4) L = fmaf(S.q[m][j + NG][i + NG], div_u, L);
-      inc[m] = L;
+    for (int k = 0; k < NQ / 2; ++k) {
+      const int m = 2 * k;
+      float2 L = mul2(sub2(make_float2(S.fx[m][j][i], S.fx[m + 1][j][i]),
+                           make_float2(S.fx[m][j][i + 1], S.fx[m + 1][j][i + 1])), idx);
+      L = fma2(sub2(make_float2(S.fy[m][j][i], S.fy[m + 1][j][i]), make_float2(S.fy[m][j + 1][i], S.fy[m + 1][j + 1][i])),
+               idy, L);
+      if (m >= 4) L = fma2(make_float2(S.q[m][j + NG][i + NG], S.q[m + 1][j + NG][i + NG]), f2(div_u), L);
+      inc[k] = L;
     }
+    auto kin = [&](int m) { return CACHE ? S.own.k[m][j][i] : a.Kin[m * N + gi]; };
     if (a.stage == 0) {
 #pragma unroll
-      for (int m = 0; m < NQ; ++m) a.Kout[m * N + gi] = inc[m];
+      for (int k = 0; k < NQ / 2; ++k) {
+        a.Kout[2 * k * N + gi] = inc[k].x;
+        a.Kout[(2 * k + 1) * N + gi] = inc[k].y;
+      }
     } else if (a.stage == 1) {
 #pragma unroll
-      for (int m = 0; m < NQ; ++m) a.Kout[m * N + gi] = a.Kin[m * N + gi] + inc[m];
+      for (int k = 0; k < NQ / 2; ++k) {
+        float2 K1 = add2(make_float2(kin(2 * k), kin(2 * k + 1)), inc[k]);
+        a.Kout[2 * k * N + gi] = K1.x;
+        a.Kout[(2 * k + 1) * N + gi] = K1.y;
+      }
     } else {
       // this cell's U^n is read only here, by this thread, so U is updated in place
       float d[NQ];
 #pragma unroll
+      for (int k = 0; k < NQ / 2; ++k) {
+        float2 dd = mul2(f2(dt), fma2(f2(1.0f / 6.0f), make_float2(kin(2 * k), kin(2 * k + 1)),
+                                      mul2(f2(2.0f / 3.0f), inc[k])));
+        d[2 * k] = dd.x;
+        d[2 * k + 1] = dd.y;
+      }
+#pragma unroll
       for (int m = 0; m < NQ; ++m) {
-        d[m] = dt * fmaf(1.0f / 6.0f, a.Kin[m * N + gi], (2.0f / 3.0f) * inc[m]);
-        a.U[m * N + gi] = a.U[m * N + gi] + f32_to_f64(d[m]);  // FP64 accumulation
+        double u = CACHE ? S.own.u[m][j][i] : a.U[m * N + gi];
+        a.U[m * N + gi] = u + f32_to_f64(d[m]);  // FP64 accumulation
       }
       // admissibility of the new state (rho > 0, Gamma > 0, (Gamma+1) p + Pi > 0)
       // from its FP32 image: a diagnostic, not part of the update
-      const float* V = a.U32;
-      float rho = V[gi] + d[0], mu = V[N + gi] + d[1], mv = V[2 * N + gi] + d[2];
-      float eint = V[3 * N + gi] + (d[3] - d[5]), Gam = V[4 * N + gi] + d[4], Pi = V[5 * N + gi] + d[5];
+      auto v = [&](int m) { return CACHE ? S.own.v[m][j][i] : a.U32[m * N + gi]; };
+      float rho = v(0) + d[0], mu = v(1) + d[1], mv = v(2) + d[2];
+      float eint = v(3) + (d[3] - d[5]), Gam = v(4) + d[4], Pi = v(5) + d[5];
       float pe = fmaf(-0.5f, (mu * mu + mv * mv) * frcp(rho), eint);  // Gamma p
       bool ok = rho > 0.0f && Gam > 0.0f && fmaf(Gam + 1.0f, pe * frcp(Gam), Pi) > 0.0f;
       if (!ok) atomicAdd(a.nbad, 1ULL);
@@ -728,14 +802,14 @@ void launch_restore(const int* redo, const double* src, double* dst, int64_t n, 
   k_restore<<<152 * 4, 256, 0, s>>>(redo, src, dst, n);
 }
 
-int fused2d_smem_bytes() { return (int)(sizeof(Smem) + sizeof(SmemGate)); }
+int fused2d_smem_bytes() { return (int)(sizeof(Smem<true>) + sizeof(SmemGate)); }
 
 cudaError_t fused2d_prepare() {
   cudaError_t e = cudaFuncSetAttribute(k_stage2d<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)sizeof(Smem));
+                                       (int)sizeof(Smem<false>));
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_stage2d<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)(sizeof(Smem) + sizeof(SmemGate)));
+                              (int)(sizeof(Smem<true>) + sizeof(SmemGate)));
 }
 
 void launch_stage2d(const GridDev& g, int stage, double* U, float* U32, const float* Kin, float* Kout,
@@ -769,7 +843,7 @@ void launch_stage2d(const GridDev& g, int stage, double* U, float* U32, const fl
     a.drift_tile = gate->drift_tile;
     a.Ubackup = gate->Ubackup;
     a.lstat = gate->lstat;
-    k_stage2d<true><<<grid, NT, sizeof(Smem) + sizeof(SmemGate), s>>>(a);
+    k_stage2d<true><<<grid, NT, sizeof(Smem<true>) + sizeof(SmemGate), s>>>(a);
   } else {
     a.mlp_frag = nullptr;
     a.mlp_bias = nullptr;
@@ -777,7 +851,7 @@ void launch_stage2d(const GridDev& g, int stage, double* U, float* U32, const fl
     a.drift_tile = -1;
     a.Ubackup = nullptr;
     a.lstat = nullptr;
-    k_stage2d<false><<<grid, NT, sizeof(Smem), s>>>(a);
+    k_stage2d<false><<<grid, NT, sizeof(Smem<false>), s>>>(a);
   }
 }
 
