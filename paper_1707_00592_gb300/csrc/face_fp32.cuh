@@ -366,29 +366,49 @@ __device__ __forceinline__ float fmax3(float a, float b, float c) {
   return r;
 }
 
-// back_project<6> of both sides at once: W[r] = (left, right) characteristic r
-__device__ __forceinline__ void back_project_pair(const float2 (&W)[6], float ic2, float irc, float2 (&Q)[6]) {
-  float2 s05 = add2(W[0], W[5]);
-  Q[0] = fma2(f2(ic2), s05, W[1]);
-  Q[1] = mul2(f2(irc), sub2(W[5], W[0]));
-  Q[2] = W[2];
-  Q[3] = s05;
-  Q[4] = W[3];
-  Q[5] = W[4];
+// back_project<NQ> of both sides at once: W[r] = (left, right) characteristic r
+template <int NQ>
+__device__ __forceinline__ void back_project_pair(const float2 (&W)[NQ], float ic2, float irc, float2 (&Q)[NQ]) {
+  constexpr int NT = NQ - 5, IP = 2 + NT;
+  float2 s0 = add2(W[0], W[NQ - 1]);
+  Q[0] = fma2(f2(ic2), s0, W[1]);
+  Q[1] = mul2(f2(irc), sub2(W[NQ - 1], W[0]));
+#pragma unroll
+  for (int t = 0; t < NT; ++t) Q[2 + t] = W[2 + t];
+  Q[IP] = s0;
+  Q[IP + 1] = W[IP];
+  Q[IP + 2] = W[IP + 1];
 }
 
-// hllc<6> (two dimensions: rho, u_n, u_t, p, Gamma, Pi) with the states of
-// both sides in the lanes of Q (x: left, y: right).  The per-side quantities
-// (conserved state, physical flux, sound speed, star flux) are computed for
-// both sides in paired instructions; the wave-speed estimates and the
-// contact speed are scalar.
-__device__ __forceinline__ void hllc_pair(const float2 (&Q)[6], float* Fhat, float& ustar) {
-  const float2 rho = Q[0], un = Q[1], ut = Q[2], p = Q[3], Gam = Q[4], Pi = Q[5];
-  float2 usq = fma2(ut, ut, mul2(un, un));
+// hllc<NQ> with the states of both sides in the lanes of Q (x: left, y:
+// right).  The per-side quantities (conserved state, physical flux, sound
+// speed, star flux) are computed for both sides in paired instructions; the
+// wave-speed estimates and the contact speed are scalar.
+template <int NQ>
+__device__ __forceinline__ void hllc_pair(const float2 (&Q)[NQ], float* Fhat, float& ustar) {
+  constexpr int NT = NQ - 5;
+  const float2 rho = Q[0], un = Q[1], p = Q[2 + NT], Gam = Q[3 + NT], Pi = Q[4 + NT];
+  float2 usq = mul2(un, un);
+#pragma unroll
+  for (int t = 0; t < NT; ++t) usq = fma2(Q[2 + t], Q[2 + t], usq);
   float2 E = fma2(mul2(f2(0.5f), rho), usq, fma2(Gam, p, Pi));
   float2 mn = mul2(rho, un);
-  float2 U[6] = {rho, mn, mul2(rho, ut), E, Gam, Pi};
-  float2 F[6] = {mn, fma2(mn, un, p), mul2(mn, ut), mul2(add2(E, p), un), mul2(Gam, un), mul2(Pi, un)};
+  float2 U[NQ], F[NQ];
+  U[0] = rho;
+  U[1] = mn;
+  F[0] = mn;
+  F[1] = fma2(mn, un, p);
+#pragma unroll
+  for (int t = 0; t < NT; ++t) {
+    U[2 + t] = mul2(rho, Q[2 + t]);
+    F[2 + t] = mul2(mn, Q[2 + t]);
+  }
+  U[2 + NT] = E;
+  F[2 + NT] = mul2(add2(E, p), un);
+  U[3 + NT] = Gam;
+  F[3 + NT] = mul2(Gam, un);
+  U[4 + NT] = Pi;
+  F[4 + NT] = mul2(Pi, un);
   float2 c2 = mul2(fma2(add2(Gam, f2(1.0f)), p, Pi), rcp2(mul2(Gam, rho)));
   float2 cc = make_float2(fsqrt(c2.x), fsqrt(c2.y));
   float sl = fsqrt(rho.x), sr = fsqrt(rho.y);
@@ -409,18 +429,18 @@ __device__ __forceinline__ void hllc_pair(const float2 (&Q)[6], float* Fhat, flo
   float2 Pk = fma2(m, sub2(SS, un), p);
   float2 SP = mul2(S, Pk);
   float2 idS = rcp2(sub2(S, SS));
-  float2 Fs[6];
+  float2 Fs[NQ];
 #pragma unroll
-  for (int k = 0; k < 6; ++k) {
+  for (int k = 0; k < NQ; ++k) {
     float2 t = mul2(SS, fma2(S, U[k], mul2(F[k], f2(-1.0f))));
     if (k == 1) t = add2(t, SP);
-    if (k == 3) t = fma2(SP, SS, t);
+    if (k == 2 + NT) t = fma2(SP, SS, t);
     Fs[k] = mul2(t, idS);
   }
   float2 us = mul2(mul2(SS, Sm), idS);
   if (Sl == Ss || Sr == Ss) {  // a wave speed equal to the contact: that side's flux is its physical flux
 #pragma unroll
-    for (int k = 0; k < 6; ++k) {
+    for (int k = 0; k < NQ; ++k) {
       if (Sl == Ss) Fs[k].x = F[k].x;
       if (Sr == Ss) Fs[k].y = F[k].y;
     }
@@ -428,7 +448,7 @@ __device__ __forceinline__ void hllc_pair(const float2 (&Q)[6], float* Fhat, flo
     if (Sr == Ss) us.y = un.y;
   }
 #pragma unroll
-  for (int k = 0; k < 6; ++k) Fhat[k] = fmaf(wl, Fs[k].x, wr * Fs[k].y);
+  for (int k = 0; k < NQ; ++k) Fhat[k] = fmaf(wl, Fs[k].x, wr * Fs[k].y);
   ustar = fmaf(wl, us.x, wr * us.y);
 }
 

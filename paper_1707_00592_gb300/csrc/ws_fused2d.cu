@@ -122,18 +122,19 @@ __device__ __forceinline__ int map_bc(int x, int n, int lo, int hi, bool& flip) 
 }
 
 // halo-tile coordinates of stencil cell k (0..5 = i-2..i+3) of face f, and
-// whether the face is an x face; false if the face lies outside the grid
-// x faces are numbered row by row for tile faces 0..TX-1 (warp = one row,
-// no shared-memory bank conflicts), then the TY right-most faces.
+// whether the face is an x face; false if the face lies outside the grid.
+// Faces are numbered so that every 32-face chunk (a warp's share) is one row
+// of one orientation: x faces 0..TX-1 of the TY rows, then the TY+1 rows of y
+// faces, then the TY right-most x faces.
 __device__ __forceinline__ bool face_geom(int f, int x0, int y0, int nx, int ny, bool& isx, int& hx, int& hy,
                                           int& dhx, int& dhy) {
-  if (f < NFX) {
+  if (f < TX * TY || f >= TX * TY + NFY) {
     int j, i;
     if (f < TX * TY) {
       j = f / TX;
       i = f - j * TX;
     } else {
-      j = f - TX * TY;
+      j = f - TX * TY - NFY;
       i = TX;
     }
     isx = true;
@@ -143,7 +144,7 @@ __device__ __forceinline__ bool face_geom(int f, int x0, int y0, int nx, int ny,
     dhy = 0;
     return (x0 + i - 1 <= nx - 1) && (y0 + j < ny);
   }
-  int ff = f - NFX;
+  int ff = f - TX * TY;
   int j = ff / TX, i = ff - j * TX;
   isx = false;
   hx = i + NG;
@@ -187,26 +188,34 @@ struct FaceAvg {
   float mic2;  // -1 / c_bar^2
 };
 
+// Orientation of a face, resolved at run time so that x and y faces share one
+// copy of the reconstruction code: offsets of the six stencil cells in the
+// halo tile and the normal / tangential velocity fields.
+struct FaceGeo {
+  int off[6];
+  int un, ut;
+};
+
 // Characteristic variable R of the six stencil cells as mirrored pairs
 // p[k] = (w_k, w_{5-k}), k = 0..4: the .x lanes are the left stencil
 // w_0..w_4, the .y lanes the right stencil w_5..w_1.
-template <int D, int R>
-__device__ __forceinline__ void project_pairs(const float* qb, const FaceAvg& fa, float2 (&p)[5]) {
-  constexpr int ST = D == 0 ? 1 : HX;
+template <int R>
+__device__ __forceinline__ void project_pairs(const float* qb, const FaceGeo& fg, const FaceAvg& fa, float2 (&p)[5]) {
   constexpr int FS = HY * HX;
-  constexpr int UN = D == 0 ? 1 : 2, UT = D == 0 ? 2 : 1;
-  auto cell = [&](int F, int k) { return make_float2(qb[F * FS + k * ST], qb[F * FS + (5 - k) * ST]); };
+  auto cell = [&](const float* b, int k) { return make_float2(b[fg.off[k]], b[fg.off[5 - k]]); };
   if (R == 0 || R == NQ - 1) {
     float2 rc = f2(R == 0 ? -fa.rc : fa.rc);
 #pragma unroll
-    for (int k = 0; k < 5; ++k) p[k] = mul2(f2(0.5f), fma2(rc, cell(UN, k), cell(3, k)));
+    for (int k = 0; k < 5; ++k) p[k] = mul2(f2(0.5f), fma2(rc, cell(qb + fg.un * FS, k), cell(qb + 3 * FS, k)));
   } else if (R == 1) {
 #pragma unroll
-    for (int k = 0; k < 5; ++k) p[k] = fma2(f2(fa.mic2), cell(3, k), cell(0, k));
-  } else {
-    constexpr int F = R == 2 ? UT : R + 1;  // shear, Gamma, Pi
+    for (int k = 0; k < 5; ++k) p[k] = fma2(f2(fa.mic2), cell(qb + 3 * FS, k), cell(qb, k));
+  } else if (R == 2) {  // shear
 #pragma unroll
-    for (int k = 0; k < 5; ++k) p[k] = cell(F, k);
+    for (int k = 0; k < 5; ++k) p[k] = cell(qb + fg.ut * FS, k);
+  } else {  // Gamma, Pi
+#pragma unroll
+    for (int k = 0; k < 5; ++k) p[k] = cell(qb + (R + 1) * FS, k);
   }
 }
 
@@ -214,11 +223,11 @@ __device__ __forceinline__ void project_pairs(const float* qb, const FaceAvg& fa
 // stencil flat to 1e-6 of its magnitude (a few FP32 ulps: rounding noise)
 // takes the linear weights, from which WENO-IS differs there by less than
 // the stencil's range; elsewhere WENO-IS.
-template <int D, int R>
-__device__ __forceinline__ void weno_item(const float* qb, const FaceAvg& fa, const WenoParams& P, float& l5,
-                                          float& r5) {
+template <int R>
+__device__ __forceinline__ void weno_item(const float* qb, const FaceGeo& fg, const FaceAvg& fa, const WenoParams& P,
+                                          float& l5, float& r5) {
   float2 p[5];
-  project_pairs<D, R>(qb, fa, p);
+  project_pairs<R>(qb, fg, fa, p);
   float mn = fminf(fmin3(p[0].x, p[1].x, p[2].x), fmin3(p[2].y, p[1].y, p[0].y));
   float mx = fmaxf(fmax3(p[0].x, p[1].x, p[2].x), fmax3(p[2].y, p[1].y, p[0].y));
   float2 v;
@@ -303,10 +312,11 @@ __device__ __forceinline__ void gate_features(const float* qb, __nv_bfloat16* ou
 }
 
 // 5th-order linear-weight reconstruction of variable R on both sides
-template <int D, int R>
-__device__ __forceinline__ void linear_item(const float* qb, const FaceAvg& fa, float& l5, float& r5) {
+template <int R>
+__device__ __forceinline__ void linear_item(const float* qb, const FaceGeo& fg, const FaceAvg& fa, float& l5,
+                                            float& r5) {
   float2 p[5];
-  project_pairs<D, R>(qb, fa, p);
+  project_pairs<R>(qb, fg, fa, p);
   float2 v = linear5_pair(p[0], p[1], p[2], p[3], p[4]);
   l5 = v.x;
   r5 = v.y;
@@ -572,6 +582,14 @@ __global__ void __launch_bounds__(NT, 2) k_stage2d(StageArgs a) {
     float inv = frcp(c2 * rc);
     float ic2 = rc * inv, irc = c2 * inv;  // 1/c^2, 1/(rho c)
     const FaceAvg fa{rc, -ic2};
+    FaceGeo fg;
+    {
+      const int st = isx ? 1 : HX;
+#pragma unroll
+      for (int k = 0; k < 6; ++k) fg.off[k] = k * st;
+      fg.un = un;
+      fg.ut = ut;
+    }
     if (LEARNED) {
       nval += 1.0f;
       nsm += sm ? 1.0f : 0.0f;
@@ -581,17 +599,11 @@ __global__ void __launch_bounds__(NT, 2) k_stage2d(StageArgs a) {
       float l5, r5;                                                       \
       bool lin = LEARNED && R != 2 && sm; /* shear: always WENO-IS */     \
       if (lin) {                                                          \
-        if (isx)                                                          \
-          linear_item<0, R>(q0 + qo, fa, l5, r5);                             \
-        else                                                              \
-          linear_item<1, R>(q0 + qo, fa, l5, r5);                             \
+        linear_item<R>(q0 + qo, fg, fa, l5, r5);                             \
       }                                                                   \
       if (!lin || drift) {                                                \
         float fl, fr;                                                     \
-        if (isx)                                                          \
-          weno_item<0, R>(q0 + qo, fa, a.P, fl, fr);                          \
-        else                                                              \
-          weno_item<1, R>(q0 + qo, fa, a.P, fl, fr);                          \
+        weno_item<R>(q0 + qo, fg, fa, a.P, fl, fr);                          \
         if (lin) {                                                        \
           dnum += fabsf(l5 - fl) + fabsf(r5 - fr);                        \
           dden += fabsf(fl) + fabsf(fr);                                  \
@@ -614,7 +626,7 @@ __global__ void __launch_bounds__(NT, 2) k_stage2d(StageArgs a) {
     float2 W[NQ], Q[NQ];  // (left, right) characteristics, then primitives
 #pragma unroll
     for (int r = 0; r < NQ; ++r) W[r] = make_float2(wl[r], wr[r]);
-    back_project_pair(W, ic2, irc, Q);
+    back_project_pair<NQ>(W, ic2, irc, Q);
     int code[2] = {0, 0};
     if (a.mood) {
       float qs[2][NQ];
@@ -659,7 +671,7 @@ __global__ void __launch_bounds__(NT, 2) k_stage2d(StageArgs a) {
       }
     }
     float Fh[NQ], us;
-    hllc_pair(Q, Fh, us);
+    hllc_pair<NQ>(Q, Fh, us);
     uint8_t mb = (uint8_t)(code[0] | (code[1] << 2));
     if (isx) {
       int j = hy - NG, i = hx;

@@ -157,18 +157,18 @@ __global__ void __launch_bounds__(NTH) k_tube_stage(TubeArgs a) {
 #pragma unroll
         for (int k = 0; k < 6; ++k) w[k] = S.q[fld][h0 + k];
       }
-      float mn = fminf(fminf(fminf(w[0], w[1]), fminf(w[2], w[3])), fminf(w[4], w[5]));
-      float mx = fmaxf(fmaxf(fmaxf(w[0], w[1]), fmaxf(w[2], w[3])), fmaxf(w[4], w[5]));
-      float l5, r5;
-      if (mx - mn <= 1e-6f * fmaxf(fabsf(mx), fabsf(mn))) {
-        l5 = linear5(w[0], w[1], w[2], w[3], w[4]);
-        r5 = linear5(w[5], w[4], w[3], w[2], w[1]);
-      } else {
-        l5 = weno_is(w[0], w[1], w[2], w[3], w[4], a.P, 5);
-        r5 = weno_is(w[5], w[4], w[3], w[2], w[1], a.P, 5);
-      }
-      S.w[0][r][f] = l5;
-      S.w[1][r][f] = r5;
+      float mn = fminf(fmin3(w[0], w[1], w[2]), fmin3(w[3], w[4], w[5]));
+      float mx = fmaxf(fmax3(w[0], w[1], w[2]), fmax3(w[3], w[4], w[5]));
+      // both sides at once: lanes (left, right) of the mirrored stencils
+      float2 p0 = make_float2(w[0], w[5]), p1 = make_float2(w[1], w[4]), p2 = make_float2(w[2], w[3]);
+      float2 p3 = make_float2(w[3], w[2]), p4 = make_float2(w[4], w[1]);
+      float2 v;
+      if (mx - mn <= 1e-6f * fmaxf(fabsf(mx), fabsf(mn)))
+        v = linear5_pair(p0, p1, p2, p3, p4);
+      else
+        v = weno5_pair(p0, p1, p2, p3, p4, a.P);
+      S.w[0][r][f] = v.x;
+      S.w[1][r][f] = v.y;
     }
     __syncthreads();
     // ---- phase B2 ----
@@ -179,48 +179,58 @@ __global__ void __launch_bounds__(NTH) k_tube_stage(TubeArgs a) {
       float c2 = c_bar * c_bar, rc = rho_bar * c_bar;
       float inv = frcp(c2 * rc);
       float ic2 = rc * inv, irc = c2 * inv;
-      float q[2][NQ];
-      int code[2];
+      float2 W[NQ], Q[NQ];  // (left, right) characteristics, then primitives
 #pragma unroll
-      for (int side = 0; side < 2; ++side) {
-        float wt[NQ];
+      for (int r = 0; r < NQ; ++r) W[r] = make_float2(S.w[0][r][f], S.w[1][r][f]);
+      back_project_pair<NQ>(W, ic2, irc, Q);
+      int code[2] = {0, 0};
+      if (a.mood) {
+        float qs[2][NQ];
 #pragma unroll
-        for (int r = 0; r < NQ; ++r) wt[r] = S.w[side][r][f];
-        back_project<NQ>(wt, ic2, irc, q[side]);
-        code[side] = 0;
-        if (a.mood && !admissible<NQ>(q[side])) {
-          // 3rd-order retry (d3 = d4 = 0) of this side
-          float qc[6][NQ], cc[6];
+        for (int r = 0; r < NQ; ++r) {
+          qs[0][r] = Q[r].x;
+          qs[1][r] = Q[r].y;
+        }
+        const bool ok0 = admissible<NQ>(qs[0]), ok1 = admissible<NQ>(qs[1]);
+        if (!ok0 || !ok1) {  // MOOD cascade of the failing side(s): rare
+#pragma unroll 1
+          for (int side = 0; side < 2; ++side) {
+            if (side == 0 ? ok0 : ok1) continue;
+            // 3rd-order retry (d3 = d4 = 0) of this side
+            float qc[6][NQ];
 #pragma unroll
-          for (int k = 0; k < 6; ++k) {
-            qc[k][0] = S.q[0][f + k];
-            qc[k][1] = S.q[1][f + k];
-            qc[k][2] = S.q[2][f + k];
-            qc[k][3] = S.q[3][f + k];
-            qc[k][4] = S.q[4][f + k];
-            cc[k] = S.q[5][f + k];
-          }
-          float hrc = 0.5f * rc;
+            for (int k = 0; k < 6; ++k) {
 #pragma unroll
-          for (int r = 0; r < NQ; ++r) {
-            float v[5];
+              for (int m = 0; m < NQ; ++m) qc[k][m] = S.q[m][f + k];
+            }
+            float hrc = 0.5f * rc, wt[NQ], q3[NQ];
 #pragma unroll
-            for (int k = 0; k < 5; ++k) v[k] = project<NQ>(qc[side == 0 ? k : 5 - k], r, hrc, ic2);
-            wt[r] = weno_is(v[0], v[1], v[2], v[3], v[4], a.P, 3);
-          }
-          (void)cc;
-          back_project<NQ>(wt, ic2, irc, q[side]);
-          code[side] = 1;
-          if (!admissible<NQ>(q[side])) {
-            int hh = side == 0 ? ha : hb;
+            for (int r = 0; r < NQ; ++r) {
+              float v[5];
 #pragma unroll
-            for (int m = 0; m < NQ; ++m) q[side][m] = S.q[m][hh];
-            code[side] = 2;
+              for (int k = 0; k < 5; ++k) v[k] = project<NQ>(qc[side == 0 ? k : 5 - k], r, hrc, ic2);
+              wt[r] = weno_is(v[0], v[1], v[2], v[3], v[4], a.P, 3);
+            }
+            back_project<NQ>(wt, ic2, irc, q3);
+            code[side] = 1;
+            if (!admissible<NQ>(q3)) {
+              int hh = side == 0 ? ha : hb;
+#pragma unroll
+              for (int m = 0; m < NQ; ++m) q3[m] = S.q[m][hh];
+              code[side] = 2;
+            }
+#pragma unroll
+            for (int r = 0; r < NQ; ++r) {
+              if (side == 0)
+                Q[r].x = q3[r];
+              else
+                Q[r].y = q3[r];
+            }
           }
         }
       }
       float Fh[NQ], us;
-      hllc<NQ>(q[0], q[1], Fh, us);
+      hllc_pair<NQ>(Q, Fh, us);
 #pragma unroll
       for (int m = 0; m < NQ; ++m) S.F[m][f] = Fh[m];
       S.F[NQ][f] = us;
