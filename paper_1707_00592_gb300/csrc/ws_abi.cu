@@ -81,6 +81,7 @@ void free_all(ws_ctx* c) {
   cudaFree(c->Q32);
   cudaFree(c->Ka);
   cudaFree(c->Kb);
+  cudaFree(c->Lp);
   for (int d = 0; d < 3; ++d) {
     cudaFree(c->Fh[d]);
     cudaFree(c->us[d]);
@@ -245,12 +246,17 @@ int step_device(ws_ctx* c, double* U, double dt) {
       if (!run_if) CK(c, cudaMemsetAsync(c->lmax, 0, sizeof(unsigned long long), c->stream));
       for (int s = 0; s < 3; ++s) {
         uint8_t* mb = c->mask + (int64_t)s * c->nmask;
-        KScope k(c, WS_K_FACE);
+        KScope k(c, WS_K_FACE, g.ndim == 3 ? 2 : 1);
         const float* Kin = s == 1 ? c->Ka : c->Kb;
         float* Kout = s == 0 ? c->Ka : c->Kb;
-        launch_stage2d(g, s, U, c->Q32, Kin, Kout, dt, c->opts.cfl, c->lmax, c->dt_dev, mb + c->mask_off[0],
-                       mb + c->mask_off[1], (float)c->opts.eps, c->opts.mood, c->opts.weights, c->nbad, gate,
-                       run_if, c->stream);
+        if (g.ndim == 3)
+          launch_stage3d(g, s, U, c->Q32, Kin, Kout, c->Lp, dt, c->opts.cfl, c->lmax, c->dt_dev, mb + c->mask_off[0],
+                         mb + c->mask_off[1], mb + c->mask_off[2], (float)c->opts.eps, c->opts.mood,
+                         c->opts.weights, c->nbad, c->stream);
+        else
+          launch_stage2d(g, s, U, c->Q32, Kin, Kout, dt, c->opts.cfl, c->lmax, c->dt_dev, mb + c->mask_off[0],
+                         mb + c->mask_off[1], (float)c->opts.eps, c->opts.mood, c->opts.weights, c->nbad, gate,
+                         run_if, c->stream);
       }
       return check_launch(c, "fused stage");
     };
@@ -379,6 +385,16 @@ int ws_init(const ws_grid* grid, const ws_opts* opts, void* stream, ws_ctx** out
         if ((rc = dalloc(c, &c->Ka, (int64_t)g.nv * g.N)) || (rc = dalloc(c, &c->Kb, (int64_t)g.nv * g.N))) goto bad;
         if (fused2d_prepare() != cudaSuccess) {
           rc = fail(c, WS_ECUDA, "cannot enable %d bytes of shared memory for the fused stage", fused2d_smem_bytes());
+          goto bad;
+        }
+        c->fused = true;
+      }
+      if (gr.ndim == 3 && !getenv("WS_NO_FUSED")) {
+        if ((rc = dalloc(c, &c->Ka, (int64_t)g.nv * g.N)) || (rc = dalloc(c, &c->Kb, (int64_t)g.nv * g.N)) ||
+            (rc = dalloc(c, &c->Lp, (int64_t)g.nv * g.N)))
+          goto bad;
+        if (fused3d_prepare() != cudaSuccess) {
+          rc = fail(c, WS_ECUDA, "cannot enable %d bytes of shared memory for the fused stage", fused3d_smem_bytes());
           goto bad;
         }
         c->fused = true;
@@ -668,7 +684,8 @@ int ws_set_mlp(ws_ctx* c, const float* params, float threshold, int flags) {
     c->learned_on = false;
     return WS_OK;
   }
-  if (!c->fused) return fail(c, WS_ENOTSUP, "the learned gate runs in the fused 2D mixed-precision path only");
+  if (!c->fused || c->gd.ndim != 2)
+    return fail(c, WS_ENOTSUP, "the learned gate runs in the fused 2D mixed-precision path only");
   std::vector<float> P(WS_MLP_NPARAM);
   CK(c, cudaMemcpy(P.data(), params, sizeof(float) * WS_MLP_NPARAM, cudaMemcpyDeviceToHost));
   const float* W1 = P.data();

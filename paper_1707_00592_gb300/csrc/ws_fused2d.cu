@@ -1,18 +1,28 @@
-// Fused mixed-precision RK stage for 2D grids: one kernel per SSP-RK3 stage.
+// Fused mixed-precision RK stage: one kernel per SSP-RK3 stage in 2D, two in
+// 3D.
 //
-// A CTA owns a TX x TY tile of cells and works through five phases separated
+// A CTA owns a TX x TY tile of cells and works through three phases separated
 // by barriers, all in shared memory:
 //   A  stage-state FP32 primitives of the tile plus a 3-cell halo; boundary
 //      conditions are applied while loading (no ghost kernel), E - Pi in FP64;
-//   B1 per (face, characteristic variable): projection of the six stencil
-//      cells with L_{i+1/2} and 5th-order WENO-IS of both sides;
-//   B2 one thread per face: back-projection, MOOD cascade (a side that fails
-//      is reconstructed again at 3rd order from the staged primitives), HLLC;
+//   B  per face: projection of the six stencil cells with L_{i+1/2}, 5th-order
+//      WENO-IS of both sides (as the two lanes of paired FP32 instructions),
+//      back-projection, MOOD cascade (a side that fails is reconstructed again
+//      at 3rd order from the staged primitives), HLLC;
 //   C  one thread per cell: flux divergence with the Gamma/Pi source and the
 //      RK stage.
-// Splitting the face into (face, variable) work items keeps the register
-// count low; with only 5th-order values staged, two 512-thread CTAs fit per
-// SM, so one CTA's memory phases overlap the other's arithmetic.
+// Two 512-thread CTAs fit per SM, so one CTA's memory phases overlap the
+// other's arithmetic.
+//
+// Passes (MODE):
+//   0  2D: the tile spans x and y; x and y faces; phase C ends the stage.
+//   1  3D, first pass: one z plane per CTA row (blockIdx.z); x and y faces;
+//      phase C writes the x + y part of the divergence (with the Gamma/Pi
+//      source of the x and y face velocities) to a scratch buffer.
+//   2  3D, second pass: an x-z tile of one y plane; z faces only; phase C adds
+//      the z part to the scratch and ends the stage.
+// The directions are summed x, y, z, as Sec. 3.1 states the dimension-by-
+// dimension divergence.
 //
 // The Shu-Osher SSP-RK3 is carried in increment form, algebraically
 // identical to U1 = U + dt L0, U2 = 3/4 U + 1/4 (U1 + dt L1),
@@ -43,27 +53,47 @@ using namespace fp32;
 
 constexpr int TX = 32, TY = 15;
 constexpr int HX = TX + 2 * NG, HY = TY + 2 * NG;
-constexpr int NQ = 6;  // rho, u, v, p, Gamma, Pi
 constexpr int NFX = (TX + 1) * TY, NFY = TX * (TY + 1), NF = NFX + NFY;
 constexpr int NT = 512;
 
-// learned gate: BF16 MMA fragments of the MLP weights (m16n8k16, 32 lanes)
+// Per-pass constants.  NQ: fields (rho, velocities, E or p, Gamma, Pi), 6 in
+// 2D and 7 in 3D; the q tile holds them as primitives plus the sound speed.
+template <int NQ_, int MODE>
+struct Tr {
+  static constexpr int NQ = NQ_;
+  static constexpr int ND = NQ - 4;                 // velocity components
+  static constexpr int NTG = NQ - 5;                // tangential components at a face
+  static constexpr bool XF = MODE != 2;             // the pass has x faces (and an x halo)
+  static constexpr int QW = XF ? HX : TX;           // row width of the q tile
+  static constexpr int QX = XF ? NG : 0;            // q column of the tile's first cell
+  static constexpr int NH = QW * HY;                // q tile cells
+  static constexpr int FS = NH;                     // field stride in the q tile
+  static constexpr int NFP = (XF ? NFX : 0) + NFY;  // faces of the pass
+  static constexpr int HPT = (NH + NT - 1) / NT;    // q tile cells per thread in phase A
+  static constexpr int IP = NQ - 3, IG = NQ - 2, IPI = NQ - 1, IC = NQ;  // q fields p, Gamma, Pi, c
+  static constexpr bool RK = MODE != 1;             // phase C ends the stage
+};
+
+// learned gate (2D): BF16 MMA fragments of the MLP weights (m16n8k16, 32 lanes)
 constexpr int NFRAG1 = 2 * 4, NFRAG2 = 2 * 4, NFRAG3 = 2;  // (k-step, n-tile) pairs per layer
 constexpr int NFRAG = NFRAG1 + NFRAG2 + NFRAG3;
 constexpr int NMT = (NF + 15) / 16;  // 16-face M tiles
 
-template <bool LEARNED>
+template <bool LEARNED, int NQ_, int MODE>
 struct Smem {
-  float q[NQ + 1][HY][HX];        // primitives + sound speed of tile and halo
-  float fx[NQ + 1][TY][TX + 1];   // x-face fluxes (global field order) + face velocity
-  float fy[NQ + 1][TY + 1][TX];   // y-face fluxes + face velocity
+  using T = Tr<NQ_, MODE>;
+  static constexpr bool CACHE = !LEARNED && T::RK;  // own cells staged for phase C
+  float q[NQ_ + 1][HY][T::QW];                // primitives + sound speed of tile and halo
+  float fx[T::XF ? NQ_ + 1 : 1][TY][TX + 1];  // x-face fluxes (global field order) + face velocity
+  float fy[NQ_ + 1][TY + 1][TX];              // fluxes + face velocity of the faces along the tile's 2nd axis
   union {
-    struct {                      // plain kernel: this tile's own cells, for phase C
-      double u[NQ][TY][TX];       // stage 2: FP64 state, copied in asynchronously from the start
-      float k[NQ][TY][TX];        // stages 1, 2: accumulated increments (kept from the phase-A loads)
-      float v[NQ][TY][TX];        // stage 2: FP32 image of U^n (kept from the phase-A loads)
+    struct {                                     // this tile's own cells, for phase C
+      double u[CACHE ? NQ_ : 1][TY][TX];         // stage 2: FP64 state, copied in asynchronously from the start
+      float k[CACHE ? NQ_ : 1][TY][TX];          // stages 1, 2: accumulated increments (kept from the phase-A loads)
+      float v[CACHE ? NQ_ : 1][TY][TX];          // stage 2: FP32 image of U^n (kept from the phase-A loads)
+      float l[MODE == 2 ? NQ_ : 1][TY][TX];      // 3D second pass: x + y part of the divergence (asynchronous copy)
     } own;
-    __nv_bfloat16 feat[NF][24];   // learned kernel: gate inputs (read before the reconstruction)
+    __nv_bfloat16 feat[LEARNED ? NF : 1][24];    // learned kernel: gate inputs (read before the reconstruction)
   };
   unsigned long long red[NT / 32];  // per-warp CFL maxima
   float dt;                         // the step, broadcast from thread 0
@@ -79,17 +109,18 @@ struct SmemGate {
 struct StageArgs {
   GridDev g;
   int stage;
-  float idx, idy;     // 1/dx, 1/dy
+  float idx, idy, idz;  // 1/dx, 1/dy, 1/dz
   float cfl;
   double dt_fixed;    // > 0: use this step; otherwise CFL
   unsigned long long* lmax;  // stage 0: max wave rate (FP64 bits)
   double* dt_out;     // stage 1 (block 0): the dt used
   double* U;          // state at t^n; stage 2 replaces it with t^{n+1}
-  float* U32;         // FP32 image of U^n (rho, m_x, m_y, E - Pi, Gamma, Pi): written in stage 0
+  float* U32;         // FP32 image of U^n (rho, momenta, E - Pi, Gamma, Pi): written in stage 0
   const float* Kin;   // stages 1, 2: accumulated increments
   float* Kout;        // stages 0, 1
-  uint8_t* mask_x;    // nullable
-  uint8_t* mask_y;
+  float* Lp;          // 3D: x + y part of the divergence (first pass writes, second reads)
+  uint8_t* mask_x;    // nullable: MOOD levels of the pass's x faces
+  uint8_t* mask_a;    // nullable: MOOD levels of the faces along the tile's 2nd axis (y, or z in pass 2)
   WenoParams P;
   int mood;
   unsigned long long* nbad;
@@ -121,14 +152,16 @@ __device__ __forceinline__ int map_bc(int x, int n, int lo, int hi, bool& flip) 
   return x < 0 ? 0 : n - 1;
 }
 
-// halo-tile coordinates of stencil cell k (0..5 = i-2..i+3) of face f, and
-// whether the face is an x face; false if the face lies outside the grid.
-// Faces are numbered so that every 32-face chunk (a warp's share) is one row
-// of one orientation: x faces 0..TX-1 of the TY rows, then the TY+1 rows of y
-// faces, then the TY right-most x faces.
-__device__ __forceinline__ bool face_geom(int f, int x0, int y0, int nx, int ny, bool& isx, int& hx, int& hy,
-                                          int& dhx, int& dhy) {
-  if (f < TX * TY || f >= TX * TY + NFY) {
+// q-tile coordinates of stencil cell 0 (cells i-2..i+3 follow at stride 1 or
+// one q row) of face f, and whether the face is an x face; false if the face
+// lies outside the grid (n1: cells along the tile's 2nd axis).  Faces are
+// numbered so that every 32-face chunk (a warp's share) is one row of one
+// orientation: x faces 0..TX-1 of the TY rows, then the TY+1 rows of faces
+// along the 2nd axis, then the TY right-most x faces.  A pass without x
+// faces numbers only the 2nd-axis rows.
+template <bool XF>
+__device__ __forceinline__ bool face_geom(int f, int x0, int y0, int nx, int n1, bool& isx, int& hx, int& hy) {
+  if (XF && (f < TX * TY || f >= TX * TY + NFY)) {
     int j, i;
     if (f < TX * TY) {
       j = f / TX;
@@ -140,45 +173,14 @@ __device__ __forceinline__ bool face_geom(int f, int x0, int y0, int nx, int ny,
     isx = true;
     hx = i;  // cell k at hx + k
     hy = j + NG;
-    dhx = 1;
-    dhy = 0;
-    return (x0 + i - 1 <= nx - 1) && (y0 + j < ny);
+    return (x0 + i - 1 <= nx - 1) && (y0 + j < n1);
   }
-  int ff = f - TX * TY;
+  int ff = XF ? f - TX * TY : f;
   int j = ff / TX, i = ff - j * TX;
   isx = false;
-  hx = i + NG;
-  hy = j;
-  dhx = 0;
-  dhy = 1;
-  return (x0 + i < nx) && (y0 + j - 1 <= ny - 1);
-}
-
-// Characteristic variable R of the face's six stencil cells (qb points at
-// cell 0 in the halo tile; cells are D-strided).  D = 0: x face (frame
-// rho, u, v, ...); D = 1: y face (rho, v, u, ...).  All shared-memory offsets
-// are compile-time constants.
-template <int D, int R>
-__device__ __forceinline__ void project6(const float* qb, float (&w)[6]) {
-  constexpr int ST = D == 0 ? 1 : HX;  // stride between stencil cells
-  constexpr int FS = HY * HX;          // stride between fields
-  constexpr int UN = D == 0 ? 1 : 2, UT = D == 0 ? 2 : 1;
-  if (R == 0 || R == NQ - 1) {
-    float rho_bar = 0.5f * (qb[2 * ST] + qb[3 * ST]);
-    float c_bar = 0.5f * (qb[6 * FS + 2 * ST] + qb[6 * FS + 3 * ST]);
-    float rc = R == 0 ? -(rho_bar * c_bar) : rho_bar * c_bar;
-#pragma unroll
-    for (int k = 0; k < 6; ++k) w[k] = 0.5f * fmaf(rc, qb[UN * FS + k * ST], qb[3 * FS + k * ST]);
-  } else if (R == 1) {
-    float c_bar = 0.5f * (qb[6 * FS + 2 * ST] + qb[6 * FS + 3 * ST]);
-    float mic2 = -frcp(c_bar * c_bar);
-#pragma unroll
-    for (int k = 0; k < 6; ++k) w[k] = fmaf(mic2, qb[3 * FS + k * ST], qb[k * ST]);
-  } else {
-    constexpr int F = R == 2 ? UT : R + 1;  // shear, Gamma, Pi
-#pragma unroll
-    for (int k = 0; k < 6; ++k) w[k] = qb[F * FS + k * ST];
-  }
+  hx = i + (XF ? NG : 0);
+  hy = j;  // cell k at row hy + k
+  return (x0 + i < nx) && (y0 + j - 1 <= n1 - 1);
 }
 
 // Per-face averages of the characteristic projection: rho c and -1/c^2 at
@@ -188,31 +190,37 @@ struct FaceAvg {
   float mic2;  // -1 / c_bar^2
 };
 
-// Orientation of a face, resolved at run time so that x and y faces share one
-// copy of the reconstruction code: offsets of the six stencil cells in the
-// halo tile and the normal / tangential velocity fields.
+// Orientation of a face, resolved at run time so that the faces of both
+// directions of a pass share one copy of the reconstruction code: offsets of
+// the six stencil cells in the q tile and the q fields of the normal and
+// tangential velocities.
+template <int NTG>
 struct FaceGeo {
   int off[6];
-  int un, ut;
+  int un;
+  int ut[NTG];
 };
 
 // Characteristic variable R of the six stencil cells as mirrored pairs
 // p[k] = (w_k, w_{5-k}), k = 0..4: the .x lanes are the left stencil
-// w_0..w_4, the .y lanes the right stencil w_5..w_1.
-template <int R>
-__device__ __forceinline__ void project_pairs(const float* qb, const FaceGeo& fg, const FaceAvg& fa, float2 (&p)[5]) {
-  constexpr int FS = HY * HX;
+// w_0..w_4, the .y lanes the right stencil w_5..w_1.  Variables: 0 w1,
+// 1 w2 (entropy), 2 .. 1+NTG tangential velocities, NQ-3 Gamma, NQ-2 Pi,
+// NQ-1 w6.
+template <class T, int R>
+__device__ __forceinline__ void project_pairs(const float* qb, const FaceGeo<T::NTG>& fg, const FaceAvg& fa,
+                                              float2 (&p)[5]) {
+  constexpr int FS = T::FS;
   auto cell = [&](const float* b, int k) { return make_float2(b[fg.off[k]], b[fg.off[5 - k]]); };
-  if (R == 0 || R == NQ - 1) {
+  if constexpr (R == 0 || R == T::NQ - 1) {
     float2 rc = f2(R == 0 ? -fa.rc : fa.rc);
 #pragma unroll
-    for (int k = 0; k < 5; ++k) p[k] = mul2(f2(0.5f), fma2(rc, cell(qb + fg.un * FS, k), cell(qb + 3 * FS, k)));
-  } else if (R == 1) {
+    for (int k = 0; k < 5; ++k) p[k] = mul2(f2(0.5f), fma2(rc, cell(qb + fg.un * FS, k), cell(qb + T::IP * FS, k)));
+  } else if constexpr (R == 1) {
 #pragma unroll
-    for (int k = 0; k < 5; ++k) p[k] = fma2(f2(fa.mic2), cell(qb + 3 * FS, k), cell(qb, k));
-  } else if (R == 2) {  // shear
+    for (int k = 0; k < 5; ++k) p[k] = fma2(f2(fa.mic2), cell(qb + T::IP * FS, k), cell(qb, k));
+  } else if constexpr (R < 2 + T::NTG) {  // tangential velocities
 #pragma unroll
-    for (int k = 0; k < 5; ++k) p[k] = cell(qb + fg.ut * FS, k);
+    for (int k = 0; k < 5; ++k) p[k] = cell(qb + fg.ut[R - 2] * FS, k);
   } else {  // Gamma, Pi
 #pragma unroll
     for (int k = 0; k < 5; ++k) p[k] = cell(qb + (R + 1) * FS, k);
@@ -223,11 +231,11 @@ __device__ __forceinline__ void project_pairs(const float* qb, const FaceGeo& fg
 // stencil flat to 1e-6 of its magnitude (a few FP32 ulps: rounding noise)
 // takes the linear weights, from which WENO-IS differs there by less than
 // the stencil's range; elsewhere WENO-IS.
-template <int R>
-__device__ __forceinline__ void weno_item(const float* qb, const FaceGeo& fg, const FaceAvg& fa, const WenoParams& P,
-                                          float& l5, float& r5) {
+template <class T, int R>
+__device__ __forceinline__ void weno_item(const float* qb, const FaceGeo<T::NTG>& fg, const FaceAvg& fa,
+                                          const WenoParams& P, float& l5, float& r5) {
   float2 p[5];
-  project_pairs<R>(qb, fg, fa, p);
+  project_pairs<T, R>(qb, fg, fa, p);
   float mn = fminf(fmin3(p[0].x, p[1].x, p[2].x), fmin3(p[2].y, p[1].y, p[0].y));
   float mx = fmaxf(fmax3(p[0].x, p[1].x, p[2].x), fmax3(p[2].y, p[1].y, p[0].y));
   float2 v;
@@ -239,25 +247,62 @@ __device__ __forceinline__ void weno_item(const float* qb, const FaceGeo& fg, co
   r5 = v.y;
 }
 
+// 5th-order linear-weight reconstruction of variable R on both sides
+template <class T, int R>
+__device__ __forceinline__ void linear_item(const float* qb, const FaceGeo<T::NTG>& fg, const FaceAvg& fa, float& l5,
+                                            float& r5) {
+  float2 p[5];
+  project_pairs<T, R>(qb, fg, fa, p);
+  float2 v = linear5_pair(p[0], p[1], p[2], p[3], p[4]);
+  l5 = v.x;
+  r5 = v.y;
+}
+
+// Characteristic variable R of the six stencil cells, one value per cell
+// (the MOOD retry's projection, with its own face averages)
+template <class T, int R>
+__device__ __forceinline__ void project6(const float* qb, const FaceGeo<T::NTG>& fg, float (&w)[6]) {
+  constexpr int FS = T::FS;
+  if constexpr (R == 0 || R == T::NQ - 1) {
+    float rho_bar = 0.5f * (qb[fg.off[2]] + qb[fg.off[3]]);
+    float c_bar = 0.5f * (qb[T::IC * FS + fg.off[2]] + qb[T::IC * FS + fg.off[3]]);
+    float rc = R == 0 ? -(rho_bar * c_bar) : rho_bar * c_bar;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) w[k] = 0.5f * fmaf(rc, qb[fg.un * FS + fg.off[k]], qb[T::IP * FS + fg.off[k]]);
+  } else if constexpr (R == 1) {
+    float c_bar = 0.5f * (qb[T::IC * FS + fg.off[2]] + qb[T::IC * FS + fg.off[3]]);
+    float mic2 = -frcp(c_bar * c_bar);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) w[k] = fmaf(mic2, qb[T::IP * FS + fg.off[k]], qb[fg.off[k]]);
+  } else if constexpr (R < 2 + T::NTG) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) w[k] = qb[fg.ut[R - 2] * FS + fg.off[k]];
+  } else {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) w[k] = qb[(R + 1) * FS + fg.off[k]];
+  }
+}
+
 // 3rd-order reconstruction (d3 = d4 = 0) of all variables of one side:
 // the MOOD retry, taken only by faces whose 5th-order state is inadmissible
-template <int D>
-__device__ __noinline__ void weno_side3(const float* qb, int side, const WenoParams& P, float* wt) {
-  float w[6];
-#define WS_SIDE3(R)                                                                                   \
-  project6<D, R>(qb, w);                                                                             \
-  wt[R] = side == 0 ? weno_is(w[0], w[1], w[2], w[3], w[4], P, 3) : weno_is(w[5], w[4], w[3], w[2], w[1], P, 3);
+template <class T>
+__device__ __noinline__ void weno_side3(const float* qb, const FaceGeo<T::NTG> fg, int side, const WenoParams P,
+                                        float* wt) {
+#define WS_SIDE3(R)                                                                                        \
+  if constexpr (R < T::NQ) {                                                                              \
+    float w[6];                                                                                           \
+    project6<T, R>(qb, fg, w);                                                                            \
+    wt[R] = side == 0 ? weno_is(w[0], w[1], w[2], w[3], w[4], P, 3) : weno_is(w[5], w[4], w[3], w[2], w[1], P, 3); \
+  }
   WS_SIDE3(0)
   WS_SIDE3(1)
   WS_SIDE3(2)
   WS_SIDE3(3)
   WS_SIDE3(4)
   WS_SIDE3(5)
+  WS_SIDE3(6)
 #undef WS_SIDE3
 }
-
-// the (at most HPT) halo cells a thread owns in phase A
-constexpr int HPT = (HX * HY + NT - 1) / NT;
 
 __device__ __forceinline__ void mma16816(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
                                          uint2 b) {
@@ -273,8 +318,8 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   return *reinterpret_cast<uint32_t*>(&v);
 }
 
-// gate inputs of one face: w1, w2, w6, w_Gamma of the six stencil cells, each
-// normalised over the stencil (zero for a stencil flat to 1e-6)
+// gate inputs of one face (2D): w1, w2, w6, w_Gamma of the six stencil cells,
+// each normalised over the stencil (zero for a stencil flat to 1e-6)
 template <int D>
 __device__ __forceinline__ void gate_features(const float* qb, __nv_bfloat16* out) {
   constexpr int ST = D == 0 ? 1 : HX;
@@ -311,18 +356,11 @@ __device__ __forceinline__ void gate_features(const float* qb, __nv_bfloat16* ou
   }
 }
 
-// 5th-order linear-weight reconstruction of variable R on both sides
-template <int R>
-__device__ __forceinline__ void linear_item(const float* qb, const FaceGeo& fg, const FaceAvg& fa, float& l5,
-                                            float& r5) {
-  float2 p[5];
-  project_pairs<R>(qb, fg, fa, p);
-  float2 v = linear5_pair(p[0], p[1], p[2], p[3], p[4]);
-  l5 = v.x;
-  r5 = v.y;
+// Asynchronous global -> shared copies (hold no register while in flight)
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+  unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
 }
-
-// Asynchronous 8-byte global -> shared copy (holds no register while in flight)
 __device__ __forceinline__ void cp_async8(void* dst, const void* src) {
   unsigned d = (unsigned)__cvta_generic_to_shared(dst);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
@@ -330,35 +368,48 @@ __device__ __forceinline__ void cp_async8(void* dst, const void* src) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
-template <bool LEARNED>
-__global__ void __launch_bounds__(NT, 2) k_stage2d(StageArgs a) {
+template <bool LEARNED, int NQ_, int MODE>
+__global__ void __launch_bounds__(NT, 2) k_stage(StageArgs a) {
+  using T = Tr<NQ_, MODE>;
+  using SM = Smem<LEARNED, NQ_, MODE>;
+  constexpr int NQ = NQ_, ND = T::ND, FS = T::FS;
+  constexpr bool CACHE = SM::CACHE;
+  // axes: x, the tile's 2nd axis (y; z in pass 2), the plane axis (z; y in pass 2; none in 2D)
+  constexpr int AX1 = MODE == 2 ? 2 : 1, AXP = MODE == 2 ? 1 : 2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  Smem<LEARNED>& S = *reinterpret_cast<Smem<LEARNED>*>(smem_raw);
-  SmemGate& SG = *reinterpret_cast<SmemGate*>(smem_raw + sizeof(Smem<LEARNED>));
+  SM& S = *reinterpret_cast<SM*>(smem_raw);
+  SmemGate& SG = *reinterpret_cast<SmemGate*>(smem_raw + sizeof(SM));
   if (a.run_if && *a.run_if == 0) return;  // a conditional redo that is not needed
   const GridDev& g = a.g;
-  const int nx = g.n[0], ny = g.n[1];
-  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-  const int64_t N = g.N, P0 = g.P[0];
+  const int nx = g.n[0], n1 = g.n[AX1];
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, plane = blockIdx.z;
+  const int64_t N = g.N, S1 = g.st[AX1];
+  const int64_t pbase = (int64_t)(g.G[AXP] + plane) * g.st[AXP] + g.G[0];  // cell (x, a) at pbase + (G1 + a) S1 + x
   const int tid = threadIdx.x;
   if (a.stage == 1 || a.stage == 2) {
     if (tid == 0) {  // one FP64 division per CTA
       double d = a.dt_fixed > 0.0 ? a.dt_fixed : (double)a.cfl / __longlong_as_double((long long)*a.lmax);
-      if (a.stage == 1 && blockIdx.x == 0 && blockIdx.y == 0) *a.dt_out = d;
+      if (a.stage == 1 && MODE != 2 && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0) *a.dt_out = d;
       S.dt = f64_to_f32(d);
     }
     __syncthreads();
   }
-  // plain kernel, stage 2: the own cells' FP64 state, needed only in phase C,
-  // is copied into shared memory while phases A and B run
-  constexpr bool CACHE = !LEARNED;
-  if (CACHE && a.stage == 2) {
+  // The own cells' FP64 state (stage 2) and, in the second 3D pass, the x + y
+  // part of their divergence are needed only in phase C: they are copied into
+  // shared memory while phases A and B run.
+  if (CACHE && (a.stage == 2 || MODE == 2)) {
     for (int c = tid; c < TX * TY; c += NT) {
       int j = c / TX, i = c - j * TX;
-      if (x0 + i >= nx || y0 + j >= ny) continue;
-      int64_t gi = (int64_t)(NG + y0 + j) * P0 + (NG + x0 + i);
+      if (x0 + i >= nx || y0 + j >= n1) continue;
+      int64_t gi = pbase + (int64_t)(g.G[AX1] + y0 + j) * S1 + x0 + i;
+      if (a.stage == 2) {
 #pragma unroll
-      for (int m = 0; m < NQ; ++m) cp_async8(&S.own.u[m][j][i], &a.U[m * N + gi]);
+        for (int m = 0; m < NQ; ++m) cp_async8(&S.own.u[m][j][i], &a.U[m * N + gi]);
+      }
+      if (MODE == 2) {
+#pragma unroll
+        for (int m = 0; m < NQ; ++m) cp_async4(&S.own.l[m][j][i], &a.Lp[m * N + gi]);
+      }
     }
     cp_async_commit();
   }
@@ -367,46 +418,48 @@ __global__ void __launch_bounds__(NT, 2) k_stage2d(StageArgs a) {
   float lam_max = 0.0f;
 
   // ---- phase A: stage-state primitives of tile + halo ----
-  // A thread owns up to HPT halo cells; all their global loads are issued
+  // A thread owns up to HPT q-tile cells; all their global loads are issued
   // before any of them is used, so that a CTA has its whole halo in flight.
   {
-    float ld[HPT][NQ];
-    float rk[HPT][NQ], rv[HPT][NQ];  // stages 1, 2: increment and FP32 image as loaded
-    int hh[HPT];
-    bool flx[HPT], fly[HPT], own[HPT];
+    float ld[T::HPT][NQ];
+    float rk[T::HPT][NQ], rv[T::HPT][NQ];  // stages 1, 2: increment and FP32 image as loaded
+    int hh[T::HPT];
+    bool flx[T::HPT], fla[T::HPT], own[T::HPT];
 #pragma unroll
-    for (int t = 0; t < HPT; ++t) {
+    for (int t = 0; t < T::HPT; ++t) {
       int h = tid + t * NT;
-      int hy = h / HX, hx = h - hy * HX;
-      int gx = x0 + hx - NG, gy = y0 + hy - NG;
-      bool outx = gx < 0 || gx >= nx, outy = gy < 0 || gy >= ny;
-      hh[t] = (h < HX * HY && !(outx && outy)) ? h : -1;  // corners are never read
-      if (hh[t] < 0) continue;
-      bool fx = false, fy = false;
+      int hy = h / T::QW, hx = h - hy * T::QW;
+      int gx = x0 + hx - T::QX, ga = y0 + hy - NG;
+      bool outx = gx < 0 || gx >= nx, outa = ga < 0 || ga >= n1;
+      // corners are never read, nor (without x faces) columns past the grid
+      bool skip = h >= T::NH || (outx && outa) || (!T::XF && outx);
+      hh[t] = skip ? -1 : h;
+      if (skip) continue;
+      bool fx = false, fa = false;
       int mx = map_bc(gx, nx, g.bc[0][0], g.bc[0][1], fx);
-      int my = map_bc(gy, ny, g.bc[1][0], g.bc[1][1], fy);
+      int ma = map_bc(ga, n1, g.bc[AX1][0], g.bc[AX1][1], fa);
       flx[t] = fx;
-      fly[t] = fy;
-      int64_t i = (int64_t)(NG + my) * P0 + (NG + mx);
+      fla[t] = fa;
+      int64_t i = pbase + (int64_t)(g.G[AX1] + ma) * S1 + mx;
+      own[t] = hx >= T::QX && hx < T::QX + TX && hy >= NG && hy < NG + TY && !outx && !outa;
       if (a.stage == 0 || a.stage == 3) {
         const double* U = a.U;
-        ld[t][0] = f64_to_f32(U[i]);
-        ld[t][1] = f64_to_f32(U[N + i]);
-        ld[t][2] = f64_to_f32(U[2 * N + i]);
-        ld[t][3] = f64_to_f32(U[3 * N + i] - U[5 * N + i]);  // E - Pi in FP64
-        ld[t][4] = f64_to_f32(U[4 * N + i]);
-        ld[t][5] = f64_to_f32(U[5 * N + i]);
-        own[t] = a.stage == 0 && hx >= NG && hx < NG + TX && hy >= NG && hy < NG + TY && !outx && !outy;
-        if (LEARNED && own[t]) {
 #pragma unroll
-          for (int m = 0; m < NQ; ++m) a.Ubackup[m * N + i] = U[m * N + i];
+        for (int m = 0; m < NQ; ++m) {
+          if (m == NQ - 3)
+            ld[t][m] = f64_to_f32(U[m * N + i] - U[(NQ - 1) * N + i]);  // E - Pi in FP64
+          else
+            ld[t][m] = f64_to_f32(U[m * N + i]);
         }
-        if (own[t]) {
+        if (a.stage == 0 && MODE != 2 && own[t]) {
+          if (LEARNED) {
+#pragma unroll
+            for (int m = 0; m < NQ; ++m) a.Ubackup[m * N + i] = U[m * N + i];
+          }
 #pragma unroll
           for (int m = 0; m < NQ; ++m) a.U32[m * N + i] = ld[t][m];
         }
       } else {
-        own[t] = hx >= NG && hx < NG + TX && hy >= NG && hy < NG + TY && !outx && !outy;
 #pragma unroll
         for (int m = 0; m < NQ; ++m) {
           rk[t][m] = __ldg(&a.Kin[m * N + i]);
@@ -416,16 +469,17 @@ __global__ void __launch_bounds__(NT, 2) k_stage2d(StageArgs a) {
     }
     if (a.stage == 1 || a.stage == 2) {
 #pragma unroll
-      for (int t = 0; t < HPT; ++t) {
+      for (int t = 0; t < T::HPT; ++t) {
         if (hh[t] < 0) continue;
-        ld[t][0] = fmaf(coef, rk[t][0], rv[t][0]);
-        ld[t][1] = fmaf(coef, rk[t][1], rv[t][1]);
-        ld[t][2] = fmaf(coef, rk[t][2], rv[t][2]);
-        ld[t][3] = fmaf(coef, rk[t][3] - rk[t][5], rv[t][3]);
-        ld[t][4] = fmaf(coef, rk[t][4], rv[t][4]);
-        ld[t][5] = fmaf(coef, rk[t][5], rv[t][5]);
+#pragma unroll
+        for (int m = 0; m < NQ; ++m) {
+          if (m == NQ - 3)
+            ld[t][m] = fmaf(coef, rk[t][m] - rk[t][NQ - 1], rv[t][m]);
+          else
+            ld[t][m] = fmaf(coef, rk[t][m], rv[t][m]);
+        }
         if (CACHE && own[t]) {  // phase C reads these instead of global memory
-          int j = hh[t] / HX - NG, i = hh[t] % HX - NG;
+          int j = hh[t] / T::QW - NG, i = hh[t] % T::QW - T::QX;
 #pragma unroll
           for (int m = 0; m < NQ; ++m) {
             S.own.k[m][j][i] = rk[t][m];
@@ -435,31 +489,35 @@ __global__ void __launch_bounds__(NT, 2) k_stage2d(StageArgs a) {
       }
     }
 #pragma unroll
-    for (int t = 0; t < HPT; ++t) {
+    for (int t = 0; t < T::HPT; ++t) {
       if (hh[t] < 0) continue;
-      int hy = hh[t] / HX, hx = hh[t] - hy * HX;
-      float rho = ld[t][0], eint = ld[t][3], Gam = ld[t][4], Pi = ld[t][5];
+      int hy = hh[t] / T::QW, hx = hh[t] - hy * T::QW;
+      float rho = ld[t][0], eint = ld[t][NQ - 3], Gam = ld[t][NQ - 2], Pi = ld[t][NQ - 1];
       float irho = frcp(rho);
-      float u = ld[t][1] * irho, v = ld[t][2] * irho;
-      if (flx[t]) u = -u;
-      if (fly[t]) v = -v;
-      float p = fmaf(-0.5f * rho, fmaf(u, u, v * v), eint) * frcp(Gam);
+      float vel[ND];
+#pragma unroll
+      for (int d = 0; d < ND; ++d) vel[d] = ld[t][1 + d] * irho;
+      if (flx[t]) vel[0] = -vel[0];
+      if (fla[t]) vel[AX1] = -vel[AX1];
+      float ksq = ND == 2 ? fmaf(vel[0], vel[0], vel[1] * vel[1])
+                          : fmaf(vel[0], vel[0], fmaf(vel[1], vel[1], vel[ND - 1] * vel[ND - 1]));
+      float p = fmaf(-0.5f * rho, ksq, eint) * frcp(Gam);
       S.q[0][hy][hx] = rho;
-      S.q[1][hy][hx] = u;
-      S.q[2][hy][hx] = v;
-      S.q[3][hy][hx] = p;
-      S.q[4][hy][hx] = Gam;
-      S.q[5][hy][hx] = Pi;
+#pragma unroll
+      for (int d = 0; d < ND; ++d) S.q[1 + d][hy][hx] = vel[d];
+      S.q[T::IP][hy][hx] = p;
+      S.q[T::IG][hy][hx] = Gam;
+      S.q[T::IPI][hy][hx] = Pi;
       float c = fsqrt(sound_speed2(rho, p, Gam, Pi));
-      S.q[6][hy][hx] = c;
-      int gx = x0 + hx - NG, gy = y0 + hy - NG;
-      if (a.stage == 0 && hx >= NG && hx < NG + TX && hy >= NG && hy < NG + TY && gx < nx && gy < ny) {
-        float lam = fmaf(fabsf(u) + c, a.idx, (fabsf(v) + c) * a.idy);
+      S.q[T::IC][hy][hx] = c;
+      if (a.stage == 0 && MODE != 2 && own[t]) {
+        float lam = fmaf(fabsf(vel[0]) + c, a.idx, (fabsf(vel[1]) + c) * a.idy);
+        if (ND == 3) lam = fmaf(fabsf(vel[ND - 1]) + c, a.idz, lam);
         if (!(lam <= lam_max)) lam_max = lam;  // NaN propagates
       }
     }
   }
-  if (a.stage == 0) {
+  if (a.stage == 0 && MODE != 2) {
     unsigned long long b = (unsigned long long)__double_as_longlong(f32_to_f64(lam_max));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -469,15 +527,15 @@ __global__ void __launch_bounds__(NT, 2) k_stage2d(StageArgs a) {
     if ((tid & 31) == 0) S.red[tid >> 5] = b;
   }
   __syncthreads();
-  if (a.stage == 0 && tid == 0) {
+  if (a.stage == 0 && MODE != 2 && tid == 0) {
     unsigned long long b = 0;
 #pragma unroll
     for (int w = 0; w < NT / 32; ++w) b = S.red[w] > b ? S.red[w] : b;
     if (b) atomicMax(a.lmax, b);
   }
 
-  // ---- phases G1, G2 (learned gate): features, then the BF16 tensor-core MLP ----
-  if (LEARNED) {
+  // ---- phases G1, G2 (learned gate, 2D): features, then the BF16 tensor-core MLP ----
+  if constexpr (LEARNED) {
     for (int i = tid; i < NFRAG * 32; i += NT) SG.frag[i / 32][i % 32] = a.mlp_frag[i];
     for (int i = tid; i < 65; i += NT) {
       float b = a.mlp_bias[i];
@@ -487,9 +545,9 @@ __global__ void __launch_bounds__(NT, 2) k_stage2d(StageArgs a) {
     }
     for (int f = tid; f < NF; f += NT) {
       bool isx;
-      int hx, hy, dhx, dhy;
+      int hx, hy;
       SG.smooth[f] = 0;
-      if (!face_geom(f, x0, y0, nx, ny, isx, hx, hy, dhx, dhy)) continue;
+      if (!face_geom<true>(f, x0, y0, nx, n1, isx, hx, hy)) continue;
       const float* qb = &S.q[0][hy][hx];
       if (isx)
         gate_features<0>(qb, S.feat[f]);
@@ -548,72 +606,69 @@ __global__ void __launch_bounds__(NT, 2) k_stage2d(StageArgs a) {
     if (a.stage == 3) {  // gate evaluation only: the decisions go to the mask arrays
       for (int f = tid; f < NF; f += NT) {
         bool isx;
-        int hx, hy, dhx, dhy;
-        if (!face_geom(f, x0, y0, nx, ny, isx, hx, hy, dhx, dhy)) continue;
+        int hx, hy;
+        if (!face_geom<true>(f, x0, y0, nx, n1, isx, hx, hy)) continue;
         if (isx)
           a.mask_x[(int64_t)(y0 + hy - NG) * (nx + 1) + (x0 + hx)] = SG.smooth[f];
         else
-          a.mask_y[(int64_t)(y0 + hy) * nx + (x0 + hx - NG)] = SG.smooth[f];
+          a.mask_a[(int64_t)(y0 + hy) * nx + (x0 + hx - NG)] = SG.smooth[f];
       }
       return;
     }
   }
 
-  // ---- phase B: per face, WENO-IS per characteristic variable (B1), then
-  // back-projection, MOOD and HLLC (B2).  The thread that reconstructs a face
-  // also solves its Riemann problem, so no barrier separates the two and the
+  // ---- phase B: per face, WENO-IS per characteristic variable, then
+  // back-projection, MOOD and HLLC.  The thread that reconstructs a face also
+  // solves its Riemann problem, so no barrier separates the two and the
   // reconstructed characteristics stay in registers.
   const bool drift = LEARNED && ((int)((blockIdx.y * gridDim.x + blockIdx.x) & 63) == a.drift_tile);
   float dnum = 0.0f, dden = 0.0f, nsm = 0.0f, nval = 0.0f;
   const float* q0 = &S.q[0][0][0];
 #pragma unroll 1
-  for (int f = tid; f < NF; f += NT) {
+  for (int f = tid; f < T::NFP; f += NT) {
     bool isx;
-    int hx, hy, dhx, dhy;
-    if (!face_geom(f, x0, y0, nx, ny, isx, hx, hy, dhx, dhy)) continue;
-    const int qo = hy * HX + hx;  // stencil cell 0 in the halo tile
+    int hx, hy;
+    if (!face_geom<T::XF>(f, x0, y0, nx, n1, isx, hx, hy)) continue;
+    const float* qb = q0 + hy * T::QW + hx;  // stencil cell 0 in the q tile
     const bool sm = LEARNED && SG.smooth[f];
-    float wl[NQ], wr[NQ];  // reconstructed characteristics, left and right
-    const int un = isx ? 1 : 2, ut = isx ? 2 : 1;
-    int ya = hy + 2 * dhy, xa = hx + 2 * dhx, yb = hy + 3 * dhy, xb = hx + 3 * dhx;
-    float rho_bar = 0.5f * (S.q[0][ya][xa] + S.q[0][yb][xb]);
-    float c_bar = 0.5f * (S.q[6][ya][xa] + S.q[6][yb][xb]);
+    FaceGeo<T::NTG> fg;
+    {
+      const int st = isx ? 1 : T::QW;
+#pragma unroll
+      for (int k = 0; k < 6; ++k) fg.off[k] = k * st;
+      fg.un = isx ? 1 : 1 + AX1;
+      fg.ut[0] = isx ? 2 : 1;  // tangential velocities in increasing axis order
+      if constexpr (T::NTG == 2) fg.ut[1] = isx ? 3 : (AX1 == 1 ? 3 : 2);
+    }
+    float rho_bar = 0.5f * (qb[fg.off[2]] + qb[fg.off[3]]);
+    float c_bar = 0.5f * (qb[T::IC * FS + fg.off[2]] + qb[T::IC * FS + fg.off[3]]);
     float c2 = c_bar * c_bar, rc = rho_bar * c_bar;
     float inv = frcp(c2 * rc);
     float ic2 = rc * inv, irc = c2 * inv;  // 1/c^2, 1/(rho c)
     const FaceAvg fa{rc, -ic2};
-    FaceGeo fg;
-    {
-      const int st = isx ? 1 : HX;
-#pragma unroll
-      for (int k = 0; k < 6; ++k) fg.off[k] = k * st;
-      fg.un = un;
-      fg.ut = ut;
-    }
+    float wl[NQ], wr[NQ];  // reconstructed characteristics, left and right
     if (LEARNED) {
       nval += 1.0f;
       nsm += sm ? 1.0f : 0.0f;
     }
-#define WS_B1(R)                                                          \
-    {                                                                     \
-      float l5, r5;                                                       \
-      bool lin = LEARNED && R != 2 && sm; /* shear: always WENO-IS */     \
-      if (lin) {                                                          \
-        linear_item<R>(q0 + qo, fg, fa, l5, r5);                             \
-      }                                                                   \
-      if (!lin || drift) {                                                \
-        float fl, fr;                                                     \
-        weno_item<R>(q0 + qo, fg, fa, a.P, fl, fr);                          \
-        if (lin) {                                                        \
-          dnum += fabsf(l5 - fl) + fabsf(r5 - fr);                        \
-          dden += fabsf(fl) + fabsf(fr);                                  \
-        } else {                                                          \
-          l5 = fl;                                                        \
-          r5 = fr;                                                        \
-        }                                                                 \
-      }                                                                   \
-      wl[R] = l5;                                                         \
-      wr[R] = r5;                                                         \
+#define WS_B1(R)                                                                 \
+    if constexpr (R < NQ) {                                                      \
+      float l5, r5;                                                              \
+      bool lin = LEARNED && R != 2 && sm; /* shear: always WENO-IS */            \
+      if (lin) linear_item<T, R>(qb, fg, fa, l5, r5);                            \
+      if (!lin || drift) {                                                       \
+        float fl, fr;                                                            \
+        weno_item<T, R>(qb, fg, fa, a.P, fl, fr);                                \
+        if (lin) {                                                               \
+          dnum += fabsf(l5 - fl) + fabsf(r5 - fr);                               \
+          dden += fabsf(fl) + fabsf(fr);                                         \
+        } else {                                                                 \
+          l5 = fl;                                                               \
+          r5 = fr;                                                               \
+        }                                                                        \
+      }                                                                          \
+      wl[R] = l5;                                                                \
+      wr[R] = r5;                                                                \
     }
     WS_B1(0)
     WS_B1(1)
@@ -621,6 +676,7 @@ __global__ void __launch_bounds__(NT, 2) k_stage2d(StageArgs a) {
     WS_B1(3)
     WS_B1(4)
     WS_B1(5)
+    WS_B1(6)
 #undef WS_B1
 
     float2 W[NQ], Q[NQ];  // (left, right) characteristics, then primitives
@@ -642,22 +698,19 @@ __global__ void __launch_bounds__(NT, 2) k_stage2d(StageArgs a) {
           if (side == 0 ? ok0 : ok1) continue;
           if (LEARNED && sm) atomicAdd(&a.lstat[0], 1.0f);
           float wt[NQ];
-          const float* qb = &S.q[0][hy][hx];
-          if (isx)
-            weno_side3<0>(qb, side, a.P, wt);
-          else
-            weno_side3<1>(qb, side, a.P, wt);
+          weno_side3<T>(qb, fg, side, a.P, wt);
           float q3[NQ];
           back_project<NQ>(wt, ic2, irc, q3);
           code[side] = 1;
-          if (!admissible<NQ>(q3)) {
-            int yy = side == 0 ? ya : yb, xx = side == 0 ? xa : xb;
-            q3[0] = S.q[0][yy][xx];
-            q3[1] = S.q[un][yy][xx];
-            q3[2] = S.q[ut][yy][xx];
-            q3[3] = S.q[3][yy][xx];
-            q3[4] = S.q[4][yy][xx];
-            q3[5] = S.q[5][yy][xx];
+          if (!admissible<NQ>(q3)) {  // 1st order: the cell's own primitive state
+            const int oc = side == 0 ? fg.off[2] : fg.off[3];
+            q3[0] = qb[oc];
+            q3[1] = qb[fg.un * FS + oc];
+#pragma unroll
+            for (int t = 0; t < T::NTG; ++t) q3[2 + t] = qb[fg.ut[t] * FS + oc];
+            q3[T::IP] = qb[T::IP * FS + oc];
+            q3[T::IP + 1] = qb[T::IG * FS + oc];
+            q3[T::IP + 2] = qb[T::IPI * FS + oc];
             code[side] = 2;
           }
 #pragma unroll
@@ -673,22 +726,31 @@ __global__ void __launch_bounds__(NT, 2) k_stage2d(StageArgs a) {
     float Fh[NQ], us;
     hllc_pair<NQ>(Q, Fh, us);
     uint8_t mb = (uint8_t)(code[0] | (code[1] << 2));
-    if (isx) {
-      int j = hy - NG, i = hx;
+    bool stored = false;
+    if constexpr (T::XF) {
+      if (isx) {  // x faces: the sweep frame is the global field order
+        int j = hy - NG, i = hx;
 #pragma unroll
-      for (int m = 0; m < NQ; ++m) S.fx[m][j][i] = Fh[m];
-      S.fx[NQ][j][i] = us;
-      if (a.mask_x) a.mask_x[(int64_t)(y0 + j) * (nx + 1) + (x0 + i)] = mb;
-    } else {
-      int j = hy, i = hx - NG;
+        for (int m = 0; m < NQ; ++m) S.fx[m][j][i] = Fh[m];
+        S.fx[NQ][j][i] = us;
+        if (a.mask_x) a.mask_x[((int64_t)plane * n1 + (y0 + j)) * (nx + 1) + (x0 + i)] = mb;
+        stored = true;
+      }
+    }
+    if (!stored) {
+      int j = hy, i = hx - T::QX;
       S.fy[0][j][i] = Fh[0];
-      S.fy[1][j][i] = Fh[2];  // rho u
-      S.fy[2][j][i] = Fh[1];  // rho v
-      S.fy[3][j][i] = Fh[3];
-      S.fy[4][j][i] = Fh[4];
-      S.fy[5][j][i] = Fh[5];
+      S.fy[fg.un][j][i] = Fh[1];  // normal momentum
+#pragma unroll
+      for (int t = 0; t < T::NTG; ++t) S.fy[fg.ut[t]][j][i] = Fh[2 + t];
+#pragma unroll
+      for (int m = NQ - 3; m < NQ; ++m) S.fy[m][j][i] = Fh[m];
       S.fy[NQ][j][i] = us;
-      if (a.mask_y) a.mask_y[(int64_t)(y0 + j) * nx + (x0 + i)] = mb;
+      if (a.mask_a) {
+        int64_t mi = MODE == 2 ? ((int64_t)(y0 + j) * g.n[1] + plane) * nx + (x0 + i)
+                               : ((int64_t)plane * (n1 + 1) + (y0 + j)) * nx + (x0 + i);
+        a.mask_a[mi] = mb;
+      }
     }
   }
   if (LEARNED) {
@@ -706,7 +768,7 @@ __global__ void __launch_bounds__(NT, 2) k_stage2d(StageArgs a) {
       SG.red[3][tid >> 5] = nval;
     }
   }
-  if (CACHE && a.stage == 2) cp_async_wait_all();  // own FP64 state, visible after the barrier
+  if (CACHE && (a.stage == 2 || MODE == 2)) cp_async_wait_all();  // own-cell copies, visible after the barrier
   __syncthreads();
   if (LEARNED && tid < 4) {
     float sum = 0.0f;
@@ -714,62 +776,75 @@ __global__ void __launch_bounds__(NT, 2) k_stage2d(StageArgs a) {
     if (tid >= 2 || drift) atomicAdd(&a.lstat[1 + tid], sum);
   }
 
-  // ---- phase C: flux divergence and RK stage (variables in pairs) ----
-  const float2 idx = f2(a.idx), idy = f2(a.idy);
+  // ---- phase C: flux divergence and RK stage ----
+  constexpr int M0 = NQ % 2;  // with an odd field count, field 0 goes alone ahead of the pairs
   for (int c = tid; c < TX * TY; c += NT) {
     int j = c / TX, i = c - j * TX;
-    int gx = x0 + i, gy = y0 + j;
-    if (gx >= nx || gy >= ny) continue;
-    int64_t gi = (int64_t)(NG + gy) * P0 + (NG + gx);
-    float div_u = (S.fx[NQ][j][i + 1] - S.fx[NQ][j][i]) * a.idx + (S.fy[NQ][j + 1][i] - S.fy[NQ][j][i]) * a.idy;
-    float2 inc[NQ / 2];
+    if (x0 + i >= nx || y0 + j >= n1) continue;
+    const int64_t gi = pbase + (int64_t)(g.G[AX1] + y0 + j) * S1 + x0 + i;
+    const int qj = j + NG, qi = i + T::QX;
+    float inc[NQ];
+    auto fy2 = [&](int m, int jj) { return make_float2(S.fy[m][jj][i], S.fy[m + 1][jj][i]); };
+    if constexpr (MODE != 2) {  // x then y faces
+      const float2 idx = f2(a.idx), idy = f2(a.idy);
+      float div_u = (S.fx[NQ][j][i + 1] - S.fx[NQ][j][i]) * a.idx + (S.fy[NQ][j + 1][i] - S.fy[NQ][j][i]) * a.idy;
+      if constexpr (M0 == 1) inc[0] = fmaf(S.fy[0][j][i] - S.fy[0][j + 1][i], a.idy, (S.fx[0][j][i] - S.fx[0][j][i + 1]) * a.idx);
 #pragma unroll
-    for (int k = 0; k < NQ / 2; ++k) {
-      const int m = 2 * k;
-      float2 L = mul2(sub2(make_float2(S.fx[m][j][i], S.fx[m + 1][j][i]),
-                           make_float2(S.fx[m][j][i + 1], S.fx[m + 1][j][i + 1])), idx);
-      L = fma2(sub2(make_float2(S.fy[m][j][i], S.fy[m + 1][j][i]), make_float2(S.fy[m][j + 1][i], S.fy[m + 1][j + 1][i])),
-               idy, L);
-      if (m >= 4) L = fma2(make_float2(S.q[m][j + NG][i + NG], S.q[m + 1][j + NG][i + NG]), f2(div_u), L);
-      inc[k] = L;
+      for (int m = M0; m < NQ; m += 2) {
+        float2 L = mul2(sub2(make_float2(S.fx[m][j][i], S.fx[m + 1][j][i]),
+                             make_float2(S.fx[m][j][i + 1], S.fx[m + 1][j][i + 1])), idx);
+        L = fma2(sub2(fy2(m, j), fy2(m, j + 1)), idy, L);
+        if (m == NQ - 2) L = fma2(make_float2(S.q[m][qj][qi], S.q[m + 1][qj][qi]), f2(div_u), L);
+        inc[m] = L.x;
+        inc[m + 1] = L.y;
+      }
+    } else {  // z faces, added to the x + y part
+      const float2 idz = f2(a.idz);
+      float div_u = (S.fy[NQ][j + 1][i] - S.fy[NQ][j][i]) * a.idz;
+      if constexpr (M0 == 1) inc[0] = fmaf(S.fy[0][j][i] - S.fy[0][j + 1][i], a.idz, S.own.l[0][j][i]);
+#pragma unroll
+      for (int m = M0; m < NQ; m += 2) {
+        float2 L = fma2(sub2(fy2(m, j), fy2(m, j + 1)), idz, make_float2(S.own.l[m][j][i], S.own.l[m + 1][j][i]));
+        if (m == NQ - 2) L = fma2(make_float2(S.q[m][qj][qi], S.q[m + 1][qj][qi]), f2(div_u), L);
+        inc[m] = L.x;
+        inc[m + 1] = L.y;
+      }
     }
-    auto kin = [&](int m) { return CACHE ? S.own.k[m][j][i] : a.Kin[m * N + gi]; };
-    if (a.stage == 0) {
+    if constexpr (MODE == 1) {
 #pragma unroll
-      for (int k = 0; k < NQ / 2; ++k) {
-        a.Kout[2 * k * N + gi] = inc[k].x;
-        a.Kout[(2 * k + 1) * N + gi] = inc[k].y;
-      }
-    } else if (a.stage == 1) {
-#pragma unroll
-      for (int k = 0; k < NQ / 2; ++k) {
-        float2 K1 = add2(make_float2(kin(2 * k), kin(2 * k + 1)), inc[k]);
-        a.Kout[2 * k * N + gi] = K1.x;
-        a.Kout[(2 * k + 1) * N + gi] = K1.y;
-      }
+      for (int m = 0; m < NQ; ++m) a.Lp[m * N + gi] = inc[m];
     } else {
-      // this cell's U^n is read only here, by this thread, so U is updated in place
-      float d[NQ];
+      auto kin = [&](int m) { return CACHE ? S.own.k[m][j][i] : a.Kin[m * N + gi]; };
+      if (a.stage == 0) {
 #pragma unroll
-      for (int k = 0; k < NQ / 2; ++k) {
-        float2 dd = mul2(f2(dt), fma2(f2(1.0f / 6.0f), make_float2(kin(2 * k), kin(2 * k + 1)),
-                                      mul2(f2(2.0f / 3.0f), inc[k])));
-        d[2 * k] = dd.x;
-        d[2 * k + 1] = dd.y;
-      }
+        for (int m = 0; m < NQ; ++m) a.Kout[m * N + gi] = inc[m];
+      } else if (a.stage == 1) {
 #pragma unroll
-      for (int m = 0; m < NQ; ++m) {
-        double u = CACHE ? S.own.u[m][j][i] : a.U[m * N + gi];
-        a.U[m * N + gi] = u + f32_to_f64(d[m]);  // FP64 accumulation
+        for (int m = 0; m < NQ; ++m) a.Kout[m * N + gi] = kin(m) + inc[m];
+      } else {
+        // this cell's U^n is read only here, by this thread, so U is updated in place
+        float d[NQ];
+#pragma unroll
+        for (int m = 0; m < NQ; ++m) {
+          d[m] = dt * fmaf(1.0f / 6.0f, kin(m), (2.0f / 3.0f) * inc[m]);
+          double u = CACHE ? S.own.u[m][j][i] : a.U[m * N + gi];
+          a.U[m * N + gi] = u + f32_to_f64(d[m]);  // FP64 accumulation
+        }
+        // admissibility of the new state (rho > 0, Gamma > 0, (Gamma+1) p + Pi > 0)
+        // from its FP32 image: a diagnostic, not part of the update
+        auto v = [&](int m) { return CACHE ? S.own.v[m][j][i] : a.U32[m * N + gi]; };
+        float rho = v(0) + d[0];
+        float msq = 0.0f;
+#pragma unroll
+        for (int e = 0; e < ND; ++e) {
+          float me = v(1 + e) + d[1 + e];
+          msq = fmaf(me, me, msq);
+        }
+        float eint = v(NQ - 3) + (d[NQ - 3] - d[NQ - 1]), Gam = v(NQ - 2) + d[NQ - 2], Pi = v(NQ - 1) + d[NQ - 1];
+        float pe = fmaf(-0.5f, msq * frcp(rho), eint);  // Gamma p
+        bool ok = rho > 0.0f && Gam > 0.0f && fmaf(Gam + 1.0f, pe * frcp(Gam), Pi) > 0.0f;
+        if (!ok) atomicAdd(a.nbad, 1ULL);
       }
-      // admissibility of the new state (rho > 0, Gamma > 0, (Gamma+1) p + Pi > 0)
-      // from its FP32 image: a diagnostic, not part of the update
-      auto v = [&](int m) { return CACHE ? S.own.v[m][j][i] : a.U32[m * N + gi]; };
-      float rho = v(0) + d[0], mu = v(1) + d[1], mv = v(2) + d[2];
-      float eint = v(3) + (d[3] - d[5]), Gam = v(4) + d[4], Pi = v(5) + d[5];
-      float pe = fmaf(-0.5f, (mu * mu + mv * mv) * frcp(rho), eint);  // Gamma p
-      bool ok = rho > 0.0f && Gam > 0.0f && fmaf(Gam + 1.0f, pe * frcp(Gam), Pi) > 0.0f;
-      if (!ok) atomicAdd(a.nbad, 1ULL);
     }
   }
 }
@@ -814,25 +889,40 @@ void launch_restore(const int* redo, const double* src, double* dst, int64_t n, 
   k_restore<<<152 * 4, 256, 0, s>>>(redo, src, dst, n);
 }
 
-int fused2d_smem_bytes() { return (int)(sizeof(Smem<true>) + sizeof(SmemGate)); }
+using SmPlain2 = Smem<false, 6, 0>;
+using SmGated2 = Smem<true, 6, 0>;
+using SmPass1 = Smem<false, 7, 1>;
+using SmPass2 = Smem<false, 7, 2>;
+
+int fused2d_smem_bytes() { return (int)(sizeof(SmGated2) + sizeof(SmemGate)); }
 
 cudaError_t fused2d_prepare() {
-  cudaError_t e = cudaFuncSetAttribute(k_stage2d<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)sizeof(Smem<false>));
+  cudaError_t e = cudaFuncSetAttribute(k_stage<false, 6, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)sizeof(SmPlain2));
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_stage2d<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)(sizeof(Smem<true>) + sizeof(SmemGate)));
+  return cudaFuncSetAttribute(k_stage<true, 6, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)(sizeof(SmGated2) + sizeof(SmemGate)));
 }
 
-void launch_stage2d(const GridDev& g, int stage, double* U, float* U32, const float* Kin, float* Kout,
-                    double dt_fixed, double cfl, unsigned long long* lmax, double* dt_out, uint8_t* mask_x,
-                    uint8_t* mask_y, float eps_rel, int mood, int weights, unsigned long long* nbad,
-                    const GateArgs* gate, const int* run_if, cudaStream_t s) {
+int fused3d_smem_bytes() { return (int)(sizeof(SmPass1) > sizeof(SmPass2) ? sizeof(SmPass1) : sizeof(SmPass2)); }
+
+cudaError_t fused3d_prepare() {
+  cudaError_t e = cudaFuncSetAttribute(k_stage<false, 7, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)sizeof(SmPass1));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_stage<false, 7, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)sizeof(SmPass2));
+}
+
+static StageArgs stage_args(const GridDev& g, int stage, double* U, float* U32, const float* Kin, float* Kout,
+                            double dt_fixed, double cfl, unsigned long long* lmax, double* dt_out, float eps_rel,
+                            int mood, int weights, unsigned long long* nbad) {
   StageArgs a;
   a.g = g;
   a.stage = stage;
   a.idx = (float)(1.0 / g.dx[0]);
   a.idy = (float)(1.0 / g.dx[1]);
+  a.idz = (float)(1.0 / g.dx[2]);
   a.cfl = (float)cfl;
   a.dt_fixed = dt_fixed;
   a.lmax = lmax;
@@ -841,13 +931,31 @@ void launch_stage2d(const GridDev& g, int stage, double* U, float* U32, const fl
   a.U32 = U32;
   a.Kin = Kin;
   a.Kout = Kout;
-  a.mask_x = mask_x;
-  a.mask_y = mask_y;
+  a.Lp = nullptr;
+  a.mask_x = nullptr;
+  a.mask_a = nullptr;
   a.P = WenoParams{eps_rel, 1e-30f, weights};
   a.mood = mood;
   a.nbad = nbad;
-  dim3 grid((g.n[0] + TX - 1) / TX, (g.n[1] + TY - 1) / TY);
+  a.mlp_frag = nullptr;
+  a.mlp_bias = nullptr;
+  a.thr = 0.0f;
+  a.drift_tile = -1;
+  a.Ubackup = nullptr;
+  a.lstat = nullptr;
+  a.run_if = nullptr;
+  return a;
+}
+
+void launch_stage2d(const GridDev& g, int stage, double* U, float* U32, const float* Kin, float* Kout,
+                    double dt_fixed, double cfl, unsigned long long* lmax, double* dt_out, uint8_t* mask_x,
+                    uint8_t* mask_y, float eps_rel, int mood, int weights, unsigned long long* nbad,
+                    const GateArgs* gate, const int* run_if, cudaStream_t s) {
+  StageArgs a = stage_args(g, stage, U, U32, Kin, Kout, dt_fixed, cfl, lmax, dt_out, eps_rel, mood, weights, nbad);
+  a.mask_x = mask_x;
+  a.mask_a = mask_y;
   a.run_if = run_if;
+  dim3 grid((g.n[0] + TX - 1) / TX, (g.n[1] + TY - 1) / TY);
   if (gate) {
     a.mlp_frag = gate->frag;
     a.mlp_bias = gate->bias;
@@ -855,16 +963,28 @@ void launch_stage2d(const GridDev& g, int stage, double* U, float* U32, const fl
     a.drift_tile = gate->drift_tile;
     a.Ubackup = gate->Ubackup;
     a.lstat = gate->lstat;
-    k_stage2d<true><<<grid, NT, sizeof(Smem<true>) + sizeof(SmemGate), s>>>(a);
+    k_stage<true, 6, 0><<<grid, NT, sizeof(SmGated2) + sizeof(SmemGate), s>>>(a);
   } else {
-    a.mlp_frag = nullptr;
-    a.mlp_bias = nullptr;
-    a.thr = 0.0f;
-    a.drift_tile = -1;
-    a.Ubackup = nullptr;
-    a.lstat = nullptr;
-    k_stage2d<false><<<grid, NT, sizeof(Smem<false>), s>>>(a);
+    k_stage<false, 6, 0><<<grid, NT, sizeof(SmPlain2), s>>>(a);
   }
+}
+
+void launch_stage3d(const GridDev& g, int stage, double* U, float* U32, const float* Kin, float* Kout, float* Lp,
+                    double dt_fixed, double cfl, unsigned long long* lmax, double* dt_out, uint8_t* mask_x,
+                    uint8_t* mask_y, uint8_t* mask_z, float eps_rel, int mood, int weights, unsigned long long* nbad,
+                    cudaStream_t s) {
+  StageArgs a = stage_args(g, stage, U, U32, Kin, Kout, dt_fixed, cfl, lmax, dt_out, eps_rel, mood, weights, nbad);
+  a.Lp = Lp;
+  // pass 1: x and y faces of every z plane -> x + y part of the divergence
+  a.mask_x = mask_x;
+  a.mask_a = mask_y;
+  dim3 g1((g.n[0] + TX - 1) / TX, (g.n[1] + TY - 1) / TY, g.n[2]);
+  k_stage<false, 7, 1><<<g1, NT, sizeof(SmPass1), s>>>(a);
+  // pass 2: z faces of every y plane, the whole divergence and the RK stage
+  a.mask_x = nullptr;
+  a.mask_a = mask_z;
+  dim3 g2((g.n[0] + TX - 1) / TX, (g.n[2] + TY - 1) / TY, g.n[1]);
+  k_stage<false, 7, 2><<<g2, NT, sizeof(SmPass2), s>>>(a);
 }
 
 }  // namespace ws

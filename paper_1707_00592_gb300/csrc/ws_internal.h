@@ -52,9 +52,10 @@ struct ws_ctx {
   double* S1 = nullptr;         // RK stage state
   double* Q = nullptr;          // primitives + sound speed, nv+1 fields
   float* Q32 = nullptr;         // mixed precision: FP32 primitives + sound speed
-  float* Ka = nullptr;          // fused 2D: RK increments K0 (stage 0 -> 1)
-  float* Kb = nullptr;          // fused 2D: RK increments K1 (stage 1 -> 2)
-  bool fused = false;           // fused 2D mixed-precision stage kernels in use
+  float* Ka = nullptr;          // fused: RK increments K0 (stage 0 -> 1)
+  float* Kb = nullptr;          // fused: RK increments K1 (stage 1 -> 2)
+  float* Lp = nullptr;          // fused 3D: x + y part of the divergence (first pass -> second)
+  bool fused = false;           // fused mixed-precision stage kernels in use (2D or 3D)
   double* Fh[3] = {nullptr, nullptr, nullptr};  // face fluxes per direction (nv fields)
   double* us[3] = {nullptr, nullptr, nullptr};  // face velocities per direction
   float* Fh32[3] = {nullptr, nullptr, nullptr}; // mixed precision face fluxes
@@ -139,7 +140,7 @@ struct GateArgs {
   float thr;           // logit threshold (smooth when below)
   int drift_tile;      // tile residue (mod 64) of this step's drift check
   double* Ubackup;     // stage 0 copies U here
-  float* lstat;        // gate statistics, see k_stage2d
+  float* lstat;        // gate statistics, see k_stage
 };
 int fused2d_smem_bytes();
 cudaError_t fused2d_prepare();
@@ -147,6 +148,14 @@ void launch_stage2d(const GridDev& g, int stage, double* U, float* U32, const fl
                     double dt_fixed, double cfl, unsigned long long* lmax, double* dt_out, uint8_t* mask_x,
                     uint8_t* mask_y, float eps_rel, int mood, int weights, unsigned long long* nbad,
                     const GateArgs* gate, const int* run_if, cudaStream_t s);
+// 3D: per stage two launches (x and y faces of every z plane, then z faces of
+// every y plane with the RK stage); Lp holds the x + y part of the divergence
+int fused3d_smem_bytes();
+cudaError_t fused3d_prepare();
+void launch_stage3d(const GridDev& g, int stage, double* U, float* U32, const float* Kin, float* Kout, float* Lp,
+                    double dt_fixed, double cfl, unsigned long long* lmax, double* dt_out, uint8_t* mask_x,
+                    uint8_t* mask_y, uint8_t* mask_z, float eps_rel, int mood, int weights, unsigned long long* nbad,
+                    cudaStream_t s);
 void launch_gate_decide(const float* lstat, unsigned long long* nbad, unsigned long long* lmax, int flags, int* redo,
                         double* stats, cudaStream_t s);
 void launch_restore(const int* redo, const double* src, double* dst, int64_t n, cudaStream_t s);
