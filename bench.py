@@ -253,6 +253,69 @@ def time_tubes(ws, stream, steps, seed=0):
             "workload": "4096 Riemann tubes, lengths log-uniform in [256, 8192], per-tube CFL, mixed precision"}
 
 
+def time_drop3d(ws, stream, steps, peak, n=256, l1_n=96, l1_steps=20):
+    """The 3D configuration: the periodic water drop with density noise on n^3,
+    mixed precision through the fused 3D stage (two launches per RK stage).
+    Also: pressure equilibrium after the timed steps, and the L1 density error
+    against the FP64 path (bit-identical to the FP64 oracle) on l1_n^3 after
+    l1_steps steps with the FP64 path's CFL time steps."""
+    import torch
+    case = wl.drop_3d(n, seed=0)
+    s = ws.Solver(3, case.n, case.dx, case.bc, precision="mixed", stream=stream)
+    with torch.cuda.stream(stream):
+        U = s.prim_to_cons(s.tensor(case.Q))
+        del case
+        for _ in range(3):
+            s.step(U)
+        ws.ws_profile(s.ctx, True)
+        ms = 0.0
+        for _ in range(steps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            s.step(U)
+            b.record(stream)
+            b.synchronize()
+            ms += a.elapsed_time(b)
+        face_ms, face_n = ws.ws_profile_read(s.ctx)["face"]
+        ws.ws_profile(s.ctx, False)
+        Q = s.cons_to_prim(U)
+        sl = wl.interior(3, (n, n, n))
+        dp = float((Q[sl][4] / 1e5 - 1.0).abs().max().item())
+        del Q
+        bad = s.nonphysical()
+    s.close()
+    del U
+    torch.cuda.empty_cache()
+    # L1 against the FP64 path on a smaller grid
+    small = wl.drop_3d(l1_n, seed=0)
+    s64 = ws.Solver(3, small.n, small.dx, small.bc, precision="fp64", stream=stream)
+    s32 = ws.Solver(3, small.n, small.dx, small.bc, precision="mixed", stream=stream)
+    with torch.cuda.stream(stream):
+        U64 = s64.prim_to_cons(s64.tensor(small.Q))
+        U32 = s32.prim_to_cons(s32.tensor(small.Q))
+        for _ in range(l1_steps):
+            dt = s64.step(U64, want_dt=True)
+            s32.step(U32, dt)
+        torch.cuda.synchronize()
+        sl = wl.interior(3, small.n)
+        l1 = float(((U32[sl][0] - U64[sl][0]).abs().sum() / U64[sl][0].abs().sum()).item())
+    s64.close()
+    s32.close()
+    cells = n ** 3
+    faces_per_stage = 3 * (n + 1) * n * n
+    achieved = face_flops(3) * faces_per_stage * 3 * steps / (face_ms * 1e-3) / 1e12
+    return {"value": cells * steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps, "steps": steps,
+            "workload": f"drop_3d_{n}^3 (periodic water drop r=0.25 in air, 1% density noise, seed 0), mixed",
+            "l2": f"state {cells * 7 * 8 / 1e9:.2f} GB, larger than L2",
+            "gpu_launches": int(face_n),
+            "roofline": {"bound": "alu", "kernel": "fused 3D RK stage, both passes", "achieved": achieved,
+                         "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                         "flops_per_face": face_flops(3), "faces_per_stage": faces_per_stage,
+                         "share_of_step": face_ms / ms},
+            "pressure_equilibrium_max_rel_dev": dp, "nonphysical_cells": bad,
+            "l1_density_vs_fp64": {"grid": [l1_n] * 3, "steps": l1_steps, "value": l1}}
+
+
 def time_learned(ws, case, stream, steps, run_steps, warmup):
     """The learned smooth-face gate on the same run: trained on the GPU by the
     library's kernels, then timed like the plain mixed path, with its L1 density
@@ -364,6 +427,10 @@ def run_ours(args):
         if args.precision == "mixed" and args.fp64_steps > 0:
             fp64_cmp = time_fp64(ws, case, stream, args.fp64_steps)
         tubes = time_tubes(ws, stream, args.tube_steps) if args.tube_steps > 0 else None
+        drop = None
+        if args.drop_steps > 0 and args.precision == "mixed":
+            p32 = args.fp32_peak if args.fp32_peak is not None else ws.ws_peak_probe("fp32")
+            drop = time_drop3d(ws, stream, args.drop_steps, p32, n=args.drop_n)
         gate = (time_learned(ws, case, stream, args.steps, args.run_steps, args.warmup)
                 if args.learned and args.precision == "mixed" else None)
 
@@ -419,6 +486,8 @@ def run_ours(args):
         line["fp64_plain"] = fp64_cmp
     if tubes is not None:
         line["batched_tubes"] = tubes
+    if drop is not None:
+        line["drop_3d"] = drop
     if gate is not None:
         line["learned_gate"] = gate
     if ws_size == 1 and not args.no_cpu_baseline:
@@ -449,6 +518,8 @@ def main():
     ap.add_argument("--l1-steps", type=int, default=200)
     ap.add_argument("--run-steps", type=int, default=2000)
     ap.add_argument("--tube-steps", type=int, default=10)
+    ap.add_argument("--drop-steps", type=int, default=10)
+    ap.add_argument("--drop-n", type=int, default=256)
     ap.add_argument("--learned", type=int, default=1)
     ap.add_argument("--fp64-steps", type=int, default=5)
     args = ap.parse_args()
