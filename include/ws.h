@@ -208,11 +208,18 @@ WS_API int ws_mlp_adam(float *params, float *m, float *v, const float *grad, int
  * inadmissible, if (flags & WS_GATE_REDO_DRIFT) on the 1/64 of the tiles
  * checked that step (rotating) the linear-weight face values differ from
  * WENO-IS by more than 1e-6 in relative L1, or if (flags &
- * WS_GATE_REDO_MOOD) any gated face needed the MOOD cascade.  Resets the
- * statistics of ws_gate_stats. */
+ * WS_GATE_REDO_MOOD) any gated face needed the MOOD cascade.  With (flags &
+ * WS_GATE_PER_STEP) the MLP runs once per step, on U^n in RK stage 0, and
+ * stages 1 and 2 apply the same decisions to their intermediate states (which
+ * lie within a CFL fraction of a cell of U^n); the drift check still runs in
+ * every stage.  Without it the MLP runs in every stage.  On a context created
+ * with a stream, a gated step is one CUDA graph launch whose redo branch is a
+ * conditional node set by the device.  Resets the statistics of
+ * ws_gate_stats. */
 #define WS_GATE_REDO_MOOD 1
 #define WS_GATE_REDO_DRIFT 2
 #define WS_GATE_REDO_NONPHYS 4
+#define WS_GATE_PER_STEP 8
 WS_API int ws_set_mlp(ws_ctx *ctx, const float *params, float threshold, int flags);
 
 /* The gate's decisions on state U (DEVICE): smooth (DEVICE, ws_mask_size()

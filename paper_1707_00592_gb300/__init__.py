@@ -239,7 +239,7 @@ def ws_mlp_adam(params, m, v, grad, step, lr, stream=None):
         raise WsError(rc, "ws_mlp_adam failed")
 
 
-GATE_REDO_MOOD, GATE_REDO_DRIFT, GATE_REDO_NONPHYS = 1, 2, 4
+GATE_REDO_MOOD, GATE_REDO_DRIFT, GATE_REDO_NONPHYS, GATE_PER_STEP = 1, 2, 4, 8
 
 
 def ws_set_mlp(ctx, params, threshold: float, flags: int = GATE_REDO_DRIFT | GATE_REDO_NONPHYS):

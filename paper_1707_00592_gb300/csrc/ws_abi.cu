@@ -104,6 +104,10 @@ void free_all(ws_ctx* c) {
   c->ev.clear();
   if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
   c->graph_exec = nullptr;
+  if (c->ggraph_exec) cudaGraphExecDestroy(c->ggraph_exec);
+  c->ggraph_exec = nullptr;
+  cudaFree(c->gate_drift);
+  cudaFree(c->gate_tile_flags);
   cudaFree(c->mlp_frag);
   cudaFree(c->mlp_bias);
   cudaFree(c->lstat);
@@ -203,6 +207,33 @@ int tube_rhs(ws_ctx* c, double* Us, int stage_slot, bool cfl) {
   return check_launch(c, "tube sweep");
 }
 
+// The three fused RK stages (the CFL reduction happens inside stage 0, dt is
+// derived in stage 1).  run_if: the stages run only if *run_if != 0.
+int fused_run3(ws_ctx* c, double* U, double dt, const GateArgs* gate, const int* run_if) {
+  const GridDev& g = c->gd;
+  if (!run_if) CK(c, cudaMemsetAsync(c->lmax, 0, sizeof(unsigned long long), c->stream));
+  for (int s = 0; s < 3; ++s) {
+    uint8_t* mb = c->mask + (int64_t)s * c->nmask;
+    KScope k(c, WS_K_FACE, g.ndim == 3 ? 2 : 1);
+    const float* Kin = s == 1 ? c->Ka : c->Kb;
+    float* Kout = s == 0 ? c->Ka : c->Kb;
+    if (g.ndim == 3)
+      launch_stage3d(g, s, U, c->Q32, Kin, Kout, c->Lp, dt, c->opts.cfl, c->lmax, c->dt_dev, mb + c->mask_off[0],
+                     mb + c->mask_off[1], mb + c->mask_off[2], (float)c->opts.eps, c->opts.mood, c->opts.weights,
+                     c->nbad, c->stream);
+    else
+      launch_stage2d(g, s, U, c->Q32, Kin, Kout, dt, c->opts.cfl, c->lmax, c->dt_dev, mb + c->mask_off[0],
+                     mb + c->mask_off[1], (float)c->opts.eps, c->opts.mood, c->opts.weights, c->nbad, gate, run_if,
+                     c->stream);
+  }
+  return check_launch(c, "fused stage");
+}
+
+GateArgs gate_args(ws_ctx* c) {
+  return GateArgs{c->mlp_frag, c->mlp_bias, c->mlp_thr, -1, c->S1, c->lstat,
+                  (c->gate_flags & WS_GATE_PER_STEP) ? c->gate_tile_flags : nullptr, c->gate_drift};
+}
+
 int step_device(ws_ctx* c, double* U, double dt) {
   const GridDev& g = c->gd;
   int rc;
@@ -241,40 +272,21 @@ int step_device(ws_ctx* c, double* U, double dt) {
     return WS_OK;
   }
   if (c->fused) {
-    // the CFL reduction happens inside stage 0, dt is derived in stage 1
-    auto run3 = [&](const GateArgs* gate, const int* run_if) -> int {
-      if (!run_if) CK(c, cudaMemsetAsync(c->lmax, 0, sizeof(unsigned long long), c->stream));
-      for (int s = 0; s < 3; ++s) {
-        uint8_t* mb = c->mask + (int64_t)s * c->nmask;
-        KScope k(c, WS_K_FACE, g.ndim == 3 ? 2 : 1);
-        const float* Kin = s == 1 ? c->Ka : c->Kb;
-        float* Kout = s == 0 ? c->Ka : c->Kb;
-        if (g.ndim == 3)
-          launch_stage3d(g, s, U, c->Q32, Kin, Kout, c->Lp, dt, c->opts.cfl, c->lmax, c->dt_dev, mb + c->mask_off[0],
-                         mb + c->mask_off[1], mb + c->mask_off[2], (float)c->opts.eps, c->opts.mood,
-                         c->opts.weights, c->nbad, c->stream);
-        else
-          launch_stage2d(g, s, U, c->Q32, Kin, Kout, dt, c->opts.cfl, c->lmax, c->dt_dev, mb + c->mask_off[0],
-                         mb + c->mask_off[1], (float)c->opts.eps, c->opts.mood, c->opts.weights, c->nbad, gate,
-                         run_if, c->stream);
-      }
-      return check_launch(c, "fused stage");
-    };
     if (!c->learned_on) {
-      if ((rc = run3(nullptr, nullptr))) return rc;
+      if ((rc = fused_run3(c, U, dt, nullptr, nullptr))) return rc;
     } else {
       // gated step, then on the device: keep or redo it without the gate
       // (restored from the backup taken in stage 0), with no host round trip
-      GateArgs ga{c->mlp_frag, c->mlp_bias, c->mlp_thr, (int)(c->gate_steps & 63), c->S1, c->lstat};
+      GateArgs ga = gate_args(c);
       CK(c, cudaMemsetAsync(c->lstat, 0, 8 * sizeof(float), c->stream));
-      if ((rc = run3(&ga, nullptr))) return rc;
+      if ((rc = fused_run3(c, U, dt, &ga, nullptr))) return rc;
       {
         KScope k(c, WS_K_OTHER, 2);
-        launch_gate_decide(c->lstat, c->nbad, c->lmax, c->gate_flags, c->gate_redo, c->gate_stats, c->stream);
+        launch_gate_decide(c->lstat, c->nbad, c->lmax, c->gate_flags, c->gate_redo, c->gate_stats, c->gate_drift, 0,
+                           c->stream);
         launch_restore(c->gate_redo, c->S1, U, c->nstate, c->stream);
       }
-      if ((rc = run3(nullptr, c->gate_redo))) return rc;
-      c->gate_steps++;
+      if ((rc = fused_run3(c, U, dt, nullptr, c->gate_redo))) return rc;
     }
     c->last_stages = 3;
     return WS_OK;
@@ -566,10 +578,95 @@ int step_graph(ws_ctx* c, double* U) {
   return WS_OK;
 }
 
+// The gated step as one graph: the gated stages and the decision kernel, then
+// an IF node whose body (restore U from the stage-0 backup, the three plain
+// stages) runs only when the decision kernel sets its condition.  Rebuilt when
+// U, dt or the gate change.
+int gated_step_graph(ws_ctx* c, double* U, double dt) {
+  if (!c->ggraph_exec || c->ggraph_U != U || c->ggraph_dt != dt) {
+    if (c->ggraph_exec) {
+      CK(c, cudaGraphExecDestroy(c->ggraph_exec));
+      c->ggraph_exec = nullptr;
+    }
+    cudaGraph_t g = nullptr;
+    CK(c, cudaGraphCreate(&g, 0));
+    struct GraphGuard {
+      cudaGraph_t g;
+      ~GraphGuard() {
+        if (g) cudaGraphDestroy(g);
+      }
+    } guard{g};
+    cudaGraphConditionalHandle cond;
+    CK(c, cudaGraphConditionalHandleCreate(&cond, g, 0, cudaGraphCondAssignDefault));
+    // main part: the gated stages and the decision
+    CK(c, cudaStreamBeginCaptureToGraph(c->stream, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    int rc = WS_OK;
+    {
+      cudaError_t e1 = cudaMemsetAsync(c->nbad, 0, sizeof(unsigned long long), c->stream);
+      cudaError_t e2 = cudaMemsetAsync(c->lstat, 0, 8 * sizeof(float), c->stream);
+      GateArgs ga = gate_args(c);
+      if (e1 != cudaSuccess || e2 != cudaSuccess) rc = fail(c, WS_ECUDA, "memset in capture failed");
+      if (!rc) rc = fused_run3(c, U, dt, &ga, nullptr);
+      if (!rc) {
+        launch_gate_decide(c->lstat, c->nbad, c->lmax, c->gate_flags, c->gate_redo, c->gate_stats, c->gate_drift,
+                           cond, c->stream);
+        rc = check_launch(c, "gate decision");
+      }
+    }
+    cudaGraph_t cap = nullptr;
+    cudaError_t e = cudaStreamEndCapture(c->stream, &cap);
+    if (rc) return rc;
+    if (e != cudaSuccess) return fail(c, WS_ECUDA, "capture of the gated step failed: %s", cudaGetErrorString(e));
+    // the decision kernel is the one node without dependents
+    size_t nn = 0;
+    CK(c, cudaGraphGetNodes(g, nullptr, &nn));
+    std::vector<cudaGraphNode_t> nodes(nn);
+    CK(c, cudaGraphGetNodes(g, nodes.data(), &nn));
+    cudaGraphNode_t leaf = nullptr;
+    int nleaf = 0;
+    for (size_t i = 0; i < nn; ++i) {
+      size_t nd = 0;
+      CK(c, cudaGraphNodeGetDependentNodes(nodes[i], nullptr, nullptr, &nd));
+      if (nd == 0) {
+        leaf = nodes[i];
+        ++nleaf;
+      }
+    }
+    if (nleaf != 1) return fail(c, WS_ECUDA, "gated step graph: %d leaf nodes", nleaf);
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = cond;
+    cp.conditional.type = cudaGraphCondTypeIf;
+    cp.conditional.size = 1;
+    cudaGraphNode_t cnode;
+    CK(c, cudaGraphAddNode(&cnode, g, &leaf, nullptr, 1, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    // redo branch
+    CK(c, cudaStreamBeginCaptureToGraph(c->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    launch_restore(c->gate_redo, c->S1, U, c->nstate, c->stream);
+    rc = check_launch(c, "restore");
+    if (!rc) rc = fused_run3(c, U, dt, nullptr, nullptr);
+    e = cudaStreamEndCapture(c->stream, &cap);
+    if (rc) return rc;
+    if (e != cudaSuccess) return fail(c, WS_ECUDA, "capture of the redo branch failed: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&c->ggraph_exec, g, 0);
+    if (e != cudaSuccess) {
+      c->ggraph_exec = nullptr;
+      return fail(c, WS_ECUDA, "gated step graph instantiation failed: %s", cudaGetErrorString(e));
+    }
+    c->ggraph_U = U;
+    c->ggraph_dt = dt;
+  }
+  CK(c, cudaGraphLaunch(c->ggraph_exec, c->stream));
+  c->last_stages = 3;
+  return WS_OK;
+}
+
 int ws_step(ws_ctx* c, double* U, double dt, double* dt_used) {
   if (!c || !U) return fail(c, WS_EINVAL, "bad pointers");
   bool graph = c->graph_on && dt <= 0.0 && c->stream != nullptr && !c->prof_on && !c->learned_on;
-  int rc = graph ? step_graph(c, U) : step_device(c, U, dt);
+  bool ggraph = c->learned_on && c->fused && c->stream != nullptr && !c->prof_on;
+  int rc = ggraph ? gated_step_graph(c, U, dt) : graph ? step_graph(c, U) : step_device(c, U, dt);
   if (rc) return rc;
   if (dt_used) {
     int64_t n = tubes(c) ? c->td.ntubes : 1;
@@ -682,6 +779,10 @@ int ws_set_mlp(ws_ctx* c, const float* params, float threshold, int flags) {
   if (!c) return fail(c, WS_EINVAL, "null context");
   if (!params) {
     c->learned_on = false;
+    if (c->ggraph_exec) {
+      cudaGraphExecDestroy(c->ggraph_exec);
+      c->ggraph_exec = nullptr;
+    }
     return WS_OK;
   }
   if (!c->fused || c->gd.ndim != 2)
@@ -710,20 +811,28 @@ int ws_set_mlp(ws_ctx* c, const float* params, float threshold, int flags) {
         (rc = dalloc(c, &c->lstat, 8)) || (rc = dalloc(c, &c->gate_redo, 1)) || (rc = dalloc(c, &c->gate_stats, 6)))
       return rc;
   }
+  if ((flags & WS_GATE_PER_STEP) && !c->gate_tile_flags &&
+      (rc = dalloc(c, &c->gate_tile_flags, fused2d_gate_flag_bytes(c->gd))))
+    return rc;
   CK(c, cudaMemset(c->gate_stats, 0, 6 * sizeof(double)));
   CK(c, cudaMemcpy(c->mlp_frag, F.data(), F.size() * 4, cudaMemcpyHostToDevice));
   CK(c, cudaMemcpy(c->mlp_bias, B.data(), 65 * sizeof(float), cudaMemcpyHostToDevice));
   c->mlp_thr = threshold;
   c->gate_flags = flags;
   c->learned_on = true;
-  c->gate_steps = 0;
+  if (!c->gate_drift && (rc = dalloc(c, &c->gate_drift, 1))) return rc;
+  CK(c, cudaMemset(c->gate_drift, 0, sizeof(int)));
+  if (c->ggraph_exec) {  // parameters baked into the gated step graph changed
+    CK(c, cudaGraphExecDestroy(c->ggraph_exec));
+    c->ggraph_exec = nullptr;
+  }
   return WS_OK;
 }
 
 int ws_gate_eval(ws_ctx* c, double* U, uint8_t* smooth) {
   if (!c || !U || !smooth) return fail(c, WS_EINVAL, "bad pointers");
   if (!c->learned_on) return fail(c, WS_EINVAL, "no gate set (ws_set_mlp)");
-  GateArgs ga{c->mlp_frag, c->mlp_bias, c->mlp_thr, -1, c->S1, c->lstat};
+  GateArgs ga{c->mlp_frag, c->mlp_bias, c->mlp_thr, -1, c->S1, c->lstat, nullptr, nullptr};
   CK(c, cudaMemsetAsync(smooth, 0, (size_t)c->nmask, c->stream));
   launch_stage2d(c->gd, 3, U, c->Q32, c->Ka, c->Kb, 0.0, c->opts.cfl, c->lmax, c->dt_dev, smooth,
                  smooth + c->mask_off[1], (float)c->opts.eps, c->opts.mood, c->opts.weights, c->nbad, &ga, nullptr,

@@ -79,10 +79,12 @@ constexpr int NFRAG1 = 2 * 4, NFRAG2 = 2 * 4, NFRAG3 = 2;  // (k-step, n-tile) p
 constexpr int NFRAG = NFRAG1 + NFRAG2 + NFRAG3;
 constexpr int NMT = (NF + 15) / 16;  // 16-face M tiles
 
-template <bool LEARNED, int NQ_, int MODE>
+// GATE: 0 plain; 1 the learned gate evaluates the MLP in this launch; 2 the
+// launch applies decisions stored by an earlier stage of the same step.
+template <int GATE, int NQ_, int MODE>
 struct Smem {
   using T = Tr<NQ_, MODE>;
-  static constexpr bool CACHE = !LEARNED && T::RK;  // own cells staged for phase C
+  static constexpr bool CACHE = GATE != 1 && T::RK;  // own cells staged for phase C
   float q[NQ_ + 1][HY][T::QW];                // primitives + sound speed of tile and halo
   float fx[T::XF ? NQ_ + 1 : 1][TY][TX + 1];  // x-face fluxes (global field order) + face velocity
   float fy[NQ_ + 1][TY + 1][TX];              // fluxes + face velocity of the faces along the tile's 2nd axis
@@ -93,7 +95,7 @@ struct Smem {
       float v[CACHE ? NQ_ : 1][TY][TX];          // stage 2: FP32 image of U^n (kept from the phase-A loads)
       float l[MODE == 2 ? NQ_ : 1][TY][TX];      // 3D second pass: x + y part of the divergence (asynchronous copy)
     } own;
-    __nv_bfloat16 feat[LEARNED ? NF : 1][24];    // learned kernel: gate inputs (read before the reconstruction)
+    __nv_bfloat16 feat[GATE == 1 ? NF : 1][24];  // gate inputs (read before the reconstruction)
   };
   unsigned long long red[NT / 32];  // per-warp CFL maxima
   float dt;                         // the step, broadcast from thread 0
@@ -104,6 +106,7 @@ struct SmemGate {
   float b1[32], b2[32], b3;         // biases
   uint8_t smooth[NF];               // 1: the face takes the linear weights
   float red[4][NT / 32];             // per-warp sums: |linear - WENO-IS|, |WENO-IS|, smooth faces, faces
+  float dpart[2][NT];                // drift check, per thread: sum |linear - WENO-IS|, sum |WENO-IS|
 };
 
 struct StageArgs {
@@ -129,10 +132,13 @@ struct StageArgs {
   const float* mlp_bias;   // b1[32], b2[32], b3
   float thr;               // logit threshold: smooth when logit < thr
   int drift_tile;          // tiles with (tile id % 64) == drift_tile run the drift check
+  const int* drift_dev;    // nullable: the drift tile residue in device memory (overrides drift_tile)
   double* Ubackup;         // stage 0: copy of U (for a plain redo)
   float* lstat;            // [0] gated faces failing MOOD, [1] drift |lin - full|, [2] drift |full|,
                            // [3] smooth-gated faces, [4] gated faces examined
   const int* run_if;       // nullable: the CTA returns at once when *run_if == 0
+  uint8_t* gflags;         // nullable: per-tile gate decisions (NF bytes per tile), written when the
+                           // MLP runs, read by launches that reuse them
 };
 
 // interior index along an axis of n cells for a (possibly out-of-range)
@@ -230,16 +236,17 @@ __device__ __forceinline__ void project_pairs(const float* qb, const FaceGeo<T::
 // 5th-order reconstruction of variable R on both sides of a face.  A
 // stencil flat to 1e-6 of its magnitude (a few FP32 ulps: rounding noise)
 // takes the linear weights, from which WENO-IS differs there by less than
-// the stencil's range; elsewhere WENO-IS.
+// the stencil's range; elsewhere WENO-IS.  linear: the learned gate sent the
+// face to the linear weights (one branch serves both reasons).
 template <class T, int R>
 __device__ __forceinline__ void weno_item(const float* qb, const FaceGeo<T::NTG>& fg, const FaceAvg& fa,
-                                          const WenoParams& P, float& l5, float& r5) {
+                                          const WenoParams& P, float& l5, float& r5, bool linear = false) {
   float2 p[5];
   project_pairs<T, R>(qb, fg, fa, p);
   float mn = fminf(fmin3(p[0].x, p[1].x, p[2].x), fmin3(p[2].y, p[1].y, p[0].y));
   float mx = fmaxf(fmax3(p[0].x, p[1].x, p[2].x), fmax3(p[2].y, p[1].y, p[0].y));
   float2 v;
-  if (mx - mn <= 1e-6f * fmaxf(fabsf(mx), fabsf(mn)))
+  if (linear || mx - mn <= 1e-6f * fmaxf(fabsf(mx), fabsf(mn)))
     v = linear5_pair(p[0], p[1], p[2], p[3], p[4]);
   else
     v = weno5_pair(p[0], p[1], p[2], p[3], p[4], P);
@@ -247,15 +254,22 @@ __device__ __forceinline__ void weno_item(const float* qb, const FaceGeo<T::NTG>
   r5 = v.y;
 }
 
-// 5th-order linear-weight reconstruction of variable R on both sides
+// A gated variable on a drift-check tile: the linear-weight values (which
+// the face uses) and WENO-IS, whose difference is added to acc[0] and the
+// WENO-IS magnitude to acc[NT] (the calling thread's own shared-memory
+// slots).  Out of line, so that the common path keeps its registers.
 template <class T, int R>
-__device__ __forceinline__ void linear_item(const float* qb, const FaceGeo<T::NTG>& fg, const FaceAvg& fa, float& l5,
-                                            float& r5) {
+__device__ __noinline__ void drift_item(const float* qb, const FaceGeo<T::NTG> fg, const FaceAvg fa,
+                                        const WenoParams P, float* acc, float& l5, float& r5) {
   float2 p[5];
   project_pairs<T, R>(qb, fg, fa, p);
-  float2 v = linear5_pair(p[0], p[1], p[2], p[3], p[4]);
-  l5 = v.x;
-  r5 = v.y;
+  float2 lin = linear5_pair(p[0], p[1], p[2], p[3], p[4]);
+  float fl, fr;
+  weno_item<T, R>(qb, fg, fa, P, fl, fr);
+  acc[0] += fabsf(lin.x - fl) + fabsf(lin.y - fr);
+  acc[NT] += fabsf(fl) + fabsf(fr);
+  l5 = lin.x;
+  r5 = lin.y;
 }
 
 // Characteristic variable R of the six stencil cells, one value per cell
@@ -368,10 +382,11 @@ __device__ __forceinline__ void cp_async8(void* dst, const void* src) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
-template <bool LEARNED, int NQ_, int MODE>
+template <int GATE, int NQ_, int MODE>
 __global__ void __launch_bounds__(NT, 2) k_stage(StageArgs a) {
   using T = Tr<NQ_, MODE>;
-  using SM = Smem<LEARNED, NQ_, MODE>;
+  using SM = Smem<GATE, NQ_, MODE>;
+  constexpr bool LEARNED = GATE != 0;  // faces may take the linear weights by the gate's decision
   constexpr int NQ = NQ_, ND = T::ND, FS = T::FS;
   constexpr bool CACHE = SM::CACHE;
   // axes: x, the tile's 2nd axis (y; z in pass 2), the plane axis (z; y in pass 2; none in 2D)
@@ -416,6 +431,15 @@ __global__ void __launch_bounds__(NT, 2) k_stage(StageArgs a) {
   const float dt = (a.stage == 1 || a.stage == 2) ? S.dt : 0.0f;
   const float coef = a.stage == 0 ? 0.0f : (a.stage == 1 ? dt : 0.25f * dt);
   float lam_max = 0.0f;
+
+  if (LEARNED) {  // this thread's drift sums (only it touches them until after phase B)
+    SG.dpart[0][tid] = 0.0f;
+    SG.dpart[1][tid] = 0.0f;
+  }
+  if constexpr (GATE == 2) {  // this step's decisions, stored by its stage 0
+    const uint8_t* fl = a.gflags + (int64_t)(blockIdx.y * gridDim.x + blockIdx.x) * NF;
+    for (int f = tid; f < NF; f += NT) SG.smooth[f] = fl[f];
+  }
 
   // ---- phase A: stage-state primitives of tile + halo ----
   // A thread owns up to HPT q-tile cells; all their global loads are issued
@@ -535,7 +559,7 @@ __global__ void __launch_bounds__(NT, 2) k_stage(StageArgs a) {
   }
 
   // ---- phases G1, G2 (learned gate, 2D): features, then the BF16 tensor-core MLP ----
-  if constexpr (LEARNED) {
+  if constexpr (GATE == 1) {
     for (int i = tid; i < NFRAG * 32; i += NT) SG.frag[i / 32][i % 32] = a.mlp_frag[i];
     for (int i = tid; i < 65; i += NT) {
       float b = a.mlp_bias[i];
@@ -603,6 +627,10 @@ __global__ void __launch_bounds__(NT, 2) k_stage(StageArgs a) {
       }
     }
     __syncthreads();
+    if (a.gflags) {  // kept for the step's later stages
+      uint8_t* fl = a.gflags + (int64_t)(blockIdx.y * gridDim.x + blockIdx.x) * NF;
+      for (int f = tid; f < NF; f += NT) fl[f] = SG.smooth[f];
+    }
     if (a.stage == 3) {  // gate evaluation only: the decisions go to the mask arrays
       for (int f = tid; f < NF; f += NT) {
         bool isx;
@@ -621,8 +649,8 @@ __global__ void __launch_bounds__(NT, 2) k_stage(StageArgs a) {
   // back-projection, MOOD and HLLC.  The thread that reconstructs a face also
   // solves its Riemann problem, so no barrier separates the two and the
   // reconstructed characteristics stay in registers.
-  const bool drift = LEARNED && ((int)((blockIdx.y * gridDim.x + blockIdx.x) & 63) == a.drift_tile);
-  float dnum = 0.0f, dden = 0.0f, nsm = 0.0f, nval = 0.0f;
+  const bool drift = LEARNED && ((int)((blockIdx.y * gridDim.x + blockIdx.x) & 63) ==
+                                  (a.drift_dev ? *a.drift_dev : a.drift_tile));
   const float* q0 = &S.q[0][0][0];
 #pragma unroll 1
   for (int f = tid; f < T::NFP; f += NT) {
@@ -647,28 +675,13 @@ __global__ void __launch_bounds__(NT, 2) k_stage(StageArgs a) {
     float ic2 = rc * inv, irc = c2 * inv;  // 1/c^2, 1/(rho c)
     const FaceAvg fa{rc, -ic2};
     float wl[NQ], wr[NQ];  // reconstructed characteristics, left and right
-    if (LEARNED) {
-      nval += 1.0f;
-      nsm += sm ? 1.0f : 0.0f;
-    }
 #define WS_B1(R)                                                                 \
     if constexpr (R < NQ) {                                                      \
-      float l5, r5;                                                              \
       bool lin = LEARNED && R != 2 && sm; /* shear: always WENO-IS */            \
-      if (lin) linear_item<T, R>(qb, fg, fa, l5, r5);                            \
-      if (!lin || drift) {                                                       \
-        float fl, fr;                                                            \
-        weno_item<T, R>(qb, fg, fa, a.P, fl, fr);                                \
-        if (lin) {                                                               \
-          dnum += fabsf(l5 - fl) + fabsf(r5 - fr);                               \
-          dden += fabsf(fl) + fabsf(fr);                                         \
-        } else {                                                                 \
-          l5 = fl;                                                               \
-          r5 = fr;                                                               \
-        }                                                                        \
-      }                                                                          \
-      wl[R] = l5;                                                                \
-      wr[R] = r5;                                                                \
+      if (LEARNED && lin && drift)                                               \
+        drift_item<T, R>(qb, fg, fa, a.P, &SG.dpart[0][tid], wl[R], wr[R]);      \
+      else                                                                       \
+        weno_item<T, R>(qb, fg, fa, a.P, wl[R], wr[R], lin);                     \
     }
     WS_B1(0)
     WS_B1(1)
@@ -753,7 +766,16 @@ __global__ void __launch_bounds__(NT, 2) k_stage(StageArgs a) {
       }
     }
   }
-  if (LEARNED) {
+  if (LEARNED) {  // drift sums, faces examined, faces the gate sent to the linear weights
+    float nsm = 0.0f, nval = 0.0f;
+    for (int f = tid; f < T::NFP; f += NT) {
+      bool isx;
+      int hx, hy;
+      if (!face_geom<T::XF>(f, x0, y0, nx, n1, isx, hx, hy)) continue;
+      nval += 1.0f;
+      nsm += SG.smooth[f] ? 1.0f : 0.0f;
+    }
+    float dnum = SG.dpart[0][tid], dden = SG.dpart[1][tid];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       dnum += __shfl_xor_sync(0xffffffffu, dnum, o);
@@ -852,9 +874,10 @@ __global__ void __launch_bounds__(NT, 2) k_stage(StageArgs a) {
 }  // namespace
 
 // After a gated step: decide on the device whether to redo it without the gate
-// (no host round trip), and keep the gate statistics.
+// (no host round trip), keep the gate statistics, advance the drift-check tile
+// and, inside a step graph, set the condition of the graph's redo branch.
 static __global__ void k_gate_decide(const float* __restrict__ lstat, unsigned long long* nbad, unsigned long long* lmax,
-                              int flags, int* redo, double* stats) {
+                              int flags, int* redo, double* stats, int* drift_dev, cudaGraphConditionalHandle cond) {
   bool r = false;
   double drift = lstat[2] > 0.0f ? (double)lstat[1] / (double)lstat[2] : 0.0;
   if ((flags & WS_GATE_REDO_MOOD) && lstat[0] > 0.0f) r = true;
@@ -871,6 +894,8 @@ static __global__ void k_gate_decide(const float* __restrict__ lstat, unsigned l
     *nbad = 0ULL;
     *lmax = 0ULL;
   }
+  if (drift_dev) *drift_dev = (*drift_dev + 1) & 63;
+  if (cond) cudaGraphSetConditional(cond, r ? 1u : 0u);
 }
 
 static __global__ void k_restore(const int* __restrict__ redo, const double* __restrict__ src, double* __restrict__ dst,
@@ -881,36 +906,44 @@ static __global__ void k_restore(const int* __restrict__ redo, const double* __r
 }
 
 void launch_gate_decide(const float* lstat, unsigned long long* nbad, unsigned long long* lmax, int flags, int* redo,
-                        double* stats, cudaStream_t s) {
-  k_gate_decide<<<1, 1, 0, s>>>(lstat, nbad, lmax, flags, redo, stats);
+                        double* stats, int* drift_dev, cudaGraphConditionalHandle cond, cudaStream_t s) {
+  k_gate_decide<<<1, 1, 0, s>>>(lstat, nbad, lmax, flags, redo, stats, drift_dev, cond);
 }
 
 void launch_restore(const int* redo, const double* src, double* dst, int64_t n, cudaStream_t s) {
   k_restore<<<152 * 4, 256, 0, s>>>(redo, src, dst, n);
 }
 
-using SmPlain2 = Smem<false, 6, 0>;
-using SmGated2 = Smem<true, 6, 0>;
-using SmPass1 = Smem<false, 7, 1>;
-using SmPass2 = Smem<false, 7, 2>;
+using SmPlain2 = Smem<0, 6, 0>;
+using SmGated2 = Smem<1, 6, 0>;
+using SmReuse2 = Smem<2, 6, 0>;
+using SmPass1 = Smem<0, 7, 1>;
+using SmPass2 = Smem<0, 7, 2>;
 
 int fused2d_smem_bytes() { return (int)(sizeof(SmGated2) + sizeof(SmemGate)); }
 
 cudaError_t fused2d_prepare() {
-  cudaError_t e = cudaFuncSetAttribute(k_stage<false, 6, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(k_stage<0, 6, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)sizeof(SmPlain2));
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_stage<true, 6, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)(sizeof(SmGated2) + sizeof(SmemGate)));
+  e = cudaFuncSetAttribute(k_stage<1, 6, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(sizeof(SmGated2) + sizeof(SmemGate)));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_stage<2, 6, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)(sizeof(SmReuse2) + sizeof(SmemGate)));
+}
+
+int64_t fused2d_gate_flag_bytes(const GridDev& g) {
+  return (int64_t)((g.n[0] + TX - 1) / TX) * ((g.n[1] + TY - 1) / TY) * NF;
 }
 
 int fused3d_smem_bytes() { return (int)(sizeof(SmPass1) > sizeof(SmPass2) ? sizeof(SmPass1) : sizeof(SmPass2)); }
 
 cudaError_t fused3d_prepare() {
-  cudaError_t e = cudaFuncSetAttribute(k_stage<false, 7, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(k_stage<0, 7, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)sizeof(SmPass1));
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_stage<false, 7, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  return cudaFuncSetAttribute(k_stage<0, 7, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)sizeof(SmPass2));
 }
 
@@ -941,9 +974,11 @@ static StageArgs stage_args(const GridDev& g, int stage, double* U, float* U32, 
   a.mlp_bias = nullptr;
   a.thr = 0.0f;
   a.drift_tile = -1;
+  a.drift_dev = nullptr;
   a.Ubackup = nullptr;
   a.lstat = nullptr;
   a.run_if = nullptr;
+  a.gflags = nullptr;
   return a;
 }
 
@@ -961,11 +996,16 @@ void launch_stage2d(const GridDev& g, int stage, double* U, float* U32, const fl
     a.mlp_bias = gate->bias;
     a.thr = gate->thr;
     a.drift_tile = gate->drift_tile;
+    a.drift_dev = gate->drift_dev;
     a.Ubackup = gate->Ubackup;
     a.lstat = gate->lstat;
-    k_stage<true, 6, 0><<<grid, NT, sizeof(SmGated2) + sizeof(SmemGate), s>>>(a);
+    a.gflags = gate->flags;
+    if (gate->flags && (stage == 1 || stage == 2))  // decisions of this step's stage 0
+      k_stage<2, 6, 0><<<grid, NT, sizeof(SmReuse2) + sizeof(SmemGate), s>>>(a);
+    else
+      k_stage<1, 6, 0><<<grid, NT, sizeof(SmGated2) + sizeof(SmemGate), s>>>(a);
   } else {
-    k_stage<false, 6, 0><<<grid, NT, sizeof(SmPlain2), s>>>(a);
+    k_stage<0, 6, 0><<<grid, NT, sizeof(SmPlain2), s>>>(a);
   }
 }
 
@@ -979,12 +1019,12 @@ void launch_stage3d(const GridDev& g, int stage, double* U, float* U32, const fl
   a.mask_x = mask_x;
   a.mask_a = mask_y;
   dim3 g1((g.n[0] + TX - 1) / TX, (g.n[1] + TY - 1) / TY, g.n[2]);
-  k_stage<false, 7, 1><<<g1, NT, sizeof(SmPass1), s>>>(a);
+  k_stage<0, 7, 1><<<g1, NT, sizeof(SmPass1), s>>>(a);
   // pass 2: z faces of every y plane, the whole divergence and the RK stage
   a.mask_x = nullptr;
   a.mask_a = mask_z;
   dim3 g2((g.n[0] + TX - 1) / TX, (g.n[2] + TY - 1) / TY, g.n[1]);
-  k_stage<false, 7, 2><<<g2, NT, sizeof(SmPass2), s>>>(a);
+  k_stage<0, 7, 2><<<g2, NT, sizeof(SmPass2), s>>>(a);
 }
 
 }  // namespace ws

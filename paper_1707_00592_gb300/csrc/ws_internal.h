@@ -91,7 +91,11 @@ struct ws_ctx {
   float* lstat = nullptr;        // device gate statistics of the current step
   int* gate_redo = nullptr;      // device: redo flag of the current step
   double* gate_stats = nullptr;  // device: steps, redone, gated faces, faces, max drift, constant faces
-  int64_t gate_steps = 0;        // host step counter (drift-check tile rotation)
+  int* gate_drift = nullptr;     // device: drift-check tile residue, advanced after every gated step
+  uint8_t* gate_tile_flags = nullptr;     // WS_GATE_PER_STEP: stage-0 decisions per tile
+  cudaGraphExec_t ggraph_exec = nullptr;  // the gated step as a graph with a conditional redo branch
+  const double* ggraph_U = nullptr;
+  double ggraph_dt = 0.0;
   // CUDA graph of one CFL step (ws_set_graph)
   bool graph_on = false;
   cudaGraphExec_t graph_exec = nullptr;
@@ -141,7 +145,10 @@ struct GateArgs {
   int drift_tile;      // tile residue (mod 64) of this step's drift check
   double* Ubackup;     // stage 0 copies U here
   float* lstat;        // gate statistics, see k_stage
+  uint8_t* flags;      // nullable: per-tile decisions of stage 0, reused by stages 1 and 2
+  const int* drift_dev;  // nullable: drift tile residue in device memory (overrides drift_tile)
 };
+int64_t fused2d_gate_flag_bytes(const GridDev& g);
 int fused2d_smem_bytes();
 cudaError_t fused2d_prepare();
 void launch_stage2d(const GridDev& g, int stage, double* U, float* U32, const float* Kin, float* Kout,
@@ -157,7 +164,7 @@ void launch_stage3d(const GridDev& g, int stage, double* U, float* U32, const fl
                     uint8_t* mask_y, uint8_t* mask_z, float eps_rel, int mood, int weights, unsigned long long* nbad,
                     cudaStream_t s);
 void launch_gate_decide(const float* lstat, unsigned long long* nbad, unsigned long long* lmax, int flags, int* redo,
-                        double* stats, cudaStream_t s);
+                        double* stats, int* drift_dev, cudaGraphConditionalHandle cond, cudaStream_t s);
 void launch_restore(const int* redo, const double* src, double* dst, int64_t n, cudaStream_t s);
 
 // ---- batched tubes, mixed precision, persistent (ws_tubes_mixed.cu) ----

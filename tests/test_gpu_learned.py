@@ -184,10 +184,14 @@ def test_tensor_core_gate_matches_fp32_mlp():
     s.close()
 
 
-def test_gate_closed_equals_plain_step_bitwise():
+@pytest.mark.parametrize("per_step", [False, True])
+def test_gate_closed_equals_plain_step_bitwise(per_step):
     """With a threshold no logit falls below, every face keeps WENO-IS and the
-    gated kernel reproduces the plain fused kernel bit for bit."""
+    gated kernel reproduces the plain fused kernel bit for bit, whether the MLP
+    runs in every RK stage or once per step (stages 1 and 2 reusing stage 0's
+    decisions)."""
     from paper_1707_00592_gb300 import learned
+    flags = ws.GATE_REDO_DRIFT | ws.GATE_REDO_NONPHYS | (ws.GATE_PER_STEP if per_step else 0)
     case = wl.random_state(2, (70, 47), seed=8, kind="two_phase")
     Uo = oracle.prim_to_cons(2, case.Q)
     outs = []
@@ -195,7 +199,7 @@ def test_gate_closed_equals_plain_step_bitwise():
         s = ws.Solver(2, case.n, case.dx, case.bc, precision="mixed")
         if gated:
             P = torch.tensor(learned.init_params(1), dtype=torch.float32, device="cuda")
-            ws.ws_set_mlp(s.ctx, P, -1e30)
+            ws.ws_set_mlp(s.ctx, P, -1e30, flags)
         U = s.tensor(Uo)
         for _ in range(3):
             s.step(U)
@@ -233,6 +237,61 @@ def test_gate_open_without_redo_runs_linear_weights():
     assert np.abs(a - b).sum() / np.abs(b).sum() < 1e-5
 
 
+def test_gate_open_per_step_equals_per_stage_bitwise():
+    """Threshold above every logit: every stage's decisions are 'smooth', so
+    reusing stage 0's decisions in stages 1 and 2 gives the per-stage result
+    bit for bit (the reuse launches read the stored decisions and stage the
+    own cells in shared memory; the arithmetic is the same)."""
+    from paper_1707_00592_gb300 import learned
+    case = wl.random_state(2, (70, 47), seed=9, kind="smooth")  # linear weights stay stable here
+    Uo = oracle.prim_to_cons(2, case.Q)
+    outs = []
+    for flags in (0, ws.GATE_PER_STEP):
+        s = ws.Solver(2, case.n, case.dx, case.bc, precision="mixed")
+        P = torch.tensor(learned.init_params(1), dtype=torch.float32, device="cuda")
+        ws.ws_set_mlp(s.ctx, P, 1e30, flags)
+        U = s.tensor(Uo)
+        for _ in range(3):
+            s.step(U, 1e-7)
+        outs.append(U.cpu().numpy())
+        st = ws.ws_gate_stats(s.ctx)
+        assert st["steps"] == 3 and st["redone"] == 0 and st["smooth_faces"] > 0
+        s.close()
+    assert np.isfinite(outs[0]).all()
+    assert np.array_equal(outs[0], outs[1])
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_gate_redo_restores_and_equals_plain(graph):
+    """Linear weights everywhere on a two-phase state fail the drift check, so
+    every gated step is redone without the gate from the stage-0 backup of U:
+    the result equals the plain path bit for bit and every step counts as
+    redone.  graph=True runs the step as one CUDA graph whose redo branch is a
+    conditional node set on the device; graph=False launches the redo stages
+    with a device-side run-if flag."""
+    from paper_1707_00592_gb300 import learned
+    case = wl.random_state(2, (70, 47), seed=12, kind="two_phase")
+    Uo = oracle.prim_to_cons(2, case.Q)
+    outs = []
+    for gated in (False, True):
+        stream = torch.cuda.Stream() if graph else None
+        s = ws.Solver(2, case.n, case.dx, case.bc, precision="mixed", stream=stream)
+        if gated:
+            P = torch.tensor(learned.init_params(1), dtype=torch.float32, device="cuda")
+            ws.ws_set_mlp(s.ctx, P, 1e30, ws.GATE_REDO_DRIFT | ws.GATE_REDO_NONPHYS)
+        with torch.cuda.stream(stream if stream is not None else torch.cuda.current_stream()):
+            U = s.tensor(Uo)
+            for _ in range(4):
+                s.step(U, 1e-7)
+            torch.cuda.synchronize()
+        outs.append(U.cpu().numpy())
+        if gated:
+            st = ws.ws_gate_stats(s.ctx)
+            assert st["steps"] == 4 and st["redone"] == 4, st
+        s.close()
+    assert np.array_equal(outs[0], outs[1])
+
+
 def test_trained_gate_ab():
     """A/B of the trained gate on a 256^2 shock-bubble (60 CFL steps): the
     plain mixed path, the gated path (MLP trained on the GPU by this library's
@@ -248,10 +307,12 @@ def test_trained_gate_ab():
     assert rep["recall"] >= 0.998
     case = wl.shock_bubble_2d(256)
     res = {}
-    for mode in ("plain", "gated", "linear"):
+    for mode in ("plain", "gated", "gated_per_step", "linear"):
         s = ws.Solver(2, case.n, case.dx, case.bc, precision="mixed")
         if mode == "gated":
             ws.ws_set_mlp(s.ctx, P, thr)
+        elif mode == "gated_per_step":
+            ws.ws_set_mlp(s.ctx, P, thr, ws.GATE_REDO_DRIFT | ws.GATE_REDO_NONPHYS | ws.GATE_PER_STEP)
         elif mode == "linear":
             ws.ws_set_mlp(s.ctx, P, 1e30, 0)
         U = s.prim_to_cons(s.tensor(case.Q))
@@ -269,5 +330,6 @@ def test_trained_gate_ab():
     print({m: (l1[m], round(r[1] * 1e3, 4), r[2]) for m, r in res.items()})
     gst = res["gated"][2]
     assert l1["gated"] < 1e-6
+    assert l1["gated_per_step"] < 1e-6
     assert gst["smooth_faces"] > 0.3 * gst["faces"]
     assert not np.isfinite(l1["linear"]) or l1["linear"] > 100 * max(l1["gated"], 1e-12)
