@@ -316,20 +316,25 @@ def time_drop3d(ws, stream, steps, peak, n=256, l1_n=96, l1_steps=20):
             "l1_density_vs_fp64": {"grid": [l1_n] * 3, "steps": l1_steps, "value": l1}}
 
 
-def time_learned(ws, case, stream, steps, run_steps, warmup):
+def time_learned(ws, case, stream, steps, run_steps, warmup, nograph=False):
     """The learned smooth-face gate on the same run: trained on the GPU by the
     library's kernels, then timed like the plain mixed path, with its L1 density
-    difference from the plain mixed path after the timed run."""
+    difference from the plain mixed path after the timed run.  nograph: the
+    contexts get no stream, so a gated step is a sequence of launches instead of
+    one graph (profilers cannot look inside graphs with conditional nodes)."""
     import torch
     from paper_1707_00592_gb300 import learned
     P, thr, rep = learned.train_gate(total=2_000_000, epochs=4)
     outs = {}
+    if nograph:  # the legacy default stream: no capture, so no graph
+        stream = torch.cuda.default_stream()
     for mode in ("plain", "gated", "gated_per_step"):
         s = ws.Solver(2, case.n, case.dx, case.bc, precision="mixed", stream=stream)
         if mode == "gated":
             ws.ws_set_mlp(s.ctx, P, thr)
         elif mode == "gated_per_step":
             ws.ws_set_mlp(s.ctx, P, thr, ws.GATE_REDO_DRIFT | ws.GATE_REDO_NONPHYS | ws.GATE_PER_STEP)
+        torch.cuda.nvtx.range_push(f"learned_{mode}")  # lets a profiler select one mode's launches
         with torch.cuda.stream(stream):
             U = s.prim_to_cons(s.tensor(case.Q))
             for _ in range(warmup):
@@ -348,6 +353,7 @@ def time_learned(ws, case, stream, steps, run_steps, warmup):
                 b.synchronize()
                 ms += a.elapsed_time(b)
             stats = ws.ws_gate_stats(s.ctx) if mode != "plain" else None
+        torch.cuda.nvtx.range_pop()
         outs[mode] = (U[wl.interior(2, case.n)][0].double(), ms / steps, stats)
         s.close()
     b = outs["plain"][0]
@@ -439,7 +445,7 @@ def run_ours(args):
         if args.drop_steps > 0 and args.precision == "mixed":
             p32 = args.fp32_peak if args.fp32_peak is not None else ws.ws_peak_probe("fp32")
             drop = time_drop3d(ws, stream, args.drop_steps, p32, n=args.drop_n)
-        gate = (time_learned(ws, case, stream, args.steps, args.run_steps, args.warmup)
+        gate = (time_learned(ws, case, stream, args.steps, args.run_steps, args.warmup, args.learned_nograph)
                 if args.learned and args.precision == "mixed" else None)
 
     clocks = clk.summary()
@@ -527,6 +533,7 @@ def main():
     ap.add_argument("--run-steps", type=int, default=2000)
     ap.add_argument("--tube-steps", type=int, default=10)
     ap.add_argument("--drop-steps", type=int, default=10)
+    ap.add_argument("--learned-nograph", action="store_true")
     ap.add_argument("--drop-n", type=int, default=256)
     ap.add_argument("--learned", type=int, default=1)
     ap.add_argument("--fp64-steps", type=int, default=5)
