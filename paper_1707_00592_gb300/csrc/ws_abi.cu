@@ -106,6 +106,11 @@ void free_all(ws_ctx* c) {
   c->graph_exec = nullptr;
   if (c->ggraph_exec) cudaGraphExecDestroy(c->ggraph_exec);
   c->ggraph_exec = nullptr;
+  for (cudaEvent_t e : c->band_ev) cudaEventDestroy(e);
+  c->band_ev.clear();
+  if (c->cp_in) cudaStreamDestroy(c->cp_in);
+  if (c->cp_out) cudaStreamDestroy(c->cp_out);
+  c->cp_in = c->cp_out = nullptr;
   cudaFree(c->gate_drift);
   cudaFree(c->gate_tile_flags);
   cudaFree(c->mlp_frag);
@@ -682,12 +687,117 @@ int ws_step(ws_ctx* c, double* U, double dt, double* dt_used) {
   return WS_OK;
 }
 
+// ws_run_host on the fused 2D path: the state comes in by bands of tile rows
+// and stage 0 of the first step starts on each band as soon as it and the
+// 3-row halo below it have arrived; stage 1 needs the CFL step of the whole
+// grid and runs once all of stage 0 is done; stage 2 of the last step runs by
+// bands again and each finished band goes back to the host while the next one
+// computes.  The kernels and their arithmetic are those of ws_step.
+int run_host_banded(ws_ctx* c, double* U_host, int nsteps, double dt, double* dt_used) {
+  const GridDev& g = c->gd;
+  const int TYv = fused2d_tile_height();
+  const int nrt = (g.n[1] + TYv - 1) / TYv;
+  const int B = nrt < 8 ? nrt : 8;
+  if (!c->cp_in) {
+    CK(c, cudaStreamCreateWithFlags(&c->cp_in, cudaStreamNonBlocking));
+    CK(c, cudaStreamCreateWithFlags(&c->cp_out, cudaStreamNonBlocking));
+  }
+  while ((int)c->band_ev.size() < 2 * B + 2) {
+    cudaEvent_t e;
+    CK(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    c->band_ev.push_back(e);
+  }
+  cudaEvent_t* ev_in = c->band_ev.data();
+  cudaEvent_t* ev_s2 = ev_in + B;
+  cudaEvent_t ev_start = ev_in[2 * B], ev_out = ev_in[2 * B + 1];
+  const int64_t P0 = g.P[0], P1 = g.P[1];
+  const size_t pitch = sizeof(double) * (size_t)g.N;  // between fields
+  // band k: tile rows [r0, r1) and the padded rows it carries (the first and
+  // last bands also carry the ghost rows)
+  auto tiles = [&](int k, int& r0, int& r1) {
+    r0 = (int)((int64_t)k * nrt / B);
+    r1 = (int)((int64_t)(k + 1) * nrt / B);
+  };
+  auto rows = [&](int k, int64_t& p0, int64_t& p1) {
+    int r0, r1;
+    tiles(k, r0, r1);
+    p0 = k == 0 ? 0 : NG + (int64_t)r0 * TYv;
+    p1 = k == B - 1 ? P1 : NG + (int64_t)r1 * TYv;
+  };
+  auto copy_band = [&](int k, bool in, cudaStream_t st) -> cudaError_t {
+    int64_t p0, p1;
+    rows(k, p0, p1);
+    size_t width = sizeof(double) * (size_t)((p1 - p0) * P0);
+    double* d = c->Uhost_dev + p0 * P0;
+    double* h = U_host + p0 * P0;
+    return in ? cudaMemcpy2DAsync(d, pitch, h, pitch, width, g.nv, cudaMemcpyHostToDevice, st)
+              : cudaMemcpy2DAsync(h, pitch, d, pitch, width, g.nv, cudaMemcpyDeviceToHost, st);
+  };
+  auto stage = [&](int st, int r0, int nr) {
+    uint8_t* mb = c->mask + (int64_t)st * c->nmask;
+    const float* Kin = st == 1 ? c->Ka : c->Kb;
+    float* Kout = st == 0 ? c->Ka : c->Kb;
+    launch_stage2d_band(g, st, c->Uhost_dev, c->Q32, Kin, Kout, dt, c->opts.cfl, c->lmax, c->dt_dev,
+                        mb + c->mask_off[0], mb + c->mask_off[1], (float)c->opts.eps, c->opts.mood, c->opts.weights,
+                        c->nbad, r0, nr, c->stream);
+  };
+  // the copy streams start after the work already queued on the context's stream
+  CK(c, cudaEventRecord(ev_start, c->stream));
+  CK(c, cudaStreamWaitEvent(c->cp_in, ev_start, 0));
+  for (int k = 0; k < B; ++k) {
+    CK(c, copy_band(k, true, c->cp_in));
+    CK(c, cudaEventRecord(ev_in[k], c->cp_in));
+  }
+  for (int n = 0; n < nsteps; ++n) {
+    CK(c, cudaMemsetAsync(c->nbad, 0, sizeof(unsigned long long), c->stream));
+    CK(c, cudaMemsetAsync(c->lmax, 0, sizeof(unsigned long long), c->stream));
+    // stage 0: band k needs its rows and the halo rows of band k + 1 (all
+    // bands when y is periodic: the first band's halo wraps to the last rows)
+    const bool wrap = g.bc[1][0] == WS_BC_PERIODIC || g.bc[1][1] == WS_BC_PERIODIC;
+    for (int k = 0; k < B; ++k) {
+      int r0, r1;
+      tiles(k, r0, r1);
+      if (n == 0) CK(c, cudaStreamWaitEvent(c->stream, ev_in[wrap || k + 1 >= B ? B - 1 : k + 1], 0));
+      if (n > 0 && k > 0) continue;
+      stage(0, n == 0 ? r0 : 0, n == 0 ? r1 - r0 : nrt);
+    }
+    stage(1, 0, nrt);
+    if (n + 1 < nsteps) {
+      stage(2, 0, nrt);
+      continue;
+    }
+    CK(c, cudaStreamWaitEvent(c->cp_out, ev_start, 0));
+    for (int k = 0; k < B; ++k) {  // stage 2 of the last step, each band copied out when done
+      int r0, r1;
+      tiles(k, r0, r1);
+      stage(2, r0, r1 - r0);
+      CK(c, cudaEventRecord(ev_s2[k], c->stream));
+      CK(c, cudaStreamWaitEvent(c->cp_out, ev_s2[k], 0));
+      CK(c, copy_band(k, false, c->cp_out));
+    }
+  }
+  if (nsteps == 0) {  // nothing computed: the state goes straight back
+    CK(c, cudaStreamWaitEvent(c->cp_out, ev_in[B - 1], 0));
+    for (int k = 0; k < B; ++k) CK(c, copy_band(k, false, c->cp_out));
+  }
+  int rc = check_launch(c, "banded stage");
+  if (rc) return rc;
+  CK(c, cudaEventRecord(ev_out, c->cp_out));
+  CK(c, cudaStreamWaitEvent(c->stream, ev_out, 0));
+  if (dt_used) CK(c, cudaMemcpyAsync(dt_used, c->dt_dev, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  c->last_stages = 3;
+  return WS_OK;
+}
+
 int ws_run_host(ws_ctx* c, double* U_host, int nsteps, double dt, double* dt_used) {
   if (!c || !U_host || nsteps < 0) return fail(c, WS_EINVAL, "bad arguments");
   if (!c->Uhost_dev) {
     int rc = dalloc(c, &c->Uhost_dev, c->nstate);
     if (rc) return rc;
   }
+  if (c->fused && c->gd.ndim == 2 && !c->learned_on && !c->prof_on)
+    return run_host_banded(c, U_host, nsteps, dt, dt_used);
   size_t bytes = sizeof(double) * (size_t)c->nstate;
   CK(c, cudaMemcpyAsync(c->Uhost_dev, U_host, bytes, cudaMemcpyHostToDevice, c->stream));
   for (int k = 0; k < nsteps; ++k) {

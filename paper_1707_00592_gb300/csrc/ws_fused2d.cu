@@ -139,6 +139,7 @@ struct StageArgs {
   const int* run_if;       // nullable: the CTA returns at once when *run_if == 0
   uint8_t* gflags;         // nullable: per-tile gate decisions (NF bytes per tile), written when the
                            // MLP runs, read by launches that reuse them
+  int row0;                // first tile row of the launch (a launch may cover a band of tile rows)
 };
 
 // interior index along an axis of n cells for a (possibly out-of-range)
@@ -397,7 +398,9 @@ __global__ void __launch_bounds__(NT, 2) k_stage(StageArgs a) {
   if (a.run_if && *a.run_if == 0) return;  // a conditional redo that is not needed
   const GridDev& g = a.g;
   const int nx = g.n[0], n1 = g.n[AX1];
-  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, plane = blockIdx.z;
+  const int trow = blockIdx.y + a.row0;  // tile row
+  const int tile = trow * gridDim.x + blockIdx.x;
+  const int x0 = blockIdx.x * TX, y0 = trow * TY, plane = blockIdx.z;
   const int64_t N = g.N, S1 = g.st[AX1];
   const int64_t pbase = (int64_t)(g.G[AXP] + plane) * g.st[AXP] + g.G[0];  // cell (x, a) at pbase + (G1 + a) S1 + x
   const int tid = threadIdx.x;
@@ -437,7 +440,7 @@ __global__ void __launch_bounds__(NT, 2) k_stage(StageArgs a) {
     SG.dpart[1][tid] = 0.0f;
   }
   if constexpr (GATE == 2) {  // this step's decisions, stored by its stage 0
-    const uint8_t* fl = a.gflags + (int64_t)(blockIdx.y * gridDim.x + blockIdx.x) * NF;
+    const uint8_t* fl = a.gflags + (int64_t)tile * NF;
     for (int f = tid; f < NF; f += NT) SG.smooth[f] = fl[f];
   }
 
@@ -628,7 +631,7 @@ __global__ void __launch_bounds__(NT, 2) k_stage(StageArgs a) {
     }
     __syncthreads();
     if (a.gflags) {  // kept for the step's later stages
-      uint8_t* fl = a.gflags + (int64_t)(blockIdx.y * gridDim.x + blockIdx.x) * NF;
+      uint8_t* fl = a.gflags + (int64_t)tile * NF;
       for (int f = tid; f < NF; f += NT) fl[f] = SG.smooth[f];
     }
     if (a.stage == 3) {  // gate evaluation only: the decisions go to the mask arrays
@@ -649,7 +652,7 @@ __global__ void __launch_bounds__(NT, 2) k_stage(StageArgs a) {
   // back-projection, MOOD and HLLC.  The thread that reconstructs a face also
   // solves its Riemann problem, so no barrier separates the two and the
   // reconstructed characteristics stay in registers.
-  const bool drift = LEARNED && ((int)((blockIdx.y * gridDim.x + blockIdx.x) & 63) ==
+  const bool drift = LEARNED && ((tile & 63) ==
                                   (a.drift_dev ? *a.drift_dev : a.drift_tile));
   const float* q0 = &S.q[0][0][0];
 #pragma unroll 1
@@ -979,6 +982,7 @@ static StageArgs stage_args(const GridDev& g, int stage, double* U, float* U32, 
   a.lstat = nullptr;
   a.run_if = nullptr;
   a.gflags = nullptr;
+  a.row0 = 0;
   return a;
 }
 
@@ -1007,6 +1011,20 @@ void launch_stage2d(const GridDev& g, int stage, double* U, float* U32, const fl
   } else {
     k_stage<0, 6, 0><<<grid, NT, sizeof(SmPlain2), s>>>(a);
   }
+}
+
+int fused2d_tile_height() { return TY; }
+
+void launch_stage2d_band(const GridDev& g, int stage, double* U, float* U32, const float* Kin, float* Kout,
+                         double dt_fixed, double cfl, unsigned long long* lmax, double* dt_out, uint8_t* mask_x,
+                         uint8_t* mask_y, float eps_rel, int mood, int weights, unsigned long long* nbad, int row0,
+                         int nrows, cudaStream_t s) {
+  StageArgs a = stage_args(g, stage, U, U32, Kin, Kout, dt_fixed, cfl, lmax, dt_out, eps_rel, mood, weights, nbad);
+  a.mask_x = mask_x;
+  a.mask_a = mask_y;
+  a.row0 = row0;
+  dim3 grid((g.n[0] + TX - 1) / TX, nrows);
+  k_stage<0, 6, 0><<<grid, NT, sizeof(SmPlain2), s>>>(a);
 }
 
 void launch_stage3d(const GridDev& g, int stage, double* U, float* U32, const float* Kin, float* Kout, float* Lp,

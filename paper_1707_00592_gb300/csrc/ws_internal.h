@@ -65,6 +65,8 @@ struct ws_ctx {
   unsigned long long* lmax = nullptr;  // 1 or ntubes, max wave rate as ordered bits
   unsigned long long* nbad = nullptr;  // inadmissible cells of the last step
   double* Uhost_dev = nullptr;  // device state for ws_run_host
+  cudaStream_t cp_in = nullptr, cp_out = nullptr;  // ws_run_host: copy streams of the banded copies
+  std::vector<cudaEvent_t> band_ev;                 // ws_run_host: one event per band and direction
   int last_stages = 0;
   // batched tubes
   ws::TubesDev td{};
@@ -149,6 +151,12 @@ struct GateArgs {
   const int* drift_dev;  // nullable: drift tile residue in device memory (overrides drift_tile)
 };
 int64_t fused2d_gate_flag_bytes(const GridDev& g);
+// plain 2D stage over the tile rows [row0, row0 + nrows) only
+int fused2d_tile_height();
+void launch_stage2d_band(const GridDev& g, int stage, double* U, float* U32, const float* Kin, float* Kout,
+                         double dt_fixed, double cfl, unsigned long long* lmax, double* dt_out, uint8_t* mask_x,
+                         uint8_t* mask_y, float eps_rel, int mood, int weights, unsigned long long* nbad, int row0,
+                         int nrows, cudaStream_t s);
 int fused2d_smem_bytes();
 cudaError_t fused2d_prepare();
 void launch_stage2d(const GridDev& g, int stage, double* U, float* U32, const float* Kin, float* Kout,

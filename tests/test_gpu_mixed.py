@@ -360,3 +360,31 @@ def test_fused_3d_close_to_oracle_with_masks():
     want = np.concatenate([np.concatenate([d.ravel() for d in mo[st]]) for st in range(3)])
     assert m.size == want.size
     assert np.mean(m == want) > 0.99
+
+
+@pytest.mark.parametrize("n,bc,nsteps", [((70, 47), "transmissive", 1), ((64, 200), "transmissive", 1),
+                                         ((64, 200), "periodic", 3), ((33, 10), "reflective", 2),
+                                         ((40, 130), "periodic", 0)])
+def test_run_host_banded_matches_device_steps(n, bc, nsteps):
+    """ws_run_host on the fused 2D path copies the state in and out by bands
+    of tile rows, overlapped with stage 0 of the first step and stage 2 of the
+    last; the result, Δt and MOOD masks equal those of ws_step on a device
+    copy bit for bit (1 to 8 bands, periodic wrap-around, zero steps)."""
+    case = wl.random_state(2, n, seed=31, kind="two_phase")
+    case.bc = ((bc, bc), (bc, bc))
+    Uo = oracle.prim_to_cons(2, case.Q)
+    s = solver_for(case)
+    U = s.tensor(Uo)
+    dts = [s.step(U, want_dt=True) for _ in range(nsteps)]
+    _, mask = s.mood(with_mask=True)
+    s.close()
+    s2 = solver_for(case)
+    Uh = torch.tensor(Uo).pin_memory()
+    dt_used = np.zeros(1)
+    ws.ws_run_host(s2.ctx, Uh, nsteps, 0.0, dt_used)
+    _, mask2 = s2.mood(with_mask=True)
+    s2.close()
+    assert np.array_equal(Uh.numpy(), U.cpu().numpy())
+    if nsteps:
+        assert dt_used[0] == dts[-1]
+        assert np.array_equal(mask.cpu().numpy(), mask2.cpu().numpy())
