@@ -52,6 +52,12 @@ def cell_update_bytes(ndim: int) -> int:
     return 8 * (ndim + 4) * 8
 
 
+# DRAM bytes moved by one launch of the fused 2D mixed stage on the 1024^2
+# shock-bubble at mid-run (ncu, 50.72 MB read + 3.03 MB written; the stage's
+# FP32 scratch mostly stays in the 129 MB L2 between launches)
+STAGE2D_DRAM_BYTES = 53.75e6
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -469,7 +475,10 @@ def run_ours(args):
         kname, psrc = ("fused RK stage (FP32 mixed: tile load, x and y faces, update)",
                        "FP32 FMA chain probe on this GPU (2 flops per FFMA)")
     roofline = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": STAGE2D_DRAM_BYTES if args.precision == "mixed" and n == 1024 else None,
+                "traffic_source": "dram__bytes_read.sum + dram__bytes_write.sum of one fused-stage launch "
+                                  "(1024^2, step ~300, stage 1), bytes per launch",
                 "peak_source": psrc,
                 "flops_per_face": face_flops(2), "faces_per_launch": faces_per_launch,
                 "face_ms_per_launch": per_launch_s * 1e3,
