@@ -26,7 +26,7 @@ UNITS = {
     "ws_tubes.cu": ["-fmad=false"],
     "ws_probe.cu": [],
     "ws_mixed.cu": [],
-    "ws_fused2d.cu": [],
+    "ws_fused.cu": [],
     "ws_learned.cu": [],
     "ws_tubes_mixed.cu": [],
     "ws_noalloc.cu": ["-fmad=false"],

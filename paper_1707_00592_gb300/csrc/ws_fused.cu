@@ -678,7 +678,7 @@ __global__ void __launch_bounds__(NT, 2) k_stage(StageArgs a) {
     float ic2 = rc * inv, irc = c2 * inv;  // 1/c^2, 1/(rho c)
     const FaceAvg fa{rc, -ic2};
     float wl[NQ], wr[NQ];  // reconstructed characteristics, left and right
-#define WS_B1(R)                                                                 \
+#define WS_RECON(R)                                                                 \
     if constexpr (R < NQ) {                                                      \
       bool lin = LEARNED && R != 2 && sm; /* shear: always WENO-IS */            \
       if (LEARNED && lin && drift)                                               \
@@ -686,14 +686,14 @@ __global__ void __launch_bounds__(NT, 2) k_stage(StageArgs a) {
       else                                                                       \
         weno_item<T, R>(qb, fg, fa, a.P, wl[R], wr[R], lin);                     \
     }
-    WS_B1(0)
-    WS_B1(1)
-    WS_B1(2)
-    WS_B1(3)
-    WS_B1(4)
-    WS_B1(5)
-    WS_B1(6)
-#undef WS_B1
+    WS_RECON(0)
+    WS_RECON(1)
+    WS_RECON(2)
+    WS_RECON(3)
+    WS_RECON(4)
+    WS_RECON(5)
+    WS_RECON(6)
+#undef WS_RECON
 
     float2 W[NQ], Q[NQ];  // (left, right) characteristics, then primitives
 #pragma unroll

@@ -139,7 +139,7 @@ void launch_update_mixed(const GridDev& g, int stage, const double* Un, const do
 
 void launch_cfl_u(const GridDev& g, const double* U, unsigned long long* lmax, cudaStream_t s);
 
-// ---- fused 2D mixed-precision RK stage (ws_fused2d.cu) ----
+// ---- fused mixed-precision RK stage, 2D and 3D (ws_fused.cu) ----
 struct GateArgs {
   const uint2* frag;   // BF16 MMA fragments of W1, W2, W3 (18 x 32 lanes)
   const float* bias;   // b1[32], b2[32], b3

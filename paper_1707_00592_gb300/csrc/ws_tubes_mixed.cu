@@ -6,7 +6,7 @@
 // 3-cell halo in shared memory (transmissive tube ends applied on load, E - Pi
 // in FP64), WENO-IS per (face, characteristic variable) with the linear
 // weights for stencils flat to 1e-6, back-projection / MOOD / HLLC per face,
-// and the increment-form SSP-RK3 with FP64 accumulation (see ws_fused2d.cu).
+// and the increment-form SSP-RK3 with FP64 accumulation (see ws_fused.cu).
 // Stage 0 also reduces each tube's CFL rate (atomicMax per tube); stages 1
 // and 2 take dt = CFL / max per tube.
 #include <cuda_runtime.h>
