@@ -145,7 +145,12 @@ WS_API int ws_step(ws_ctx *ctx, double *U, double dt, double *dt_used);
  * U_host (ws_state_size() doubles; pinned memory gives full copy speed) to
  * the context's device buffer, runs nsteps ws_step's (dt as in ws_step), and
  * copies the state back to U_host.  Synchronises.  dt_used (nullable, HOST)
- * receives the last step's dt (ntubes values in batched-tube mode). */
+ * receives the last step's dt (ntubes values in batched-tube mode).  On the
+ * fused 2D mixed-precision path (learned gate off) the copies go by bands of
+ * tile rows on two internal copy streams: stage 0 of the first step starts on
+ * each band as it arrives and each band of the last step's stage 2 is copied
+ * back while the next computes; the results are those of ws_step.  The
+ * opts.check test of ws_step is not made here. */
 WS_API int ws_run_host(ws_ctx *ctx, double *U_host, int nsteps, double dt, double *dt_used);
 
 /* MOOD record of the last ws_step (3 stages) or ws_flux_divergence (stage 0
