@@ -259,6 +259,37 @@ def time_tubes(ws, stream, steps, seed=0):
             "workload": "4096 Riemann tubes, lengths log-uniform in [256, 8192], per-tube CFL, mixed precision"}
 
 
+def time_setups(ws, stream, steps):
+    """The shock-interface setups of Secs. 6.1 and 6.2 at the paper's grid
+    sizes (air shock on an R22 or helium cylinder, 3000 x 1000, reflective
+    walls; air shock on a water droplet, 800 x 800), mixed precision, MOOD off
+    as in the paper, CFL steps from the initial state."""
+    import torch
+    out = {}
+    for name, make in (("air_R22_3000x1000", lambda: wl.haas_sturtevant("R22")),
+                       ("air_He_3000x1000", lambda: wl.haas_sturtevant("He")),
+                       ("shock_droplet_800x800", lambda: wl.shock_droplet(800))):
+        case = make()
+        s = ws.Solver(2, case.n, case.dx, case.bc, precision="mixed", mood=False, stream=stream)
+        with torch.cuda.stream(stream):
+            U = s.prim_to_cons(s.tensor(case.Q))
+            for _ in range(3):
+                s.step(U)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(steps):
+                s.step(U)
+            b.record(stream)
+            b.synchronize()
+            ms = a.elapsed_time(b) / steps
+            bad = s.nonphysical()
+        out[name] = {"value": case.cells / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": steps,
+                     "nonphysical_cells": bad}
+        s.close()
+        del U
+    return out
+
+
 def time_drop3d(ws, stream, steps, peak, n=256, l1_n=96, l1_steps=20):
     """The 3D configuration: the periodic water drop with density noise on n^3,
     mixed precision through the fused 3D stage (two launches per RK stage).
@@ -447,6 +478,7 @@ def run_ours(args):
         if args.precision == "mixed" and args.fp64_steps > 0:
             fp64_cmp = time_fp64(ws, case, stream, args.fp64_steps)
         tubes = time_tubes(ws, stream, args.tube_steps) if args.tube_steps > 0 else None
+        setups = time_setups(ws, stream, args.setup_steps) if args.setup_steps > 0 and args.precision == "mixed" else None
         drop = None
         if args.drop_steps > 0 and args.precision == "mixed":
             p32 = args.fp32_peak if args.fp32_peak is not None else ws.ws_peak_probe("fp32")
@@ -511,6 +543,8 @@ def run_ours(args):
         line["batched_tubes"] = tubes
     if drop is not None:
         line["drop_3d"] = drop
+    if setups is not None:
+        line["shock_interface_setups"] = setups
     if gate is not None:
         line["learned_gate"] = gate
     if ws_size == 1 and not args.no_cpu_baseline:
@@ -544,6 +578,7 @@ def main():
     ap.add_argument("--drop-steps", type=int, default=10)
     ap.add_argument("--learned-nograph", action="store_true")
     ap.add_argument("--drop-n", type=int, default=256)
+    ap.add_argument("--setup-steps", type=int, default=10)
     ap.add_argument("--learned", type=int, default=1)
     ap.add_argument("--fp64-steps", type=int, default=5)
     args = ap.parse_args()

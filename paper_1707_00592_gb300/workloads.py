@@ -194,6 +194,63 @@ def shock_bubble_2d(n: int = 1024, Ms: float = 1.5) -> Case:
                 meta={"Ms": Ms, "post_shock": (rs, us, ps)})
 
 
+def _shock_cylinder(name, nx, ny, Lx, Ly, x_shock, centre, radius, pre, post, inner, bc, **kw) -> Case:
+    """A planar shock at x = x_shock running in -x (post-shock state on
+    x > x_shock) towards a cylinder of another material at rest in the
+    pre-shock state.  States are (rho, u, p, gamma, P_inf); the cylinder's
+    interface is smeared over two cells (rho, Gamma, Pi mixed in the volume
+    fraction, p and u uniform)."""
+    hx, hy = Lx / nx, Ly / ny
+    X, Y, _ = _centres(2, (nx, ny, 1), (0.0, 0.0, 0.0), (hx, hy, 1.0))
+    X, Y = X[0], Y[0]
+    a = _volume_fraction(np.hypot(X - centre[0], Y - centre[1]), radius, min(hx, hy))  # cylinder fraction
+    Go, Po = material(pre[3], pre[4])
+    Gi, Pi_ = material(inner[3], inner[4])
+    rho = a * inner[0] + (1.0 - a) * pre[0]
+    G = a * Gi + (1.0 - a) * Go
+    P = a * Pi_ + (1.0 - a) * Po
+    u = np.full_like(X, pre[1])
+    v = np.zeros_like(X)
+    p = np.full_like(X, pre[2])
+    shocked = X > x_shock
+    Gs, Ps = material(post[3], post[4])
+    rho = np.where(shocked, post[0], rho)
+    u = np.where(shocked, post[1], u)
+    p = np.where(shocked, post[2], p)
+    G = np.where(shocked, Gs, G)
+    P = np.where(shocked, Ps, P)
+    Q = _fill(2, (nx, ny, 1), [rho, u, v, p, G, P])
+    return Case(name, 2, (nx, ny, 1), (hx, hy, 1.0), bc, Q, **kw)
+
+
+def haas_sturtevant(gas: str = "R22", nx: int = 3000, ny: int = 1000) -> Case:
+    """Sec. 6.1: a Ms = 1.22 shock in air meets a cylinder of R22 (heavier than
+    air) or helium (lighter) in a 267 x 89 mm channel (SI units).  Pre-shock
+    air (1.4 kg/m^3, 0 m/s, 0.1 MPa), post-shock air (1.927, -114.42, 0.157
+    MPa) right of x = 203 mm; cylinder of diameter 50 mm centred at (178, 44.5)
+    mm: R22 (4.415, gamma 1.249) or He (0.255, gamma 1.648); P_inf = 0 for all
+    (the single-phase limit).  Reflective walls at y = 0 and y = 89 mm,
+    transmissive ends in x; MOOD is off for these runs."""
+    inner = {"R22": (4.415, 0.0, 1.0e5, 1.249, 0.0), "He": (0.255, 0.0, 1.0e5, 1.648, 0.0)}[gas]
+    return _shock_cylinder(f"haas_sturtevant_{gas}", nx, ny, 0.267, 0.089, 0.203, (0.178, 0.0445), 0.025,
+                           (1.4, 0.0, 1.0e5, 1.4, 0.0), (1.927, -114.42, 1.57e5, 1.4, 0.0), inner,
+                           (("transmissive", "transmissive"), ("reflective", "reflective")),
+                           t_end={"R22": 420e-6, "He": 674e-6}[gas], meta={"mood": False, "Ms": 1.22})
+
+
+def shock_droplet(n: int = 800) -> Case:
+    """Sec. 6.2: a Ms = 2.0 shock in air meets a water droplet on a 20 x 20 mm
+    domain (SI units).  Pre-shock air (1.2 kg/m^3, 0 m/s, 0.1 MPa, gamma 1.4),
+    post-shock air (3.2, -434, 0.456 MPa) right of x = 16 mm; droplet of
+    diameter 8 mm centred at (12, 10) mm: water (1000, 0.1 MPa, gamma 4.34,
+    P_inf 0.484 GPa).  Transmissive boundaries; MOOD is off for this run."""
+    return _shock_cylinder("shock_droplet", n, n, 0.02, 0.02, 0.016, (0.012, 0.010), 0.004,
+                           (1.2, 0.0, 1.0e5, 1.4, 0.0), (3.2, -434.0, 4.56e5, 1.4, 0.0),
+                           (1000.0, 0.0, 1.0e5, 4.34, 4.84e8),
+                           (("transmissive", "transmissive"), ("transmissive", "transmissive")),
+                           meta={"mood": False, "Ms": 2.0})
+
+
 def drop_3d(n: int = 256, seed: int = 0) -> Case:
     """Water drop (r = 0.25) centred in air on the periodic unit cube, uniform
     u = (1, 0.5, 0.25), p = 1e5, density times (1 + 0.01 S/max|S|) with

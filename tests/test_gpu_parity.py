@@ -263,3 +263,22 @@ def test_invalid_arguments(bad):
     with pytest.raises(ws.WsError) as ei:
         ws.ws_init(g, ws.make_opts(**opts), 0)
     assert ei.value.code == ws.WS_EINVAL
+
+
+@pytest.mark.parametrize("make", [lambda: wl.haas_sturtevant("R22", 90, 30), lambda: wl.haas_sturtevant("He", 90, 30),
+                                  lambda: wl.shock_droplet(48)], ids=["air_R22", "air_He", "shock_droplet"])
+def test_shock_interface_setups_small_bitwise(make):
+    """The shock-gas-cylinder (Sec. 6.1; reflective walls, ideal-gas limit)
+    and shock-droplet (Sec. 6.2) setups, down-sized, with MOOD off as in the
+    paper: 8 CFL steps bit-identical to the oracle, Δt included."""
+    case = make()
+    s = solver_for(case, mood=False)
+    g = ogrid(case, mood=False)
+    Uo = oracle.prim_to_cons(2, case.Q)
+    U = s.tensor(Uo)
+    sl = wl.interior(2, case.n)
+    for _ in range(8):
+        dt = s.step(U, want_dt=True)
+        Uo, dto, _ = oracle.step(g, Uo)
+        assert dt == dto
+    assert same(U.cpu().numpy()[sl], Uo[sl])
