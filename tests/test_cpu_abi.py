@@ -57,3 +57,37 @@ def test_init_without_gpu_fails_cleanly(lib):
     g, _ = ws.make_grid(1, (10,), (0.1,))
     with pytest.raises(ws.WsError):
         ws.ws_init(g, ws.make_opts(), 0)
+
+
+def _grid(ndim, n, dx, bc=None, tubes=None):
+    return ws.make_grid(ndim, n, dx, bc, tubes)
+
+
+@pytest.mark.parametrize("desc,args,opts", [
+    ("no dimensions", (0, (10,), (0.1,)), {}),
+    ("four dimensions", (3, (4, 4, 4), (0.1,) * 3), {"ndim": 4}),
+    ("empty grid", (1, (0,), (0.1,)), {}),
+    ("empty 2D extent", (2, (16, 0), (0.1, 0.1)), {}),
+    ("zero cell size", (2, (8, 8), (0.1, 0.0)), {}),
+    ("negative cell size", (1, (8,), (-0.1,)), {}),
+    ("periodic on one side only", (1, (8,), (0.1,), (("periodic", "transmissive"),)), {}),
+    ("two cells between reflective walls", (1, (2,), (0.1,), (("reflective", "reflective"),)), {}),
+    ("tubes in 2D", (2, (8, 8), (0.1, 0.1), None, [0, 20, 40]), {}),
+    ("bad precision", (1, (8,), (0.1,)), {"precision": 7}),
+    ("bad mood flag", (1, (8,), (0.1,)), {"mood": 2}),
+    ("learned gate in FP64", (2, (8, 8), (0.1, 0.1)), {"learned": True}),
+])
+def test_init_rejects_invalid_input(lib, desc, args, opts):
+    """Empty or inconsistent grids and options are refused with WS_EINVAL
+    and a message, before any device work (so also without a GPU)."""
+    g, keep = _grid(*args)
+    o = ws.make_opts()
+    for k, v in opts.items():
+        if k == "ndim":
+            g.ndim = v  # a value the Python helper cannot express
+        else:
+            setattr(o, k, int(v))
+    with pytest.raises(ws.WsError) as e:
+        ws.ws_init(g, o, 0)
+    assert e.value.code == ws.WS_EINVAL, (desc, e.value)
+    assert str(e.value), desc

@@ -465,3 +465,26 @@ def test_shock_interface_setups_mixed_close_to_oracle(make):
     b = torch.tensor(Uo[sl])
     for f, e in enumerate(_l1_by_field(a, b, 2)):
         assert e < 1e-5, (f, e)
+
+
+@pytest.mark.parametrize("ndim,n", [(2, (1, 9)), (2, (9, 1)), (2, (2, 2)), (2, (33, 1)), (3, (1, 1, 7)),
+                                    (3, (5, 1, 1)), (3, (2, 2, 2)), (3, (1, 16, 3))])
+def test_fused_degenerate_extents_close_to_oracle(ndim, n):
+    """The fused mixed stages on grids one or two cells wide in some
+    directions (one partial tile, the halo mostly boundary images): 3 steps
+    with the oracle's time steps, every field within 1e-5 relative L1 (a
+    momentum component against the whole momentum)."""
+    case = wl.random_state(ndim, n, seed=41, kind="shock")
+    s = solver_for(case)
+    g = ogrid(case)
+    Uo = oracle.prim_to_cons(ndim, case.Q)
+    U = s.tensor(Uo)
+    for _ in range(3):
+        dt = oracle.cfl_dt(g, Uo)
+        s.step(U, dt)
+        Uo, _, _ = oracle.step(g, Uo, dt=dt)
+    sl = wl.interior(ndim, case.n)
+    a = torch.tensor(U.cpu().numpy()[sl])
+    b = torch.tensor(Uo[sl])
+    for f, e in enumerate(_l1_by_field(a, b, ndim)):
+        assert e < 1e-5, (f, e)
