@@ -164,6 +164,23 @@ WS_API int ws_get_mood(ws_ctx *ctx, uint8_t *mask, int64_t counts[9]);
  * ws_step (HOST out).  Synchronises. */
 WS_API int ws_nonphysical(ws_ctx *ctx, int64_t *count);
 
+/* Census step (a measurement aid; the paper has no counterpart): one ws_step
+ * of U in place, with the same kernels' arithmetic and results, that also
+ * counts how the reconstruction of Sec. 3.3 was evaluated.  A characteristic
+ * variable whose six stencil values are flat to 1e-6 of their magnitude takes
+ * the linear weights; every other one takes WENO-IS.  counts (HOST int64[4]),
+ * summed over the three RK stages and every face evaluation (the fused stage
+ * evaluates all faces of each 32 x 15 tile, so a face on the edge between two
+ * tiles is evaluated twice):
+ *   [0] face-variables (one per characteristic variable per face evaluation),
+ *   [1] those whose stencil was flat,
+ *   [2] warp passes (32 consecutive faces evaluating one variable together),
+ *   [3] warp passes in which at least one face took WENO-IS.
+ * Only on the fused mixed-precision 2D and 3D paths (WS_EINVAL elsewhere); the
+ * learned gate, if set, is not applied.  dt, dt_used and opts.check as in
+ * ws_step.  Synchronises. */
+WS_API int ws_census_step(ws_ctx *ctx, double *U, double dt, double *dt_used, int64_t counts[4]);
+
 /* ---- learned smooth-face gate (not in the paper) ----
  * A 24 -> 32 -> 32 -> 1 MLP (ReLU, ReLU, sigmoid) marks faces whose WENO-IS
  * value would equal the 5th-order linear-weight value (d = (4,2,3,1)/10 of

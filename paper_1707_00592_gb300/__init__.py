@@ -75,6 +75,7 @@ def load():
         "ws_run_host": (ctypes.c_int, [vp, vp, ctypes.c_int, ctypes.c_double, dp]),
         "ws_get_mood": (ctypes.c_int, [vp, vp, ctypes.POINTER(ctypes.c_int64)]),
         "ws_nonphysical": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int64)]),
+        "ws_census_step": (ctypes.c_int, [vp, vp, ctypes.c_double, dp, ctypes.POINTER(ctypes.c_int64)]),
         "ws_last_error": (ctypes.c_char_p, [vp]),
         "ws_init_error": (ctypes.c_char_p, []),
         "ws_destroy": (None, [vp]),
@@ -198,6 +199,19 @@ def ws_nonphysical(ctx) -> int:
     n = ctypes.c_int64(0)
     _check(ctx, load().ws_nonphysical(ctx, ctypes.byref(n)))
     return n.value
+
+
+CENSUS_KEYS = ("face_variables", "flat", "warp_passes", "warp_passes_weno")
+
+
+def ws_census_step(ctx, U, dt: float = 0.0) -> dict:
+    """One RK3 step of U with the counts of flat-stencil (linear-weight) and
+    WENO-IS evaluations of the reconstruction (Sec. 3.3), summed over the
+    three stages."""
+    c = (ctypes.c_int64 * 4)()
+    dt_used = ctypes.c_double(0.0)
+    _check(ctx, load().ws_census_step(ctx, _ptr(U), ctypes.c_double(dt), ctypes.byref(dt_used), c))
+    return {**dict(zip(CENSUS_KEYS, (int(v) for v in c))), "dt": dt_used.value}
 
 
 KERNEL_CLASSES = ["ghost", "prim", "cfl", "face", "update", "other"]
@@ -383,6 +397,9 @@ class Solver:
 
     def nonphysical(self):
         return ws_nonphysical(self.ctx)
+
+    def census_step(self, U, dt=0.0):
+        return ws_census_step(self.ctx, U, dt)
 
     def close(self):
         if self.ctx:

@@ -92,6 +92,7 @@ void free_all(ws_ctx* c) {
   cudaFree(c->dt_dev);
   cudaFree(c->lmax);
   cudaFree(c->nbad);
+  cudaFree(c->census);
   cudaFree(c->Uhost_dev);
   cudaFree(c->off_dev);
   cudaFree(c->cell_tube);
@@ -214,7 +215,8 @@ int tube_rhs(ws_ctx* c, double* Us, int stage_slot, bool cfl) {
 
 // The three fused RK stages (the CFL reduction happens inside stage 0, dt is
 // derived in stage 1).  run_if: the stages run only if *run_if != 0.
-int fused_run3(ws_ctx* c, double* U, double dt, const GateArgs* gate, const int* run_if) {
+int fused_run3(ws_ctx* c, double* U, double dt, const GateArgs* gate, const int* run_if,
+               unsigned long long* census = nullptr) {
   const GridDev& g = c->gd;
   if (!run_if) CK(c, cudaMemsetAsync(c->lmax, 0, sizeof(unsigned long long), c->stream));
   for (int s = 0; s < 3; ++s) {
@@ -225,11 +227,11 @@ int fused_run3(ws_ctx* c, double* U, double dt, const GateArgs* gate, const int*
     if (g.ndim == 3)
       launch_stage3d(g, s, U, c->Q32, Kin, Kout, c->Lp, dt, c->opts.cfl, c->lmax, c->dt_dev, mb + c->mask_off[0],
                      mb + c->mask_off[1], mb + c->mask_off[2], (float)c->opts.eps, c->opts.mood, c->opts.weights,
-                     c->nbad, c->stream);
+                     c->nbad, census, c->stream);
     else
       launch_stage2d(g, s, U, c->Q32, Kin, Kout, dt, c->opts.cfl, c->lmax, c->dt_dev, mb + c->mask_off[0],
                      mb + c->mask_off[1], (float)c->opts.eps, c->opts.mood, c->opts.weights, c->nbad, gate, run_if,
-                     c->stream);
+                     census, c->stream);
   }
   return check_launch(c, "fused stage");
 }
@@ -399,7 +401,9 @@ int ws_init(const ws_grid* grid, const ws_opts* opts, void* stream, ws_ctx** out
     if (op.precision == WS_PREC_MIXED) {
       if ((rc = dalloc(c, &c->Q32, (int64_t)(g.nv + 1) * g.N))) goto bad;
       if (gr.ndim == 2 && !getenv("WS_NO_FUSED")) {
-        if ((rc = dalloc(c, &c->Ka, (int64_t)g.nv * g.N)) || (rc = dalloc(c, &c->Kb, (int64_t)g.nv * g.N))) goto bad;
+        if ((rc = dalloc(c, &c->Ka, (int64_t)g.nv * g.N)) || (rc = dalloc(c, &c->Kb, (int64_t)g.nv * g.N)) ||
+            (rc = dalloc(c, &c->census, 4)))
+          goto bad;
         if (fused2d_prepare() != cudaSuccess) {
           rc = fail(c, WS_ECUDA, "cannot enable %d bytes of shared memory for the fused stage", fused2d_smem_bytes());
           goto bad;
@@ -408,7 +412,7 @@ int ws_init(const ws_grid* grid, const ws_opts* opts, void* stream, ws_ctx** out
       }
       if (gr.ndim == 3 && !getenv("WS_NO_FUSED")) {
         if ((rc = dalloc(c, &c->Ka, (int64_t)g.nv * g.N)) || (rc = dalloc(c, &c->Kb, (int64_t)g.nv * g.N)) ||
-            (rc = dalloc(c, &c->Lp, (int64_t)g.nv * g.N)))
+            (rc = dalloc(c, &c->Lp, (int64_t)g.nv * g.N)) || (rc = dalloc(c, &c->census, 4)))
           goto bad;
         if (fused3d_prepare() != cudaSuccess) {
           rc = fail(c, WS_ECUDA, "cannot enable %d bytes of shared memory for the fused stage", fused3d_smem_bytes());
@@ -687,6 +691,28 @@ int ws_step(ws_ctx* c, double* U, double dt, double* dt_used) {
   return WS_OK;
 }
 
+int ws_census_step(ws_ctx* c, double* U, double dt, double* dt_used, int64_t counts[4]) {
+  if (!c || !U || !counts) return fail(c, WS_EINVAL, "bad pointers");
+  if (!c->fused) return fail(c, WS_EINVAL, "the census needs a fused mixed-precision 2D or 3D context");
+  CK(c, cudaMemsetAsync(c->census, 0, 4 * sizeof(unsigned long long), c->stream));
+  CK(c, cudaMemsetAsync(c->nbad, 0, sizeof(unsigned long long), c->stream));
+  int rc = fused_run3(c, U, dt, nullptr, nullptr, c->census);
+  if (rc) return rc;
+  c->last_stages = 3;
+  unsigned long long h[4];
+  CK(c, cudaMemcpyAsync(h, c->census, sizeof h, cudaMemcpyDeviceToHost, c->stream));
+  if (dt_used) CK(c, cudaMemcpyAsync(dt_used, c->dt_dev, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  for (int k = 0; k < 4; ++k) counts[k] = (int64_t)h[k];
+  if (c->opts.check) {
+    unsigned long long nb = 0;
+    CK(c, cudaMemcpyAsync(&nb, c->nbad, sizeof nb, cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    if (nb) return fail(c, WS_ENONPHYS, "%llu inadmissible cells after the step", nb);
+  }
+  return WS_OK;
+}
+
 // ws_run_host on the fused 2D path: the state comes in by bands of tile rows
 // and stage 0 of the first step starts on each band as soon as it and the
 // 3-row halo below it have arrived; stage 1 needs the CFL step of the whole
@@ -946,7 +972,7 @@ int ws_gate_eval(ws_ctx* c, double* U, uint8_t* smooth) {
   CK(c, cudaMemsetAsync(smooth, 0, (size_t)c->nmask, c->stream));
   launch_stage2d(c->gd, 3, U, c->Q32, c->Ka, c->Kb, 0.0, c->opts.cfl, c->lmax, c->dt_dev, smooth,
                  smooth + c->mask_off[1], (float)c->opts.eps, c->opts.mood, c->opts.weights, c->nbad, &ga, nullptr,
-                 c->stream);
+                 nullptr, c->stream);
   return check_launch(c, "gate eval");
 }
 

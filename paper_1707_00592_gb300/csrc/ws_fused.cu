@@ -80,7 +80,8 @@ constexpr int NFRAG = NFRAG1 + NFRAG2 + NFRAG3;
 constexpr int NMT = (NF + 15) / 16;  // 16-face M tiles
 
 // GATE: 0 plain; 1 the learned gate evaluates the MLP in this launch; 2 the
-// launch applies decisions stored by an earlier stage of the same step.
+// launch applies decisions stored by an earlier stage of the same step; 3 a
+// plain launch that also counts the flat-stencil decisions (census).
 template <int GATE, int NQ_, int MODE>
 struct Smem {
   using T = Tr<NQ_, MODE>;
@@ -140,6 +141,8 @@ struct StageArgs {
   uint8_t* gflags;         // nullable: per-tile gate decisions (NF bytes per tile), written when the
                            // MLP runs, read by launches that reuse them
   int row0;                // first tile row of the launch (a launch may cover a band of tile rows)
+  unsigned long long* census;  // census launches: [0] face-variables, [1] those with a flat stencil,
+                               // [2] warp passes over a variable, [3] those in which a face took WENO-IS
 };
 
 // interior index along an axis of n cells for a (possibly out-of-range)
@@ -253,6 +256,28 @@ __device__ __forceinline__ void weno_item(const float* qb, const FaceGeo<T::NTG>
     v = weno5_pair(p[0], p[1], p[2], p[3], p[4], P);
   l5 = v.x;
   r5 = v.y;
+}
+
+// Census of variable R at a face: the flat-stencil test of weno_item on the
+// same projected values.  cnt: [0] face-variables, [1] flat ones (linear
+// weights), [2] warp passes, [3] warp passes in which some active lane has a
+// non-flat stencil, so that the warp runs the WENO-IS branch.
+template <class T, int R>
+__device__ __forceinline__ void census_item(const float* qb, const FaceGeo<T::NTG>& fg, const FaceAvg& fa,
+                                            unsigned (&cnt)[4]) {
+  float2 p[5];
+  project_pairs<T, R>(qb, fg, fa, p);
+  float mn = fminf(fmin3(p[0].x, p[1].x, p[2].x), fmin3(p[2].y, p[1].y, p[0].y));
+  float mx = fmaxf(fmax3(p[0].x, p[1].x, p[2].x), fmax3(p[2].y, p[1].y, p[0].y));
+  const bool flat = mx - mn <= 1e-6f * fmaxf(fabsf(mx), fabsf(mn));
+  const unsigned act = __activemask();
+  const unsigned rough = __ballot_sync(act, !flat);
+  cnt[0] += 1u;
+  cnt[1] += flat ? 1u : 0u;
+  if ((threadIdx.x & 31) == __ffs(act) - 1) {
+    cnt[2] += 1u;
+    cnt[3] += rough ? 1u : 0u;
+  }
 }
 
 // A gated variable on a drift-check tile: the linear-weight values (which
@@ -387,7 +412,8 @@ template <int GATE, int NQ_, int MODE>
 __global__ void __launch_bounds__(NT, 2) k_stage(StageArgs a) {
   using T = Tr<NQ_, MODE>;
   using SM = Smem<GATE, NQ_, MODE>;
-  constexpr bool LEARNED = GATE != 0;  // faces may take the linear weights by the gate's decision
+  constexpr bool LEARNED = GATE == 1 || GATE == 2;  // faces may take the linear weights by the gate's decision
+  constexpr bool CENSUS = GATE == 3;
   constexpr int NQ = NQ_, ND = T::ND, FS = T::FS;
   constexpr bool CACHE = SM::CACHE;
   // axes: x, the tile's 2nd axis (y; z in pass 2), the plane axis (z; y in pass 2; none in 2D)
@@ -655,6 +681,7 @@ __global__ void __launch_bounds__(NT, 2) k_stage(StageArgs a) {
   const bool drift = LEARNED && ((tile & 63) ==
                                   (a.drift_dev ? *a.drift_dev : a.drift_tile));
   const float* q0 = &S.q[0][0][0];
+  unsigned cnt[4] = {0u, 0u, 0u, 0u};  // census counts of this thread (GATE 3)
 #pragma unroll 1
   for (int f = tid; f < T::NFP; f += NT) {
     bool isx;
@@ -680,6 +707,7 @@ __global__ void __launch_bounds__(NT, 2) k_stage(StageArgs a) {
     float wl[NQ], wr[NQ];  // reconstructed characteristics, left and right
 #define WS_RECON(R)                                                                 \
     if constexpr (R < NQ) {                                                      \
+      if constexpr (CENSUS) census_item<T, R>(qb, fg, fa, cnt);                  \
       bool lin = LEARNED && R != 2 && sm; /* shear: always WENO-IS */            \
       if (LEARNED && lin && drift)                                               \
         drift_item<T, R>(qb, fg, fa, a.P, &SG.dpart[0][tid], wl[R], wr[R]);      \
@@ -767,6 +795,13 @@ __global__ void __launch_bounds__(NT, 2) k_stage(StageArgs a) {
                                : ((int64_t)plane * (n1 + 1) + (y0 + j)) * nx + (x0 + i);
         a.mask_a[mi] = mb;
       }
+    }
+  }
+  if constexpr (CENSUS) {  // every lane is back from the face loop
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      unsigned v = __reduce_add_sync(0xffffffffu, cnt[k]);
+      if ((tid & 31) == 0 && v) atomicAdd(&a.census[k], (unsigned long long)v);
     }
   }
   if (LEARNED) {  // drift sums, faces examined, faces the gate sent to the linear weights
@@ -922,6 +957,9 @@ using SmGated2 = Smem<1, 6, 0>;
 using SmReuse2 = Smem<2, 6, 0>;
 using SmPass1 = Smem<0, 7, 1>;
 using SmPass2 = Smem<0, 7, 2>;
+using SmCensus2 = Smem<3, 6, 0>;
+using SmCensus3a = Smem<3, 7, 1>;
+using SmCensus3b = Smem<3, 7, 2>;
 
 int fused2d_smem_bytes() { return (int)(sizeof(SmGated2) + sizeof(SmemGate)); }
 
@@ -931,6 +969,8 @@ cudaError_t fused2d_prepare() {
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_stage<1, 6, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)(sizeof(SmGated2) + sizeof(SmemGate)));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_stage<3, 6, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(SmCensus2));
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_stage<2, 6, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)(sizeof(SmReuse2) + sizeof(SmemGate)));
@@ -945,6 +985,10 @@ int fused3d_smem_bytes() { return (int)(sizeof(SmPass1) > sizeof(SmPass2) ? size
 cudaError_t fused3d_prepare() {
   cudaError_t e = cudaFuncSetAttribute(k_stage<0, 7, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)sizeof(SmPass1));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_stage<3, 7, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(SmCensus3a));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_stage<3, 7, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(SmCensus3b));
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_stage<0, 7, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)sizeof(SmPass2));
@@ -983,17 +1027,19 @@ static StageArgs stage_args(const GridDev& g, int stage, double* U, float* U32, 
   a.run_if = nullptr;
   a.gflags = nullptr;
   a.row0 = 0;
+  a.census = nullptr;
   return a;
 }
 
 void launch_stage2d(const GridDev& g, int stage, double* U, float* U32, const float* Kin, float* Kout,
                     double dt_fixed, double cfl, unsigned long long* lmax, double* dt_out, uint8_t* mask_x,
                     uint8_t* mask_y, float eps_rel, int mood, int weights, unsigned long long* nbad,
-                    const GateArgs* gate, const int* run_if, cudaStream_t s) {
+                    const GateArgs* gate, const int* run_if, unsigned long long* census, cudaStream_t s) {
   StageArgs a = stage_args(g, stage, U, U32, Kin, Kout, dt_fixed, cfl, lmax, dt_out, eps_rel, mood, weights, nbad);
   a.mask_x = mask_x;
   a.mask_a = mask_y;
   a.run_if = run_if;
+  a.census = census;
   dim3 grid((g.n[0] + TX - 1) / TX, (g.n[1] + TY - 1) / TY);
   if (gate) {
     a.mlp_frag = gate->frag;
@@ -1008,6 +1054,8 @@ void launch_stage2d(const GridDev& g, int stage, double* U, float* U32, const fl
       k_stage<2, 6, 0><<<grid, NT, sizeof(SmReuse2) + sizeof(SmemGate), s>>>(a);
     else
       k_stage<1, 6, 0><<<grid, NT, sizeof(SmGated2) + sizeof(SmemGate), s>>>(a);
+  } else if (census) {
+    k_stage<3, 6, 0><<<grid, NT, sizeof(SmCensus2), s>>>(a);
   } else {
     k_stage<0, 6, 0><<<grid, NT, sizeof(SmPlain2), s>>>(a);
   }
@@ -1030,19 +1078,26 @@ void launch_stage2d_band(const GridDev& g, int stage, double* U, float* U32, con
 void launch_stage3d(const GridDev& g, int stage, double* U, float* U32, const float* Kin, float* Kout, float* Lp,
                     double dt_fixed, double cfl, unsigned long long* lmax, double* dt_out, uint8_t* mask_x,
                     uint8_t* mask_y, uint8_t* mask_z, float eps_rel, int mood, int weights, unsigned long long* nbad,
-                    cudaStream_t s) {
+                    unsigned long long* census, cudaStream_t s) {
   StageArgs a = stage_args(g, stage, U, U32, Kin, Kout, dt_fixed, cfl, lmax, dt_out, eps_rel, mood, weights, nbad);
   a.Lp = Lp;
+  a.census = census;
   // pass 1: x and y faces of every z plane -> x + y part of the divergence
   a.mask_x = mask_x;
   a.mask_a = mask_y;
   dim3 g1((g.n[0] + TX - 1) / TX, (g.n[1] + TY - 1) / TY, g.n[2]);
-  k_stage<0, 7, 1><<<g1, NT, sizeof(SmPass1), s>>>(a);
+  if (census)
+    k_stage<3, 7, 1><<<g1, NT, sizeof(SmCensus3a), s>>>(a);
+  else
+    k_stage<0, 7, 1><<<g1, NT, sizeof(SmPass1), s>>>(a);
   // pass 2: z faces of every y plane, the whole divergence and the RK stage
   a.mask_x = nullptr;
   a.mask_a = mask_z;
   dim3 g2((g.n[0] + TX - 1) / TX, (g.n[2] + TY - 1) / TY, g.n[1]);
-  k_stage<0, 7, 2><<<g2, NT, sizeof(SmPass2), s>>>(a);
+  if (census)
+    k_stage<3, 7, 2><<<g2, NT, sizeof(SmCensus3b), s>>>(a);
+  else
+    k_stage<0, 7, 2><<<g2, NT, sizeof(SmPass2), s>>>(a);
 }
 
 }  // namespace ws

@@ -64,6 +64,7 @@ struct ws_ctx {
   double* dt_dev = nullptr;     // 1 (grid) or ntubes
   unsigned long long* lmax = nullptr;  // 1 or ntubes, max wave rate as ordered bits
   unsigned long long* nbad = nullptr;  // inadmissible cells of the last step
+  unsigned long long* census = nullptr;  // fused paths: the counts of ws_census_step
   double* Uhost_dev = nullptr;  // device state for ws_run_host
   cudaStream_t cp_in = nullptr, cp_out = nullptr;  // ws_run_host: copy streams of the banded copies
   std::vector<cudaEvent_t> band_ev;                 // ws_run_host: one event per band and direction
@@ -162,7 +163,10 @@ cudaError_t fused2d_prepare();
 void launch_stage2d(const GridDev& g, int stage, double* U, float* U32, const float* Kin, float* Kout,
                     double dt_fixed, double cfl, unsigned long long* lmax, double* dt_out, uint8_t* mask_x,
                     uint8_t* mask_y, float eps_rel, int mood, int weights, unsigned long long* nbad,
-                    const GateArgs* gate, const int* run_if, cudaStream_t s);
+                    const GateArgs* gate, const int* run_if, unsigned long long* census, cudaStream_t s);
+// census (nullable, without a gate): the same stage, also counting the
+// flat-stencil decisions into census[4] (face-variables, flat ones, warp
+// passes, warp passes that ran WENO-IS)
 // 3D: per stage two launches (x and y faces of every z plane, then z faces of
 // every y plane with the RK stage); Lp holds the x + y part of the divergence
 int fused3d_smem_bytes();
@@ -170,7 +174,7 @@ cudaError_t fused3d_prepare();
 void launch_stage3d(const GridDev& g, int stage, double* U, float* U32, const float* Kin, float* Kout, float* Lp,
                     double dt_fixed, double cfl, unsigned long long* lmax, double* dt_out, uint8_t* mask_x,
                     uint8_t* mask_y, uint8_t* mask_z, float eps_rel, int mood, int weights, unsigned long long* nbad,
-                    cudaStream_t s);
+                    unsigned long long* census, cudaStream_t s);
 void launch_gate_decide(const float* lstat, unsigned long long* nbad, unsigned long long* lmax, int flags, int* redo,
                         double* stats, int* drift_dev, cudaGraphConditionalHandle cond, cudaStream_t s);
 void launch_restore(const int* redo, const double* src, double* dst, int64_t n, cudaStream_t s);
