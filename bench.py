@@ -177,6 +177,17 @@ def cpu_oracle_rate(n: int, rows: int, steps: int):
     return n * rows, times, oracle.get_threads()
 
 
+def workload_config(args, ws_size: int) -> dict:
+    """The headline workload, as both arms name it."""
+    n = args.n
+    return {"workload": f"shock_bubble_2d_{n}x{n}", "grid": [n, n], "run_steps": args.run_steps,
+            "timed_steps": f"{args.steps} steps spread evenly over the {args.run_steps}-step run "
+                           f"(after {args.warmup} warm-up steps)",
+            "cfl": 0.5, "mood": True, "weights": "modified",
+            "l2": "L2 flushed (258 MB write) between timed steps",
+            "parallelism": f"replicas x{ws_size}"}
+
+
 def run_reference(args):
     ws_size, rank, _ = dist_setup()
     if rank != 0:
@@ -189,8 +200,10 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"shock_bubble_2d_{n}x{n}", "grid": [n, n], "rk3_steps": "CFL 0.5",
-                       "l2": "inputs larger than L2 are not applicable (CPU)"},
+            "config": {**workload_config(args, ws_size),
+                       "timed_steps": f"{args.steps} oracle steps on a strip of the workload "
+                                      f"(after {args.warmup} warm-up steps)",
+                       "l2": "CPU run: no GPU cache to flush"},
             "cpu_baseline": {"kind": "oracle", "value": value, "unit": UNIT, "cores": cores, "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -590,13 +603,7 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
             "data": "synthetic",
-            "config": {"workload": f"shock_bubble_2d_{n}x{n}", "grid": [n, n], "precision": args.precision,
-                       "run_steps": args.run_steps,
-                       "timed_steps": f"{args.steps} steps spread evenly over the {args.run_steps}-step run "
-                                      f"(after {args.warmup} warm-up steps)",
-                       "cfl": 0.5, "mood": True, "weights": "modified",
-                       "l2": "L2 flushed (258 MB write) between timed steps",
-                       "parallelism": f"replicas x{ws_size}"},
+            "config": {**workload_config(args, ws_size), "precision": args.precision},
             "gpu_launches": launches,
             "kernel_ms": {k: v[0] for k, v in prof.items() if v[1]},
             "roofline": roofline,
