@@ -448,3 +448,51 @@ def test_mood_quiet_on_smooth_data():
         cc = np.array([oracle.sound_speed(q[0], q[3], q[4], q[5]) for q in qc])
         _, _, lev, _ = oracle.face(qc, cc)
         assert lev == (5, 5)
+
+
+# --------------------------------------------------------------------------
+# Sec. 4 (time step): dt = CFL / max over cells of sum_d (|u_d| + c) / dx_d
+
+def _sound_speed(rho, p, gamma, pinf):
+    """Stiffened-gas sound speed from its definition, c^2 = gamma (p + P_inf) / rho."""
+    return np.sqrt(gamma * (p + pinf) / rho)
+
+
+def test_cfl_dt_uniform_state_closed_form():
+    n, dx = (12, 9), (1.0 / 12, 1.0 / 9)
+    gamma, pinf = wl.WATER
+    G, P = wl.material(gamma, pinf)
+    shape = (n[1], n[0])
+    Q = wl._fill(2, n, [np.full(shape, 1000.0), np.full(shape, 3.0), np.full(shape, -2.0),
+                        np.full(shape, 1.0e5), np.full(shape, G), np.full(shape, P)])
+    g = oracle.Grid(2, n, dx, (("periodic", "periodic"),) * 2)
+    c = _sound_speed(1000.0, 1.0e5, gamma, pinf)
+    expect = 0.5 / ((3.0 + c) / dx[0] + (2.0 + c) / dx[1])
+    assert oracle.cfl_dt(g, oracle.prim_to_cons(2, Q)) == pytest.approx(expect, rel=1e-13)
+
+
+@pytest.mark.parametrize("ndim", [1, 2, 3])
+def test_cfl_dt_is_the_maximum_over_cells(ndim):
+    """Brute force over the cells of a random two-phase state, with the sound
+    speed from gamma = 1 + 1/Gamma and P_inf = Pi / (Gamma + 1)."""
+    n = (40, 24, 10)[:ndim]
+    case = wl.random_state(ndim, n, seed=11 + ndim, kind="two_phase")
+    g = oracle.Grid(ndim, case.n, case.dx, case.bc)
+    sl = wl.interior(ndim, case.n)
+    Q = case.Q[sl].reshape(case.nv, -1)
+    rho, vel, p, G, P = Q[0], Q[1:1 + ndim], Q[1 + ndim], Q[2 + ndim], Q[3 + ndim]
+    c = _sound_speed(rho, p, 1.0 + 1.0 / G, P / (G + 1.0))
+    rate = sum((np.abs(vel[d]) + c) / case.dx[d] for d in range(ndim))
+    expect = 0.5 / rate.max()
+    assert oracle.cfl_dt(g, oracle.prim_to_cons(ndim, case.Q)) == pytest.approx(expect, rel=1e-10)
+    # raising the pressure of the cell that sets the step (p -> 4p) raises only
+    # its sound speed: the step follows that cell's new rate
+    k = int(np.argmax(rate))
+    Q2 = case.Q.copy()
+    idx = np.unravel_index(k, case.Q[sl][0].shape)
+    full = tuple((s.start or 0) + i for s, i in zip(sl[1:], idx))
+    Q2[(1 + ndim,) + full] *= 4.0  # p -> 4p raises c at that cell only
+    c2 = c.copy()
+    c2[k] = _sound_speed(rho[k], 4.0 * p[k], 1.0 + 1.0 / G[k], P[k] / (G[k] + 1.0))
+    rate2 = sum((np.abs(vel[d]) + c2) / case.dx[d] for d in range(ndim))
+    assert oracle.cfl_dt(g, oracle.prim_to_cons(ndim, Q2)) == pytest.approx(0.5 / rate2.max(), rel=1e-10)
