@@ -496,3 +496,32 @@ def test_cfl_dt_is_the_maximum_over_cells(ndim):
     c2[k] = _sound_speed(rho[k], 4.0 * p[k], 1.0 + 1.0 / G[k], P[k] / (G[k] + 1.0))
     rate2 = sum((np.abs(vel[d]) + c2) / case.dx[d] for d in range(ndim))
     assert oracle.cfl_dt(g, oracle.prim_to_cons(ndim, Q2)) == pytest.approx(0.5 / rate2.max(), rel=1e-10)
+
+
+# --------------------------------------------------------------------------
+# Sec. 2, Eq. (material-equation) and Sec. 3.1: Gamma and Pi are advected,
+# d/dt Gamma + u . grad Gamma = 0, so a uniform Gamma and Pi stay uniform
+# under any velocity field: the face fluxes Gamma u* and the source
+# Gamma (u*_{i+1/2} - u*_{i-1/2}) / dx cancel in every direction.
+
+@pytest.mark.parametrize("ndim", [1, 2, 3])
+@pytest.mark.parametrize("gas", ["air", "water"])
+def test_uniform_material_stays_uniform(ndim, gas):
+    n = (48, 20, 10)[:ndim]
+    case = wl.random_state(ndim, n, seed=21 + ndim, kind="shock")
+    G, P = wl.material(*(wl.AIR if gas == "air" else wl.WATER))
+    sl = wl.interior(ndim, case.n)
+    case.Q[(2 + ndim,) + sl[1:]] = G
+    case.Q[(3 + ndim,) + sl[1:]] = P
+    if gas == "water":  # a liquid state of the same shape: rho ~ 1000, p >= 1e5
+        case.Q[(0,) + sl[1:]] *= 1000.0
+        case.Q[(1 + ndim,) + sl[1:]] = 1.0e5 + case.Q[(1 + ndim,) + sl[1:]] * 1.0e3
+    g = oracle.Grid(ndim, case.n, case.dx, case.bc)
+    L, _ = oracle.rhs(g, oracle.prim_to_cons(ndim, case.Q))
+    vel = case.Q[1:1 + ndim][(slice(None),) + sl[1:]]
+    dumax = max(float(np.abs(np.diff(vel[d], axis=2 - d)).max()) for d in range(ndim))
+    assert dumax > 0.1  # the velocity field has real jumps (u in [-0.5, 0.5])
+    # a dropped or sign-flipped source would leave about value x dumax / dx
+    for f, value in ((2 + ndim, G), (3 + ndim, P)):
+        scale = max(abs(value), 1.0) * dumax / min(case.dx[:ndim])
+        assert np.abs(L[(f,) + sl[1:]]).max() <= 1e-12 * scale
