@@ -151,6 +151,28 @@ def test_drop_3d_small_bitwise():
     assert same(U.cpu().numpy()[sl], Uo[sl])
 
 
+def test_full_size_drop_3d_one_step():
+    """The 3D benchmark grid (256^3 periodic water drop with density noise):
+    one CFL step of the FP64 kernels matches the oracle bit for bit (state,
+    dt and every MOOD mask byte of the three stages)."""
+    case = wl.drop_3d(256, seed=0)
+    g = ogrid(case)
+    Un = oracle.prim_to_cons(3, case.Q)
+    del case.Q
+    s = solver_for(case)
+    U = s.tensor(Un)
+    dt = s.step(U, want_dt=True)
+    Uo, dto, mo = oracle.step(g, Un, with_mask=True)
+    assert dt == dto
+    sl = wl.interior(3, case.n)
+    assert same(U.cpu().numpy()[sl], Uo[sl])
+    _, mask = s.mood(with_mask=True)
+    mask = mask.cpu().numpy().reshape(3, -1)
+    for st in range(3):
+        assert same(mask[st], flat_masks(mo[st])), st
+    s.close()
+
+
 def test_reflective_and_mixed_bcs_bitwise():
     case = wl.random_state(2, (21, 17), seed=9, kind="shock")
     case.bc = (("reflective", "transmissive"), ("periodic", "periodic"))
