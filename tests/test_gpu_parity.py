@@ -346,3 +346,33 @@ def test_shock_interface_setups_small_bitwise(make):
         Uo, dto, _ = oracle.step(g, Uo)
         assert dt == dto
     assert same(U.cpu().numpy()[sl], Uo[sl])
+
+
+@pytest.mark.parametrize("make", [lambda: wl.haas_sturtevant("R22"), lambda: wl.haas_sturtevant("He"),
+                                  lambda: wl.shock_droplet()], ids=["air_R22", "air_He", "shock_droplet"])
+def test_shock_interface_setups_full_size(make):
+    """The same setups at the benchmark's sizes (3000 x 1000 cylinders,
+    800^2 droplet), MOOD off: one CFL step of the FP64 kernels bit-identical
+    to the oracle, and the mixed kernels from the same state within 1e-6
+    relative L1 per field (a momentum component against the whole momentum)."""
+    case = make()
+    g = ogrid(case, mood=False)
+    Un = oracle.prim_to_cons(2, case.Q)
+    Uo, dto, _ = oracle.step(g, Un)
+    sl = wl.interior(2, case.n)
+    s = solver_for(case, mood=False)
+    U = s.tensor(Un)
+    dt = s.step(U, want_dt=True)
+    assert dt == dto
+    assert same(U.cpu().numpy()[sl], Uo[sl])
+    s.close()
+    sm = solver_for(case, mood=False, precision="mixed")
+    Um = sm.tensor(Un)
+    sm.step(Um, dto)
+    a, b = Um.cpu().numpy()[sl], Uo[sl]
+    mom = np.abs(b[1]).sum() + np.abs(b[2]).sum()
+    for f in range(6):
+        ref = mom if f in (1, 2) else np.abs(b[f]).sum()
+        err = np.abs(a[f] - b[f]).sum()
+        assert (err <= 1e-6 * ref) if ref > 0 else err == 0.0, f
+    sm.close()
