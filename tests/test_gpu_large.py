@@ -112,3 +112,61 @@ def test_state_beyond_2_31_elements_mixed(reference):
     s.close()
     del U
     torch.cuda.empty_cache()
+
+
+# 3D: 1024 x 1024 x 400 cells, 7 fields (3.0e9 elements; the E, Gamma and Pi
+# fields of the last planes sit beyond element 2^31), the fused two-pass
+# mixed stage, a 12 x 10 x 8 two-phase block at the far corner.
+N3 = (1024, 1024, 400)
+B3 = (12, 10, 8)
+DX3 = (1.0e-3, 1.0e-3, 1.0e-3)
+BC3 = (("transmissive", "transmissive"),) * 3
+
+
+def block3():
+    return wl.random_state(3, B3, seed=6, kind="two_phase").Q[wl.interior(3, B3)]
+
+
+def background3():
+    G, P = wl.material(*wl.AIR)
+    return [1.2, 0.0, 0.0, 0.0, 1.0e5, G, P]
+
+
+@pytest.fixture(scope="module")
+def reference3():
+    if torch.cuda.get_device_properties(0).total_memory < 250 * 2**30:
+        pytest.skip("needs a GPU with 250 GB")
+    n = tuple(B3[d] + 2 * MARGIN for d in range(3))
+    shape = (n[2], n[1], n[0])
+    Q = wl._fill(3, n, [np.full(shape, v) for v in background3()])
+    Q[:, NG + MARGIN:NG + MARGIN + B3[2], NG + MARGIN:NG + MARGIN + B3[1],
+      NG + MARGIN:NG + MARGIN + B3[0]] = block3()
+    g = oracle.Grid(3, n, DX3, BC3)
+    U1, dt, _ = oracle.step(g, oracle.prim_to_cons(3, Q))
+    return U1[wl.interior(3, n)], dt
+
+
+def test_state_beyond_2_31_elements_mixed_3d(reference3):
+    ref, dto = reference3
+    s = ws.Solver(3, N3, DX3, BC3, precision="mixed")
+    assert s.size > 2**31
+    Q = s.tensor()
+    for f, v in enumerate(background3()):
+        Q[f].fill_(v)
+    o = [N3[d] - B3[d] - MARGIN for d in range(3)]
+    Q[:, NG + o[2]:NG + o[2] + B3[2], NG + o[1]:NG + o[1] + B3[1], NG + o[0]:NG + o[0] + B3[0]] = \
+        torch.tensor(block3(), device="cuda")
+    U = s.prim_to_cons(Q)
+    del Q
+    f0 = U[:, NG:NG + 4, NG:NG + 4, NG:NG + 4].cpu().numpy()
+    s.step(U, dto)
+    c = [N3[d] - B3[d] - 2 * MARGIN for d in range(3)]
+    a = U[:, NG + c[2]:NG + N3[2], NG + c[1]:NG + N3[1], NG + c[0]:NG + N3[0]].cpu().numpy()
+    mom = sum(np.abs(ref[1 + d]).sum() for d in range(3))
+    for f in range(7):
+        scale = mom if 1 <= f <= 3 else np.abs(ref[f]).sum()
+        assert np.abs(a[f] - ref[f]).sum() <= 1e-6 * scale, f
+    assert np.array_equal(U[:, NG:NG + 4, NG:NG + 4, NG:NG + 4].cpu().numpy(), f0)
+    s.close()
+    del U
+    torch.cuda.empty_cache()
