@@ -490,6 +490,7 @@ def run_ours(args):
         # census of the reconstruction's evaluations at each timed step's state,
         # on a copy, outside the timed events and the kernel profile
         census = {k: 0 for k in ws.CENSUS_KEYS} if args.precision == "mixed" else None
+        mood_counts = np.zeros((3, 3), dtype=np.int64)  # direction x order (5th, 3rd, 1st)
         Uc = torch.empty_like(U) if census is not None else None
         ws.ws_profile(s.ctx, True)
         with ClockSampler(dev) as clk:
@@ -505,6 +506,7 @@ def run_ours(args):
                     c = s.census_step(Uc)
                     for key in ws.CENSUS_KEYS:
                         census[key] += c[key]
+                    mood_counts += s.mood()[0]  # the census step replays the timed step bit for bit
                     ws.ws_profile(s.ctx, True, reset=False)
                 flush.zero_()  # evict the state from L2 between timed steps
                 ev[k][0].record(stream)
@@ -611,6 +613,11 @@ def run_ours(args):
                     "d2h_bytes_per_step": state_bytes}}
     if clocks:
         line["clocks"] = clocks
+    if census is not None:
+        line["mood"] = {"what": "face sides reconstructed at each order by the MOOD cascade (Sec. 3.4), summed "
+                                "over the three RK stages of every timed step (from the census replay of each)",
+                        **{ax: dict(zip(("5th", "3rd", "1st"), (int(v) for v in mood_counts[d])))
+                           for d, ax in enumerate(("x", "y"))}}
     if l1 is not None:
         line["l1_density_vs_fp64"] = l1
     if fp64_cmp is not None:
