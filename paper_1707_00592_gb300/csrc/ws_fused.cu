@@ -24,6 +24,12 @@
 // The directions are summed x, y, z, as Sec. 3.1 states the dimension-by-
 // dimension divergence.
 //
+// Gate modes (GATE): 0 plain; 1 and 2 the learned smooth-face gate (the MLP
+// evaluated in this launch, or decisions stored by an earlier stage of the
+// step); 3 the census: the plain stage, bit for bit, that also counts per
+// face-variable whether the stencil was flat (linear weights) or took
+// WENO-IS, and per warp whether the WENO-IS branch ran.
+//
 // The Shu-Osher SSP-RK3 is carried in increment form, algebraically
 // identical to U1 = U + dt L0, U2 = 3/4 U + 1/4 (U1 + dt L1),
 // U' = 1/3 U + 2/3 (U2 + dt L2) with L_s = L(U_s):
