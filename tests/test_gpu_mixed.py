@@ -488,3 +488,32 @@ def test_fused_degenerate_extents_close_to_oracle(ndim, n):
     b = torch.tensor(Uo[sl])
     for f, e in enumerate(_l1_by_field(a, b, ndim)):
         assert e < 1e-5, (f, e)
+
+
+@pytest.mark.parametrize("kind", ["drop_3d", "tubes"])
+def test_run_host_unbanded_matches_device_steps(kind):
+    """ws_run_host on the paths that copy the whole state in and out (the
+    fused 3D stage, the batched tubes): the result and the last step's time
+    steps equal those of ws_step on a device copy, bit for bit."""
+    if kind == "drop_3d":
+        case = wl.drop_3d(20, seed=2)
+        Uo = oracle.prim_to_cons(3, case.Q)
+        make = lambda: solver_for(case)  # noqa: E731
+        nt = 1
+    else:
+        off, Q = _tubes_case(ntubes=40, lmin=64, lmax=700, seed=8)
+        Uo = oracle.prim_to_cons(1, Q.reshape(5, 1, 1, -1)).reshape(5, -1)
+        make = lambda: ws.Solver(1, (1,), (1.0,), tube_offsets=off, precision="mixed")  # noqa: E731
+        nt = len(off) - 1
+    s = make()
+    U = s.tensor(Uo)
+    for _ in range(3):
+        dts = s.step(U, want_dt=True)
+    s.close()
+    s2 = make()
+    Uh = torch.tensor(Uo).pin_memory()
+    dt_used = np.zeros(max(nt, 1))
+    ws.ws_run_host(s2.ctx, Uh, 3, 0.0, dt_used)
+    s2.close()
+    assert np.array_equal(Uh.numpy(), U.cpu().numpy())
+    assert np.array_equal(dt_used[:nt], np.atleast_1d(dts))
