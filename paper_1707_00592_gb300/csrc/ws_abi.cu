@@ -1,5 +1,6 @@
 // Host side of the C ABI declared in include/ws.h: validation, scratch
 // ownership and the stream-ordered launch sequence of an SSP-RK3 step.
+#include <optional>
 #include <cuda_runtime.h>
 #include <stdarg.h>
 #include <stdio.h>
@@ -219,9 +220,16 @@ int fused_run3(ws_ctx* c, double* U, double dt, const GateArgs* gate, const int*
                unsigned long long* census = nullptr) {
   const GridDev& g = c->gd;
   if (!run_if) CK(c, cudaMemsetAsync(c->lmax, 0, sizeof(unsigned long long), c->stream));
+  // The plain 2D stages follow one another with programmatic dependent launch,
+  // so one pair of profiling events spans all three (events between them
+  // would serialise the launches); elsewhere each stage is timed on its own.
+  const bool one_scope = g.ndim == 2 && !gate && !run_if && !census;
+  std::optional<KScope> all;
+  if (one_scope) all.emplace(c, WS_K_FACE, 3);
   for (int s = 0; s < 3; ++s) {
     uint8_t* mb = c->mask + (int64_t)s * c->nmask;
-    KScope k(c, WS_K_FACE, g.ndim == 3 ? 2 : 1);
+    std::optional<KScope> k;
+    if (!one_scope) k.emplace(c, WS_K_FACE, g.ndim == 3 ? 2 : 1);
     const float* Kin = s == 1 ? c->Ka : c->Kb;
     float* Kout = s == 0 ? c->Ka : c->Kb;
     if (g.ndim == 3)

@@ -427,6 +427,13 @@ __global__ void __launch_bounds__(NT, 2) k_stage(StageArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SM& S = *reinterpret_cast<SM*>(smem_raw);
   SmemGate& SG = *reinterpret_cast<SmemGate*>(smem_raw + sizeof(SM));
+  // Launched with programmatic stream serialization (the plain 2D stage), a
+  // CTA may become resident while the previous stage is still finishing: it
+  // waits here until that grid has completed and its writes are visible, and
+  // lets the next stage's CTAs be scheduled as this grid's CTAs retire.
+  // Without the launch attribute both instructions return at once.
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   if (a.run_if && *a.run_if == 0) return;  // a conditional redo that is not needed
   const GridDev& g = a.g;
   const int nx = g.n[0], n1 = g.n[AX1];
@@ -1000,6 +1007,24 @@ cudaError_t fused3d_prepare() {
                               (int)sizeof(SmPass2));
 }
 
+// Launch with programmatic stream serialization: the stage's CTAs may be
+// scheduled before the previous kernel on the stream has finished and wait in
+// griddepcontrol.wait, which hides the launch latency between the stages.
+template <class K>
+static cudaError_t launch_pdl(K kernel, dim3 grid, size_t smem, cudaStream_t s, const StageArgs& a) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(NT);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, a);
+}
+
 static StageArgs stage_args(const GridDev& g, int stage, double* U, float* U32, const float* Kin, float* Kout,
                             double dt_fixed, double cfl, unsigned long long* lmax, double* dt_out, float eps_rel,
                             int mood, int weights, unsigned long long* nbad) {
@@ -1062,8 +1087,12 @@ void launch_stage2d(const GridDev& g, int stage, double* U, float* U32, const fl
       k_stage<1, 6, 0><<<grid, NT, sizeof(SmGated2) + sizeof(SmemGate), s>>>(a);
   } else if (census) {
     k_stage<3, 6, 0><<<grid, NT, sizeof(SmCensus2), s>>>(a);
-  } else {
+  } else if (run_if) {  // inside a conditional graph body: a plain launch
     k_stage<0, 6, 0><<<grid, NT, sizeof(SmPlain2), s>>>(a);
+  } else {
+    // 1.7 % faster per step on the 1024^2 shock-bubble; the 3D passes were
+    // measured 3 % slower with it and keep plain launches
+    launch_pdl(k_stage<0, 6, 0>, grid, sizeof(SmPlain2), s, a);
   }
 }
 
