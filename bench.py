@@ -63,9 +63,9 @@ def cell_update_bytes(ndim: int) -> int:
 
 
 # DRAM bytes moved by one launch of the fused 2D mixed stage on the 1024^2
-# shock-bubble at mid-run (ncu, 50.72 MB read + 2.67 MB written; the stage's
+# shock-bubble at mid-run (ncu, 50.72 MB read + 2.37 MB written; the stage's
 # FP32 scratch mostly stays in the 129 MB L2 between launches)
-STAGE2D_DRAM_BYTES = 53.39e6
+STAGE2D_DRAM_BYTES = 53.09e6
 
 
 def load_peaks():
