@@ -22,8 +22,11 @@
  *    (ws_grid.ntubes > 0) each field is the concatenation of the tubes' padded
  *    segments, tube t on [tube_offsets[t], tube_offsets[t+1]).
  *  - Ghost cells of a state passed to ws_step / ws_flux_divergence /
- *    ws_cfl_dt are overwritten from the boundary conditions; interior cells
- *    are only written by ws_step.
+ *    ws_cfl_dt are scratch: the FP64 path overwrites them from the boundary
+ *    conditions, the fused mixed-precision paths apply the boundary
+ *    conditions while loading and leave them as they were.  Their contents
+ *    are not inputs and should not be relied on.  Interior cells are only
+ *    written by ws_step (and ws_run_host, ws_census_step).
  *  - Work is enqueued on the CUDA stream given to ws_init, in order.  Calls
  *    return once the work is enqueued, except where a host-side result is
  *    requested (noted per call), which synchronises that stream.
