@@ -292,7 +292,10 @@ WS_API int ws_set_graph(ws_ctx *ctx, int enable);
 
 /* enable == 1: from now on record a CUDA event pair around every kernel the
  * context launches (on its stream) and reset the totals; 2: resume recording
- * without resetting; 0: stop recording. */
+ * without resetting; 0: stop recording.  The three stages of a plain fused 2D
+ * step follow one another with programmatic dependent launch, which events
+ * between them would undo: one event pair spans the three and counts as three
+ * launches of WS_K_FACE (the span includes the two short gaps). */
 WS_API int ws_profile(ws_ctx *ctx, int enable);
 
 /* Device time (ms, summed over launches, from the recorded events) and launch
