@@ -31,3 +31,25 @@ def test_executed_counts(ndim):
 def test_cell_update_bytes():
     # three stages read U^n and U^(s) and write U^(s+1): (2 + 3 + 3) nv doubles
     assert [bench.cell_update_bytes(d) for d in (1, 2, 3)] == [320, 384, 448]
+
+
+def test_reference_arm_line():
+    """`bench.py --impl reference` runs the FP64 oracle on the host cores and
+    prints one JSON line with the contract's keys, on the same workload
+    configuration as the GPU arm."""
+    import json
+    import subprocess
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--steps", "1",
+                          "--warmup", "3"], capture_output=True, text=True, timeout=600, cwd=root)
+    assert out.returncode == 0, out.stderr
+    d = json.loads(out.stdout.strip().splitlines()[-1])
+    assert d["impl"] == "reference"
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["metric"] == "cell-updates/s per RK3 step" and d["unit"] == "cell-updates/s"
+    assert d["higher_is_better"] is True and d["value"] > 0
+    assert d["config"]["workload"] == "shock_bubble_2d_1024x1024"
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
