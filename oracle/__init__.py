@@ -29,7 +29,13 @@ LIB = os.path.join(BUILD, "libweno_is_oracle.so")
 NG = 3
 
 BC = {"transmissive": 0, "periodic": 1, "reflective": 2}
-WEIGHTS = {"modified": 0, "basic": 1}
+WEIGHTS = {"modified": 0, "basic": 1, "js": 2}
+
+
+def default_eps(weights: str) -> float:
+    """WENO epsilon: 1e-40 for WENO-IS (the paper leaves it open), 1e-6 for
+    WENO-JS (Jiang & Shu's value)."""
+    return 1e-6 if weights == "js" else 1e-40
 
 _lib = None
 
@@ -90,12 +96,14 @@ class Grid:
     n: tuple
     dx: tuple
     bc: tuple = ()          # ((lo, hi), ...) per direction, names from BC
-    eps: float = 1e-40
+    eps: float = None       # None: default_eps(weights)
     mood: bool = True
     weights: str = "modified"
     _c: _Grid = field(default=None, repr=False, compare=False)
 
     def __post_init__(self):
+        if self.eps is None:
+            self.eps = default_eps(self.weights)
         if not self.bc:
             self.bc = tuple(("transmissive", "transmissive") for _ in range(self.ndim))
         g = _Grid()
@@ -212,9 +220,12 @@ def cons_to_prim(ndim: int, U: np.ndarray) -> np.ndarray:
     return Q
 
 
-def weno_is(v, eps: float = 1e-40, order: int = 5, weights: str = "modified"):
+def weno_is(v, eps: float = None, order: int = 5, weights: str = "modified"):
     """Left face value at x_{i+1/2} from (q_{i-2}..q_{i+2}); returns (value, dbg) with
-    dbg = (beta1..beta4, beta12, tau5, alpha1..alpha4)."""
+    dbg = (beta1..beta4, beta12, tau5, alpha1..alpha4), or for WENO-JS at order 5
+    (beta0, beta1, beta2, 0, 0, tau5, alpha0, alpha1, alpha2, 0)."""
+    if eps is None:
+        eps = default_eps(weights)
     v = np.ascontiguousarray(v, dtype=np.float64)
     dbg = np.zeros(10)
     val = lib().or_weno_is(_dp(v), ctypes.c_double(eps), ctypes.c_int(order),
@@ -240,8 +251,23 @@ def hllc(ql, qr):
     return F, us.value
 
 
-def face(qc, cc, eps: float = 1e-40, mood: bool = True, weights: str = "modified"):
+def hllc_waves(ql, qr):
+    """or_hllc with the wave-speed estimates; returns (Fhat, u_hllc, waves) with
+    waves = (u_bar, c2_bar, S_l, S_r, S*) of Eqs. (wave-speeds), (wave-speed)."""
+    ql = np.ascontiguousarray(ql, dtype=np.float64)
+    qr = np.ascontiguousarray(qr, dtype=np.float64)
+    nq = ql.size
+    F = np.zeros(nq)
+    us = ctypes.c_double(0.0)
+    w = np.zeros(5)
+    lib().or_hllc_waves(ctypes.c_int(nq), _dp(ql), _dp(qr), _dp(F), ctypes.byref(us), _dp(w))
+    return F, us.value, w
+
+
+def face(qc, cc, eps: float = None, mood: bool = True, weights: str = "modified"):
     """One face from the sweep-frame primitives of 6 cells; returns (Fhat, u_hllc, levels, qlr)."""
+    if eps is None:
+        eps = default_eps(weights)
     qc = np.ascontiguousarray(qc, dtype=np.float64)
     cc = np.ascontiguousarray(cc, dtype=np.float64)
     nq = qc.shape[1]

@@ -26,6 +26,8 @@
  *   Sec. 3.3.1-3.3.2, Eqs. (final-weighting), (candidates), (weight-new),
  *           (smoothness-indicator), (tau-5), (weighting-modification): WENO-IS.
  *   Sec. 3.4, Eq. (upwind): MOOD-type positivity cascade 5th -> 3rd -> 1st.
+ *   Sec. 5, Sec. 6: the comparison scheme WENO-JS (Jiang & Shu 1996), as an
+ *           option of the reconstruction.
  *
  * Readings where the paper is silent or garbled (each one is applied here,
  * in the CUDA path and in the tests):
@@ -40,7 +42,11 @@
  *   - S_12 = {i-1, i, i+1}, matching the printed beta_12;
  *   - L_{i+1/2} and R_{i+1/2} are both built from rho_bar = (rho_i+rho_{i+1})/2
  *     and c_bar = (c_i+c_{i+1})/2, so that L R = I;
- *   - epsilon is a parameter (1e-40 by default in FP64);
+ *   - epsilon is a parameter (1e-40 by default in FP64; WENO-JS: 1e-6 and
+ *     the power 2 of Jiang & Shu, which the paper does not restate);
+ *   - WENO-JS under MOOD: its 3rd-order level is the scheme's own (the
+ *     2-point candidates with the modified weights), since WENO-JS has no
+ *     smaller candidates;
  *   - the MOOD check is rho > 0, Gamma > 0 and (Gamma+1) p + Pi > 0, done per
  *     face and per side; the 3rd-order retry keeps tau_5 and the modified
  *     alpha_1, alpha_2 and sets d_3 = d_4 = 0; the 1st-order level takes the
@@ -60,7 +66,7 @@
 #define MAXV 7 /* rho, 3 momenta, E, Gamma, Pi */
 
 enum { OR_BC_TRANSMISSIVE = 0, OR_BC_PERIODIC = 1, OR_BC_REFLECTIVE = 2 };
-enum { OR_W_MODIFIED = 0, OR_W_BASIC = 1 };
+enum { OR_W_MODIFIED = 0, OR_W_BASIC = 1, OR_W_JS = 2 };
 
 typedef struct {
   int ndim;        /* 1, 2 or 3 */
@@ -69,7 +75,7 @@ typedef struct {
   int bc[3][2];    /* boundary kind per direction and side */
   double eps;      /* WENO epsilon */
   int mood;        /* 1: MOOD positivity cascade on */
-  int weights;     /* OR_W_MODIFIED (the scheme) or OR_W_BASIC (Eq. weight-new) */
+  int weights;     /* OR_W_MODIFIED (the scheme), OR_W_BASIC (Eq. weight-new) or OR_W_JS (WENO-JS) */
 } or_grid;
 
 /* ------------------------------------------------------------------ */
@@ -137,7 +143,8 @@ static double sound_speed2(double rho, double p, double Gam, double Pi) {
 /* Sec. 3.3.1-3.3.2: WENO-IS reconstruction of the left face value at
  * x_{i+1/2} from v[0..4] = q_{i-2}, q_{i-1}, q_i, q_{i+1}, q_{i+2}.
  * order 5: all four candidates; order 3: d_3 = d_4 = 0 (end of Sec. 3.3.1).
- * dbg (nullable) receives beta_1..beta_4, beta_12, tau_5, alpha_1..alpha_4. */
+ * dbg (nullable) receives beta_1..beta_4, beta_12, tau_5, alpha_1..alpha_4;
+ * for WENO-JS at order 5: beta_0..beta_2, 0, 0, tau_5, alpha_0..alpha_2, 0. */
 double or_weno_is(const double v[5], double eps, int order, int weights, double *dbg) {
   const double qm2 = v[0], qm1 = v[1], q0 = v[2], qp1 = v[3], qp2 = v[4];
   const double c13_12 = 13.0 / 12.0;
@@ -173,13 +180,38 @@ double or_weno_is(const double v[5], double eps, int order, int weights, double 
   b = ((((qp2 - 4.0 * qp1) + 6.0 * q0) - 4.0 * qm1) + qm2);
   double tau5 = (0.25 * (a * a)) + (c13_12 * (b * b));
 
-  /* Eq. (weighting-modification) (or Eq. (weight-new) with q = 1) */
+  if (weights == OR_W_JS && order == 5) {
+    /* Classical WENO-JS (Jiang & Shu 1996), the paper's comparison scheme:
+     * three 3-point candidates S_0 = {i-2,i-1,i}, S_1 = {i-1,i,i+1},
+     * S_2 = {i,i+1,i+2} with linear weights (1,6,3)/10 and
+     * alpha_k = d_k / (eps + beta_k)^2.  S_0 and S_2 are the paper's S_4 and
+     * S_3 (candidates q^(4), q^(3), indicators beta_4, beta_3); S_1 is S_12
+     * (indicator beta_12), whose 3rd-order candidate is
+     *   -q_{i-1}/6 + 5q_i/6 + q_{i+1}/3 = q_i + (1/3)(q_{i+1}-q_i) - (1/6)(q_{i-1}-q_i). */
+    double deltaC = ((1.0 / 3.0) * (qp1 - q0)) - ((1.0 / 6.0) * (qm1 - q0));
+    double e0 = eps + beta4, e1 = eps + beta12, e2 = eps + beta3;
+    double a0 = 1.0 / (e0 * e0);
+    double a1 = 6.0 / (e1 * e1);
+    double a2 = 3.0 / (e2 * e2);
+    if (dbg) {
+      dbg[0] = beta4; dbg[1] = beta12; dbg[2] = beta3;
+      dbg[3] = 0.0; dbg[4] = 0.0; dbg[5] = tau5;
+      dbg[6] = a0; dbg[7] = a1; dbg[8] = a2; dbg[9] = 0.0;
+    }
+    double numJ = ((a0 * delta4) + (a1 * deltaC)) + (a2 * delta3);
+    double denJ = (a0 + a1) + a2;
+    return q0 + numJ / denJ;
+  }
+
+  /* Eq. (weighting-modification) (or Eq. (weight-new) with q = 1).  The
+   * 3rd-order level of WENO-JS is the one of the scheme (modified weights,
+   * d_3 = d_4 = 0): WENO-JS has no 2-point candidates of its own. */
   double r1 = tau5 / (beta1 + eps);
   double r2 = tau5 / (beta2 + eps);
   double r3 = tau5 / (beta3 + eps);
   double r4 = tau5 / (beta4 + eps);
   double alpha1, alpha2;
-  if (weights == OR_W_MODIFIED) {
+  if (weights != OR_W_BASIC) {
     double r12 = tau5 / (beta12 + eps);
     alpha1 = 4.0 * (1.0 + r1 * r12);
     alpha2 = 2.0 * (1.0 + r2 * r12);
@@ -261,7 +293,7 @@ static int admissible(int nq, const double *q) {
  * ql, qr: (rho, u_n, u_t.., p, Gamma, Pi).  Fhat receives the nq flux
  * components of (rho, rho u_n, rho u_t.., E, Gamma, Pi); *ustar the face
  * velocity of Eq. (velocities). */
-void or_hllc(int nq, const double *ql, const double *qr, double *Fhat, double *ustar) {
+static void hllc_core(int nq, const double *ql, const double *qr, double *Fhat, double *ustar, double *waves) {
   int nt = nq - 5;
   const double *qs[2] = {ql, qr};
   double U[2][MAXV], F[2][MAXV], c2[2], cc[2];
@@ -304,6 +336,9 @@ void or_hllc(int nq, const double *ql, const double *qr, double *Fhat, double *u
   double num = ((pr - pl) + ((rl * ul) * (Sl - ul))) - ((rr * ur) * (Sr - ur));
   double dd = (rl * (Sl - ul)) - (rr * (Sr - ur));
   double Ss = num / dd;
+  if (waves) {
+    waves[0] = ubar; waves[1] = c2bar; waves[2] = Sl; waves[3] = Sr; waves[4] = Ss;
+  }
   /* Eq. (flux-function) with D* = (0, 1, 0.., S*, 0, 0) */
   double Fs[2][MAXV], us[2];
   double Sk[2] = {Sl, Sr};
@@ -330,6 +365,16 @@ void or_hllc(int nq, const double *ql, const double *qr, double *Fhat, double *u
   double wl = (1.0 + s) / 2.0, wr = (1.0 - s) / 2.0;
   for (int m = 0; m < nq; ++m) Fhat[m] = (wl * Fs[0][m]) + (wr * Fs[1][m]);
   *ustar = (wl * us[0]) + (wr * us[1]);
+}
+
+void or_hllc(int nq, const double *ql, const double *qr, double *Fhat, double *ustar) {
+  hllc_core(nq, ql, qr, Fhat, ustar, NULL);
+}
+
+/* or_hllc that also reports the wave-speed estimates of Eq. (wave-speeds)
+ * and Eq. (wave-speed): waves = (u_bar, c2_bar, S_l, S_r, S*). */
+void or_hllc_waves(int nq, const double *ql, const double *qr, double *Fhat, double *ustar, double *waves) {
+  hllc_core(nq, ql, qr, Fhat, ustar, waves);
 }
 
 /* ------------------------------------------------------------------ */
@@ -378,7 +423,7 @@ void or_face(int nq, const double *qc /* [6][nq] */, const double *cc /* [6] */,
       qlr[nq + r] = q[1][r];
     }
   }
-  or_hllc(nq, q[0], q[1], Fhat, ustar);
+  hllc_core(nq, q[0], q[1], Fhat, ustar, NULL);
 }
 
 /* ------------------------------------------------------------------ */

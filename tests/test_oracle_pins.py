@@ -100,6 +100,96 @@ def test_step_stencil_hand_values():
     assert abs(valr - g["right"]) < 1e-30
 
 
+def test_basic_weights_hand_values():
+    """Sec. 3.3.1, Eq. (weight-new) with q = 1 (the basic weights): alpha_1..alpha_4
+    and the face value on the step stencil worked by hand with eps = 1; the
+    modified weights of Eq. (weighting-modification) give another alpha_1 there."""
+    g = read_golden("weno_basic_weights_step.txt")
+    step = np.array([0.0, 0.0, 0.0, 1.0, 1.0])
+    val, dbg = oracle.weno_is(step, eps=1.0, weights="basic")
+    for k, nm in enumerate(["alpha1", "alpha2", "alpha3", "alpha4"]):
+        assert dbg[6 + k] == pytest.approx(g[nm], rel=1e-15)
+    assert val == pytest.approx(g["value"], rel=1e-15)
+    # 3rd-order level (d3 = d4 = 0): (alpha1 q1 + alpha2 q2)/(alpha1 + alpha2) = 12/46
+    val3, _ = oracle.weno_is(step, eps=1.0, order=3, weights="basic")
+    assert val3 == pytest.approx(12.0 / 46.0, rel=1e-15)
+    _, dbg_m = oracle.weno_is(step, eps=1.0, weights="modified")
+    assert dbg_m[6] == pytest.approx(628.0 / 7.0, rel=1e-15)
+
+
+def test_basic_weights_in_the_scheme():
+    """Sec. 3.3.2: with the basic weights the 2-point candidates take too much
+    weight near critical points of smooth data, where beta_1 or beta_2 are
+    small, and the scheme falls to about 2nd order; the modified weights keep
+    5th order on the same wave (test_convergence_1d_entropy_wave).  The sine
+    wave has two critical points."""
+    errs = []
+    for n in (20, 40, 80):
+        case = wl.entropy_wave(n, 1, amp=0.2, kind="sine")
+        g = oracle.Grid(1, case.n, case.dx, case.bc, mood=False, weights="basic")
+        h = 1.0 / n
+        U = _fixed_dt_run(g, _U(case), 0.25, 0.5 * h ** (5.0 / 3.0))
+        x = (np.arange(n) + 0.5) * h
+        ex = 1.0 + 0.2 * np.sin(2 * np.pi * (x - 0.25)) * np.sin(np.pi * h) / (np.pi * h)
+        errs.append(np.abs(U[0, 0, 0, 3:3 + n] - ex).mean())
+    orders = [math.log2(errs[k] / errs[k + 1]) for k in range(2)]
+    assert max(orders) < 3.0, (errs, orders)
+
+
+# --------------------------------------------------------------------------
+# The comparison scheme WENO-JS (Jiang & Shu 1996; Secs. 5 and 6 compare with it)
+
+def test_js_linear_weights_recover_weno5():
+    """With eps >> beta the WENO-JS weights are d = (1, 6, 3)/10 and the face
+    value is the 5th-order linear scheme (2, -13, 47, 27, -3)/60."""
+    rng = np.random.default_rng(21)
+    for _ in range(200):
+        v = rng.normal(size=5)
+        val, dbg = oracle.weno_is(v, eps=1e100, weights="js")
+        expect = (2 * v[0] - 13 * v[1] + 47 * v[2] + 27 * v[3] - 3 * v[4]) / 60.0
+        assert abs(val - expect) <= 1e-14 * (1 + np.abs(v).max())
+        np.testing.assert_allclose(dbg[6:9] * 1e200, [1.0, 6.0, 3.0], rtol=1e-12)
+
+
+def test_js_step_stencil_hand_values():
+    """WENO-JS on the step 0 0 0 1 1 (1), eps = 1e-6, power 2: hand-worked
+    indicators, weights and face values."""
+    g = read_golden("weno_js_step_stencil.txt")
+    val, dbg = oracle.weno_is(np.array([0.0, 0.0, 0.0, 1.0, 1.0]), weights="js")
+    for k, nm in enumerate(["beta0", "beta1", "beta2"]):
+        assert dbg[k] == pytest.approx(g[nm], rel=1e-15, abs=0)
+    for k, nm in enumerate(["alpha0", "alpha1", "alpha2"]):
+        assert dbg[6 + k] == pytest.approx(g[nm], rel=1e-14)
+    assert val == pytest.approx(g["left"], rel=1e-12)
+    valr, _ = oracle.weno_is(np.array([1.0, 1.0, 1.0, 0.0, 0.0]), weights="js")
+    assert valr - 1.0 == pytest.approx(g["right_minus_one"], abs=2e-16)
+
+
+def test_js_third_order_level():
+    """Reading: under MOOD, the 3rd-order level of WENO-JS is the scheme's own
+    (2-point candidates, modified weights, d3 = d4 = 0)."""
+    rng = np.random.default_rng(22)
+    for _ in range(50):
+        v = rng.normal(size=5)
+        a, _ = oracle.weno_is(v, eps=1e-6, order=3, weights="js")
+        b, _ = oracle.weno_is(v, eps=1e-6, order=3, weights="modified")
+        assert a == b
+
+
+def test_js_whole_scheme_fifth_order():
+    """The WENO-JS option in the whole scheme: 5th order on the smooth entropy wave."""
+    errs = []
+    for n in (20, 40, 80):
+        case = wl.entropy_wave(n, 1, amp=0.2, kind="sine")
+        g = oracle.Grid(1, case.n, case.dx, case.bc, mood=False, weights="js")
+        h = 1.0 / n
+        U = _fixed_dt_run(g, _U(case), 0.25, 0.5 * h ** (5.0 / 3.0))
+        x = (np.arange(n) + 0.5) * h
+        ex = 1.0 + 0.2 * np.sin(2 * np.pi * (x - 0.25)) * np.sin(np.pi * h) / (np.pi * h)
+        errs.append(np.abs(U[0, 0, 0, 3:3 + n] - ex).mean())
+    assert math.log2(errs[1] / errs[2]) > 4.5, errs
+
+
 def test_weno_is_order_of_accuracy_pointwise():
     """Reconstruction error on a smooth function at fixed position falls as h^5
     (Sec. 3.3.1: tau5/(beta+eps) = O(h^(6-r)) keeps 5th order), including at a
@@ -184,6 +274,74 @@ def test_hllc_supersonic_upwinding_and_rest():
     F, us = oracle.hllc(ql, qr)
     assert F[0] == 0.0 and us == 0.0
     assert F[1] == pytest.approx(1e5, rel=1e-14)
+
+
+def test_hllc_wave_speeds_hand_values():
+    """Eqs. (wave-speeds), (wave-speed), (flux-function), (hllc-flux) and
+    (velocities) on a subsonic two-material face (S_l < 0 < S_r, u_l != u_r),
+    worked by hand: Roe u_bar, the Einfeldt c2_bar, S_l, S_r, S*, the flux and
+    the face velocity.  A printed typo in u_bar or c2_bar, or a dropped Einfeldt
+    term, changes S_l and S_r and hence S* and every flux component."""
+    g = read_golden("hllc_subsonic_face.txt")
+    # gamma 2, P_inf 1 and gamma 1.4, P_inf 0: Gamma = 1/(gamma-1), Pi = gamma P_inf/(gamma-1)
+    G_l, P_l, G_r, P_r = 1.0, 2.0, 2.5, 0.0
+    ql = np.array([4.0, 1.0, 10.0, G_l, P_l])
+    qr = np.array([1.0, -2.0, 5.0, G_r, P_r])
+    F, us, w = oracle.hllc_waves(ql, qr)
+    assert w[0] == pytest.approx(g["u_bar"], abs=1e-15)
+    assert w[1] == pytest.approx(g["c2_bar"], rel=1e-15)
+    for k, nm in ((2, "S_l"), (3, "S_r"), (4, "S_star")):
+        assert w[k] == pytest.approx(g[nm], rel=1e-14), nm
+    for m, nm in enumerate(["F_rho", "F_mom", "F_E", "F_Gamma", "F_Pi"]):
+        assert F[m] == pytest.approx(g[nm], rel=1e-14), nm
+    assert us == pytest.approx(g["u_star"], rel=1e-14)
+    # the same face with a tangential velocity (nq = 6): the five fluxes are
+    # unchanged and the tangential flux is the mass flux times the upwind v
+    ql6 = np.array([4.0, 1.0, 0.5, 10.0, G_l, P_l])
+    qr6 = np.array([1.0, -2.0, -0.25, 5.0, G_r, P_r])
+    F6, us6, w6 = oracle.hllc_waves(ql6, qr6)
+    np.testing.assert_allclose(w6[2:], w[2:], rtol=1e-15)
+    np.testing.assert_allclose(F6[[0, 1, 4, 5]], F[[0, 1, 3, 4]], rtol=1e-14)
+    assert F6[2] == pytest.approx(g["F_rho"] * 0.5, rel=1e-14)
+
+
+def test_hllc_contact_speed_weak_waves():
+    """Weak two-state problems (jumps of 1e-3): S_l < S* < S_r, and S* is the
+    exact stiffened-gas solution's contact velocity to within the jump's size."""
+    rng = np.random.default_rng(31)
+    for _ in range(20):
+        gam, pinf = (wl.AIR if rng.random() < 0.5 else wl.WATER)
+        G, P = wl.material(gam, pinf)
+        rho = 1.0 if gam == wl.AIR[0] else 1000.0
+        p = 1.0e5
+        c = math.sqrt(gam * (p + pinf) / rho)
+        u = rng.uniform(-0.5, 0.5) * c
+        d = 1e-3
+        sides = []
+        for k in range(2):
+            sides.append((rho * (1 + d * rng.normal()), u + d * c * rng.normal(), p * (1 + d * rng.normal())))
+        ql = np.array([sides[0][0], sides[0][1], sides[0][2], G, P])
+        qr = np.array([sides[1][0], sides[1][1], sides[1][2], G, P])
+        _, _, w = oracle.hllc_waves(ql, qr)
+        ps, ust = er.star_state(er.Side(*sides[0], gam, pinf), er.Side(*sides[1], gam, pinf))
+        assert w[2] < w[4] < w[3]
+        assert abs(w[4] - ust) <= 1e-3 * c
+
+
+def test_hllc_mirrored_states_zero_mass_flux():
+    """A face between a state and its mirror image (u_n negated), as at a
+    reflective wall: S* = 0, so no mass, Gamma or Pi crosses the face and the
+    face velocity is 0, exactly."""
+    rng = np.random.default_rng(32)
+    for _ in range(100):
+        G, P = wl.material(*(wl.AIR if rng.random() < 0.5 else wl.WATER))
+        q = np.array([rng.uniform(0.5, 1000), rng.uniform(-300, 300), rng.uniform(-50, 50),
+                      rng.uniform(1e4, 1e9), G, P])
+        m = q.copy()
+        m[1] = -m[1]
+        F, us, w = oracle.hllc_waves(m, q)
+        assert w[4] == 0.0 and us == 0.0
+        assert F[0] == 0.0 and F[4] == 0.0 and F[5] == 0.0
 
 
 # --------------------------------------------------------------------------
@@ -300,6 +458,63 @@ def test_conservation_periodic(ndim):
     for f in range(ndim + 2):
         scale = np.abs(U[(f,) + sl[1:]]).sum()
         assert abs(s1[f] - s0[f]) <= 1e-13 * scale
+
+
+def _doubled(Q, ndim, axis_field):
+    """The state mirrored about its low wall along the last active axis (the
+    normal momentum component negated), followed by the state itself."""
+    ax = {1: 3, 2: 2}[ndim]
+    sl = [slice(None)] * 4
+    inner = Q.copy()
+    m = np.flip(inner, axis=ax).copy()
+    m[axis_field] *= -1.0
+    return np.concatenate([m, inner], axis=ax)
+
+
+@pytest.mark.parametrize("ndim", [1, 2])
+def test_reflective_walls_equal_doubled_periodic_domain(ndim):
+    """Sec. 6.1 reflective (slip) walls: a box with walls on both ends of an
+    axis advances exactly as the periodic box of twice the length that holds
+    the state and its mirror image (normal velocity negated) -- the ghost cells
+    of a wall are the mirror cells of that doubled box.  Bit for bit, dt
+    included; this pins the reflective ghost fill against the periodic one."""
+    n = (24,) if ndim == 1 else (12, 10)
+    case = wl.random_state(ndim, n, seed=40 + ndim, kind="two_phase")
+    sl = wl.interior(ndim, case.n)
+    Qi = case.Q[sl]                     # interior primitives [f, z, y, x]
+    d = ndim - 1                        # the walled axis: x in 1D, y in 2D
+    bc = [("transmissive", "transmissive")] * ndim
+    bc[d] = ("reflective", "reflective")
+    g = oracle.Grid(ndim, case.n, case.dx, tuple(bc))
+    n2 = list(case.n[:ndim])
+    n2[d] *= 2
+    bc2 = list(bc)
+    bc2[d] = ("periodic", "periodic")
+    g2 = oracle.Grid(ndim, tuple(n2), case.dx, tuple(bc2))
+    Q2 = wl._fill(ndim, tuple(n2), list(_doubled(Qi, ndim, 1 + d)))
+    U1, dt1, _ = oracle.step(g, _U(case))
+    U2, dt2, _ = oracle.step(g2, oracle.prim_to_cons(ndim, Q2))
+    assert dt1 == dt2
+    sl2 = wl.interior(ndim, tuple(n2))
+    half = [slice(None)] * 4
+    ax = {1: 3, 2: 2}[ndim]
+    half[ax] = slice(n[d], 2 * n[d])
+    assert np.array_equal(U1[sl], U2[sl2][tuple(half)])
+
+
+def test_reflective_box_conserves_mass_and_energy():
+    """No mass or energy crosses a reflective wall: in a box walled on all sides
+    the totals of rho and E change only by round-off over a step."""
+    case = wl.random_state(2, (14, 12), seed=44, kind="two_phase")
+    g = oracle.Grid(2, case.n, case.dx, (("reflective", "reflective"),) * 2)
+    U = _U(case)
+    sl = wl.interior(2, case.n)
+    s0 = U[sl].reshape(case.nv, -1).sum(axis=1)
+    for _ in range(3):
+        U, _, _ = oracle.step(g, U)
+    s1 = U[sl].reshape(case.nv, -1).sum(axis=1)
+    for f in (0, 3):
+        assert abs(s1[f] - s0[f]) <= 1e-13 * np.abs(U[(f,) + sl[1:]]).sum()
 
 
 def test_mirror_symmetry_1d():
