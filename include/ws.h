@@ -70,6 +70,9 @@ extern "C" {
 /* nonlinear weights */
 #define WS_W_MODIFIED 0 /* Sec. 3.3.2, Eq. (weighting-modification): the scheme */
 #define WS_W_BASIC 1    /* Sec. 3.3.1, Eq. (weight-new) with q = 1 */
+#define WS_W_JS 2       /* the comparison scheme of Secs. 5 and 6: classical WENO-JS (Jiang & Shu 1996),
+                           3-point candidates, d = (1,6,3)/10, alpha_k = d_k/(eps + beta_k)^2; under MOOD
+                           its 3rd-order level is the scheme's own (the 2-point candidates, modified weights) */
 
 typedef struct ws_grid {
   int ndim;                    /* 1, 2 or 3 */
@@ -90,7 +93,9 @@ typedef struct ws_opts {
   int learned;   /* 1: smooth-face gate by the face-classifier MLP (mixed precision only) */
   double eps;    /* WENO epsilon (the paper leaves it open).  FP64: absolute, <= 0 selects 1e-40.
                     Mixed: relative to beta1 + beta2 + tau5 of the stencil (floor 1e-30), <= 0
-                    selects 1e-10 -- keeps tau5/(beta+eps) within FP32 range for p ~ 1e9 */
+                    selects 1e-10 -- keeps tau5/(beta+eps) within FP32 range for p ~ 1e9.
+                    WS_W_JS: the absolute epsilon of WENO-JS in both precisions, <= 0 selects
+                    Jiang & Shu's 1e-6 (its MOOD 3rd-order level then uses the defaults above) */
   double cfl;    /* CFL number; <= 0 selects 0.5 (Secs. 5, 6) */
   int check;     /* 1: ws_step synchronises and returns WS_ENONPHYS when a cell is inadmissible */
 } ws_opts;
@@ -101,6 +106,15 @@ typedef struct ws_ctx ws_ctx;
  * n, dx, bc, tube offsets) and options, allocates the context's scratch
  * (primitive cache, face fluxes, RK stage state, MOOD masks) and returns it in
  * *out.  stream: a cudaStream_t (NULL = legacy default stream).
+ * The problem is the initial-value problem of Sec. 2: the Euler equations
+ * (Eq. governing-equation) closed by the stiffened-gas EOS rho e = Gamma p +
+ * Pi (Eq. eos), with the material functions Gamma = 1/(gamma-1) and Pi =
+ * gamma P_inf/(gamma-1) (Eq. material-properties) advected by Eq.
+ * (material-equation).  The EOS parameters are therefore not arguments of
+ * ws_init: every cell of the state carries its own Gamma and Pi (two of its
+ * fields), which is also what describes a mixture cell of a smeared
+ * interface, where no single (gamma, P_inf) exists.  A fluid with (gamma,
+ * P_inf) enters through ws_prim_to_cons with those two fields set.
  * Errors: WS_EINVAL (bad grid/options; *out untouched), WS_ECUDA. */
 WS_API int ws_init(const ws_grid *grid, const ws_opts *opts, void *stream, ws_ctx **out);
 
@@ -325,7 +339,10 @@ WS_API int ws_peak_probe(int kind, int blocks, double *tflops);
  * conditions) and L (DEVICE, interior written) are caller buffers in the state
  * layout above.  Grids whose primitive cache plus face fluxes exceed the
  * scratch (beyond 313 x 313 cells in 2D, 38^3 in 3D or 174756 cells in 1D) are
- * rejected with WS_EINVAL; batched tubes and mixed precision with WS_ENOTSUP.
+ * rejected with WS_EINVAL; batched tubes and mixed precision with WS_ENOTSUP;
+ * the options are checked as ws_init checks them (WS_EINVAL).  U, L and the
+ * stream must belong to the current CUDA device: the scratch used is that
+ * device's copy of the array.
  * err (nullable, HOST, err_len bytes) receives a message on failure.
  * Work is enqueued on `stream` (a cudaStream_t; NULL = legacy default).
  * The first call on each device looks up the scratch's device address with

@@ -284,14 +284,17 @@ def sound_speed(rho, p, Gam, Pi) -> float:
     return float(lib().or_sound_speed(rho, p, Gam, Pi))
 
 
-def tubes_step(offsets: np.ndarray, U: np.ndarray, cfl: float = 0.5, eps: float = 1e-40, mood: bool = True):
+def tubes_step(offsets: np.ndarray, U: np.ndarray, cfl: float = 0.5, eps: float = None, mood: bool = True,
+               weights: str = "modified"):
     """One CFL step of every independent 1D tube (padded segments given by ``offsets``).
     Returns ``(U, dts)``."""
+    if eps is None:
+        eps = default_eps(weights)
     offsets = np.ascontiguousarray(offsets, dtype=np.int64)
     U = np.ascontiguousarray(U, dtype=np.float64).copy()
     nt = offsets.size - 1
     dts = np.zeros(nt)
     lib().or_tubes_step(ctypes.c_int64(nt), offsets.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
                         ctypes.c_int64(U.shape[1]), _dp(U), ctypes.c_double(cfl), ctypes.c_double(eps),
-                        ctypes.c_int(int(mood)), _dp(dts))
+                        ctypes.c_int(int(mood)), ctypes.c_int(WEIGHTS[weights]), _dp(dts))
     return U, dts

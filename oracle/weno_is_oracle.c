@@ -715,7 +715,7 @@ void or_cons_to_prim_array(int ndim, int64_t ncell, const double *U, double *Q) 
  * [off[t], off[t+1]) of every field (3 ghosts each side), dx = 1/len,
  * transmissive ends, its own CFL dt.  dts (nullable) receives the dt used. */
 void or_tubes_step(int64_t ntubes, const int64_t *off, int64_t total, double *U, double cfl, double eps,
-                   int mood, double *dts) {
+                   int mood, int weights, double *dts) {
 #pragma omp parallel for schedule(dynamic, 1)
   for (int64_t t = 0; t < ntubes; ++t) {
     int64_t len = off[t + 1] - off[t] - 2 * NG;
@@ -728,7 +728,7 @@ void or_tubes_step(int64_t ntubes, const int64_t *off, int64_t total, double *U,
     g.dx[1] = g.dx[2] = 1.0;
     g.eps = eps;
     g.mood = mood;
-    g.weights = OR_W_MODIFIED;
+    g.weights = weights;
     int64_t P = len + 2 * NG;
     double *Ut = (double *)malloc(sizeof(double) * 5 * (size_t)P);
     for (int f = 0; f < 5; ++f) memcpy(&Ut[f * P], &U[f * total + off[t]], sizeof(double) * (size_t)P);

@@ -22,7 +22,7 @@ HEADER = os.path.join(HERE, "..", "include", "ws.h")
 WS_OK, WS_EINVAL, WS_ECUDA, WS_ENONPHYS, WS_ETIMEOUT, WS_ENOTSUP = range(6)
 BC = {"transmissive": 0, "periodic": 1, "reflective": 2}
 PRECISION = {"fp64": 0, "mixed": 1}
-WEIGHTS = {"modified": 0, "basic": 1}
+WEIGHTS = {"modified": 0, "basic": 1, "js": 2}
 NG = 3
 
 
@@ -304,11 +304,27 @@ def ws_peak_probe(kind: str, blocks: int = 0) -> float:
 
 def ws_flux_divergence_noalloc(grid: ws_grid, opts: ws_opts, stream: int, U, L):
     """L(U) without any device allocation (static scratch inside the library);
-    for callers that cannot call cudaMalloc.  Raises WsError with the
-    library's message on failure."""
+    for callers that cannot call cudaMalloc.  U and L must be contiguous
+    float64 CUDA tensors on one device, each holding at least one padded state
+    of the grid (the C side cannot check buffer sizes); the call runs with that
+    device current.  Raises ValueError on a bad tensor and WsError with the
+    library's message on a failing call."""
+    import torch
+    nv = grid.ndim + 4
+    need = nv
+    for d in range(max(1, min(grid.ndim, 3))):
+        need *= int(grid.n[d]) + 2 * NG
+    for name, t in (("U", U), ("L", L)):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+            raise ValueError(f"{name} must be a contiguous float64 CUDA tensor")
+        if t.numel() < need:
+            raise ValueError(f"{name} holds {t.numel()} doubles; the grid's padded state needs {need}")
+    if U.device != L.device:
+        raise ValueError("U and L must be on the same device")
     buf = ctypes.create_string_buffer(256)
-    rc = load().ws_flux_divergence_noalloc(ctypes.byref(grid), ctypes.byref(opts), ctypes.c_void_p(stream), _ptr(U),
-                                           _ptr(L), buf, 256)
+    with torch.cuda.device(U.device):
+        rc = load().ws_flux_divergence_noalloc(ctypes.byref(grid), ctypes.byref(opts), ctypes.c_void_p(stream),
+                                               _ptr(U), _ptr(L), buf, 256)
     if rc != WS_OK:
         raise WsError(rc, buf.value.decode())
 

@@ -18,10 +18,19 @@ namespace ws {
 namespace fp32 {
 
 struct WenoParams {
-  float eps_rel;  // relative epsilon
+  float eps_rel;  // relative epsilon of WENO-IS
   float eps_abs;  // absolute floor (keeps 0/0 away on flat stencils)
-  int weights;    // WS_W_MODIFIED or WS_W_BASIC
+  int weights;    // WS_W_MODIFIED, WS_W_BASIC or WS_W_JS
+  float eps_js;   // WS_W_JS: the absolute epsilon of WENO-JS (> 0)
 };
+
+// eps: the context's epsilon option (already defaulted).  With WENO-JS it is
+// the JS epsilon, and the 3rd-order MOOD level (the scheme's own) takes the
+// default relative epsilon of WENO-IS.
+inline WenoParams weno_params(float eps, int weights) {
+  if (weights == WS_W_JS) return WenoParams{1e-10f, 1e-30f, weights, eps};
+  return WenoParams{eps, 1e-30f, weights, 0.0f};
+}
 
 // hardware approximations (MUFU): rcp and sqrt to about 1 ulp, no IEEE
 // special-case sequences; subnormals flush to zero
@@ -66,9 +75,38 @@ __device__ __forceinline__ double f32_to_f64(float v) {
   return __longlong_as_double((long long)(((unsigned long long)hi << 32) | lo));
 }
 
+// WENO-JS of Jiang & Shu (1996), the paper's comparison scheme: candidates on
+// S_0 = {i-2,i-1,i}, S_1 = {i-1,i,i+1}, S_2 = {i,i+1,i+2} (the paper's S_4,
+// S_12, S_3), d = (1,6,3)/10, alpha_k = d_k/(eps + beta_k)^2.  In FP32 the
+// weights are scaled by (eps + beta_min)^2, which cancels in the
+// normalisation and keeps every alpha_k in [0, d_k] for any magnitude of beta.
+__device__ __forceinline__ float weno_js(float qm2, float qm1, float q0, float qp1, float qp2, float eps) {
+  const float c13_12 = 13.0f / 12.0f;
+  float dp1 = qp1 - q0, dm1 = q0 - qm1;
+  float a = (q0 - 2.0f * qp1) + qp2;
+  float b = ((3.0f * q0) - (4.0f * qp1)) + qp2;
+  float e2 = fmaf(c13_12, a * a, fmaf(0.25f, b * b, eps));
+  a = (qm2 - 2.0f * qm1) + q0;
+  b = (qm2 - (4.0f * qm1)) + (3.0f * q0);
+  float e0 = fmaf(c13_12, a * a, fmaf(0.25f, b * b, eps));
+  a = (qm1 - 2.0f * q0) + qp1;
+  b = qm1 - qp1;
+  float e1 = fmaf(c13_12, a * a, fmaf(0.25f, b * b, eps));
+  float em = fminf(fminf(e0, e1), e2);
+  float r0 = em * frcp(e0), r1 = em * frcp(e1), r2 = em * frcp(e2);
+  float a0 = r0 * r0, a1 = 6.0f * (r1 * r1), a2 = 3.0f * (r2 * r2);
+  float delta0 = fmaf(1.0f / 3.0f, qm2 - q0, (7.0f / 6.0f) * dm1);
+  float delta1 = fmaf(1.0f / 3.0f, dp1, (1.0f / 6.0f) * dm1);
+  float delta2 = fmaf(5.0f / 6.0f, dp1, -(1.0f / 6.0f) * (qp2 - q0));
+  float num = fmaf(a0, delta0, fmaf(a1, delta1, a2 * delta2));
+  return fmaf(num, frcp((a0 + a1) + a2), q0);
+}
+
 // Sec. 3.3.1-3.3.2: left value at x_{i+1/2} from q_{i-2..i+2}; order 5 or 3.
+// WENO-JS at order 5 goes to weno_js; its 3rd-order level is the scheme's.
 __device__ __forceinline__ float weno_is(float qm2, float qm1, float q0, float qp1, float qp2, const WenoParams& P,
                                          int order) {
+  if (P.weights == WS_W_JS && order == 5) return weno_js(qm2, qm1, q0, qp1, qp2, P.eps_js);
   const float c13_12 = 13.0f / 12.0f;
   float dp1 = qp1 - q0, dm1 = q0 - qm1;
   float delta1 = 0.5f * dp1;
@@ -85,7 +123,7 @@ __device__ __forceinline__ float weno_is(float qm2, float qm1, float q0, float q
   float r1 = fdiv(tau5, beta1 + eps);
   float r2 = fdiv(tau5, beta2 + eps);
   float alpha1, alpha2;
-  if (P.weights == WS_W_MODIFIED) {
+  if (P.weights != WS_W_BASIC) {
     float r12 = fdiv(tau5, beta12 + eps);
     alpha1 = 4.0f * fmaf(r1, r12, 1.0f);
     alpha2 = 2.0f * fmaf(r2, r12, 1.0f);
@@ -113,51 +151,6 @@ __device__ __forceinline__ float weno_is(float qm2, float qm1, float q0, float q
   return fmaf(num, frcp(den), q0);
 }
 
-// Both MOOD levels of one side at once: v5 (all four candidates) and v3
-// (d3 = d4 = 0, the same tau5 and modified alpha1, alpha2).
-__device__ __forceinline__ void weno_is_both(float qm2, float qm1, float q0, float qp1, float qp2,
-                                             const WenoParams& P, float& v5, float& v3) {
-  const float c13_12 = 13.0f / 12.0f;
-  float dp1 = qp1 - q0, dm1 = q0 - qm1;
-  float beta1 = dp1 * dp1;
-  float beta2 = dm1 * dm1;
-  float a = (qm1 - 2.0f * q0) + qp1;
-  float b = qm1 - qp1;
-  float beta12 = fmaf(c13_12, a * a, 0.25f * (b * b));
-  a = ((qp2 - 2.0f * qp1) + 2.0f * qm1) - qm2;
-  b = ((((qp2 - 4.0f * qp1) + 6.0f * q0) - 4.0f * qm1) + qm2);
-  float tau5 = fmaf(0.25f, a * a, c13_12 * (b * b));
-  float eps = fmaf(P.eps_rel, (beta1 + beta2) + tau5, P.eps_abs);
-  float r1 = fdiv(tau5, beta1 + eps);
-  float r2 = fdiv(tau5, beta2 + eps);
-  float alpha1, alpha2;
-  if (P.weights == WS_W_MODIFIED) {
-    float r12 = fdiv(tau5, beta12 + eps);
-    alpha1 = 4.0f * fmaf(r1, r12, 1.0f);
-    alpha2 = 2.0f * fmaf(r2, r12, 1.0f);
-  } else {
-    alpha1 = 4.0f * (1.0f + r1);
-    alpha2 = 2.0f * (1.0f + r2);
-  }
-  float num3 = 0.5f * fmaf(alpha1, dp1, alpha2 * dm1);
-  float den3 = alpha1 + alpha2;
-  float d3 = qp2 - q0, d4 = qm2 - q0;
-  float delta3 = fmaf(5.0f / 6.0f, dp1, -(1.0f / 6.0f) * d3);
-  float delta4 = fmaf(1.0f / 3.0f, d4, (7.0f / 6.0f) * dm1);
-  a = (q0 - 2.0f * qp1) + qp2;
-  b = ((3.0f * q0) - (4.0f * qp1)) + qp2;
-  float beta3 = fmaf(c13_12, a * a, 0.25f * (b * b));
-  a = (qm2 - 2.0f * qm1) + q0;
-  b = (qm2 - (4.0f * qm1)) + (3.0f * q0);
-  float beta4 = fmaf(c13_12, a * a, 0.25f * (b * b));
-  float alpha3 = 3.0f * (1.0f + fdiv(tau5, beta3 + eps));
-  float alpha4 = 1.0f + fdiv(tau5, beta4 + eps);
-  float num5 = fmaf(alpha3, delta3, fmaf(alpha4, delta4, num3));
-  float den5 = (den3 + alpha3) + alpha4;
-  v3 = fmaf(num3, frcp(den3), q0);
-  v5 = fmaf(num5, frcp(den5), q0);
-}
-
 // 5th-order reconstruction with the linear weights d = (4,2,3,1)/10, i.e.
 // (2 q_{i-2} - 13 q_{i-1} + 47 q_i + 27 q_{i+1} - 3 q_{i+2})/60, in increment
 // form about q_i (a constant stencil reconstructs exactly)
@@ -180,11 +173,35 @@ __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ float2 rcp2(float2 a) { return make_float2(frcp(a.x), frcp(a.y)); }
 
+// weno_js on both lanes
+__device__ __forceinline__ float2 js5_pair(float2 qm2, float2 qm1, float2 q0, float2 qp1, float2 qp2, float eps) {
+  const float2 c13 = f2(13.0f / 12.0f), half = f2(0.5f), ep = f2(eps);
+  float2 dp1 = sub2(qp1, q0), dm1 = sub2(q0, qm1);
+  float2 a = add2(fma2(qp1, f2(-2.0f), q0), qp2);
+  float2 b = mul2(add2(fma2(qp1, f2(-4.0f), mul2(f2(3.0f), q0)), qp2), half);
+  float2 e2 = fma2(c13, mul2(a, a), fma2(b, b, ep));
+  a = add2(fma2(qm1, f2(-2.0f), qm2), q0);
+  b = mul2(fma2(q0, f2(3.0f), fma2(qm1, f2(-4.0f), qm2)), half);
+  float2 e0 = fma2(c13, mul2(a, a), fma2(b, b, ep));
+  a = add2(fma2(q0, f2(-2.0f), qm1), qp1);
+  b = mul2(sub2(qm1, qp1), half);
+  float2 e1 = fma2(c13, mul2(a, a), fma2(b, b, ep));
+  float2 em = make_float2(fminf(fminf(e0.x, e1.x), e2.x), fminf(fminf(e0.y, e1.y), e2.y));
+  float2 r0 = mul2(em, rcp2(e0)), r1 = mul2(em, rcp2(e1)), r2 = mul2(em, rcp2(e2));
+  float2 a0 = mul2(r0, r0), a1 = mul2(f2(6.0f), mul2(r1, r1)), a2 = mul2(f2(3.0f), mul2(r2, r2));
+  float2 delta0 = fma2(f2(1.0f / 3.0f), sub2(qm2, q0), mul2(f2(7.0f / 6.0f), dm1));
+  float2 delta1 = fma2(f2(1.0f / 3.0f), dp1, mul2(f2(1.0f / 6.0f), dm1));
+  float2 delta2 = fma2(f2(5.0f / 6.0f), dp1, mul2(f2(-1.0f / 6.0f), sub2(qp2, q0)));
+  float2 num = fma2(a0, delta0, fma2(a1, delta1, mul2(a2, delta2)));
+  return fma2(num, rcp2(add2(add2(a0, a1), a2)), q0);
+}
+
 // weno_is(..., 5) on both lanes.  Factors of 1/2 and 4 are moved between
 // products where the scaling is exact (powers of two), and 3 (1 + r3) is
 // formed as one fused multiply-add.
 __device__ __forceinline__ float2 weno5_pair(float2 qm2, float2 qm1, float2 q0, float2 qp1, float2 qp2,
                                              const WenoParams& P) {
+  if (P.weights == WS_W_JS) return js5_pair(qm2, qm1, q0, qp1, qp2, P.eps_js);
   const float2 c13 = f2(13.0f / 12.0f), one = f2(1.0f), half = f2(0.5f);
   float2 dp1 = sub2(qp1, q0), dm1 = sub2(q0, qm1);
   float2 beta1 = mul2(dp1, dp1);
@@ -199,7 +216,7 @@ __device__ __forceinline__ float2 weno5_pair(float2 qm2, float2 qm1, float2 q0, 
   float2 r1 = mul2(tau5, rcp2(add2(beta1, eps)));
   float2 r2 = mul2(tau5, rcp2(add2(beta2, eps)));
   float2 alpha1, alpha2;
-  if (P.weights == WS_W_MODIFIED) {
+  if (P.weights != WS_W_BASIC) {
     float2 r12 = mul2(tau5, rcp2(add2(beta12, eps)));
     alpha1 = fma2(mul2(r1, f2(4.0f)), r12, f2(4.0f));  // 4 (1 + r1 r12)
     alpha2 = fma2(add2(r2, r2), r12, f2(2.0f));        // 2 (1 + r2 r12)

@@ -14,10 +14,40 @@
 namespace ws {
 namespace fp64 {
 
+// WENO-JS (Jiang & Shu 1996), the paper's comparison scheme: candidates on
+// S_0 = {i-2,i-1,i}, S_1 = {i-1,i,i+1}, S_2 = {i,i+1,i+2} (the paper's S_4,
+// S_12, S_3) with linear weights (1,6,3)/10 and alpha_k = d_k/(eps+beta_k)^2.
+__device__ __forceinline__ double weno_js(double qm2, double qm1, double q0, double qp1, double qp2, double eps) {
+  const double c13_12 = 13.0 / 12.0;
+  double delta3 = ((5.0 / 6.0) * (qp1 - q0)) - ((1.0 / 6.0) * (qp2 - q0));
+  double delta4 = ((1.0 / 3.0) * (qm2 - q0)) - ((7.0 / 6.0) * (qm1 - q0));
+  double deltaC = ((1.0 / 3.0) * (qp1 - q0)) - ((1.0 / 6.0) * (qm1 - q0));
+  double a, b;
+  a = (q0 - 2.0 * qp1) + qp2;
+  b = ((3.0 * q0) - (4.0 * qp1)) + qp2;
+  double beta3 = (c13_12 * (a * a)) + (0.25 * (b * b));
+  a = (qm2 - 2.0 * qm1) + q0;
+  b = (qm2 - (4.0 * qm1)) + (3.0 * q0);
+  double beta4 = (c13_12 * (a * a)) + (0.25 * (b * b));
+  a = (qm1 - 2.0 * q0) + qp1;
+  b = qm1 - qp1;
+  double beta12 = (c13_12 * (a * a)) + (0.25 * (b * b));
+  double e0 = eps + beta4, e1 = eps + beta12, e2 = eps + beta3;
+  double a0 = 1.0 / (e0 * e0);
+  double a1 = 6.0 / (e1 * e1);
+  double a2 = 3.0 / (e2 * e2);
+  double num = ((a0 * delta4) + (a1 * deltaC)) + (a2 * delta3);
+  double den = (a0 + a1) + a2;
+  return q0 + num / den;
+}
+
 // Sec. 3.3.1-3.3.2: left value at x_{i+1/2} from q_{i-2..i+2}.
-// order 5: all four candidates; order 3: d3 = d4 = 0.
+// order 5: all four candidates; order 3: d3 = d4 = 0.  WENO-JS at order 5
+// goes to weno_js; its 3rd-order MOOD level is the scheme's own (modified
+// weights).
 __device__ __forceinline__ double weno_is(double qm2, double qm1, double q0, double qp1, double qp2, double eps,
                                           int order, int weights) {
+  if (weights == WS_W_JS && order == 5) return weno_js(qm2, qm1, q0, qp1, qp2, eps);
   const double c13_12 = 13.0 / 12.0;
   // Eq. (candidates) as increments about q_i
   double delta1 = 0.5 * (qp1 - q0);
@@ -40,7 +70,7 @@ __device__ __forceinline__ double weno_is(double qm2, double qm1, double q0, dou
   double r1 = tau5 / (beta1 + eps);
   double r2 = tau5 / (beta2 + eps);
   double alpha1, alpha2;
-  if (weights == WS_W_MODIFIED) {
+  if (weights != WS_W_BASIC) {
     double r12 = tau5 / (beta12 + eps);
     alpha1 = 4.0 * (1.0 + r1 * r12);
     alpha2 = 2.0 * (1.0 + r2 * r12);

@@ -360,11 +360,12 @@ int ws_init(const ws_grid* grid, const ws_opts* opts, void* stream, ws_ctx** out
   }
   if (op.precision != WS_PREC_FP64 && op.precision != WS_PREC_MIXED)
     return fail(nullptr, WS_EINVAL, "bad precision %d", op.precision);
-  if (op.weights != WS_W_MODIFIED && op.weights != WS_W_BASIC) return fail(nullptr, WS_EINVAL, "bad weights");
+  if (op.weights != WS_W_MODIFIED && op.weights != WS_W_BASIC && op.weights != WS_W_JS)
+    return fail(nullptr, WS_EINVAL, "bad weights %d", op.weights);
   if (op.mood != 0 && op.mood != 1) return fail(nullptr, WS_EINVAL, "mood must be 0 or 1");
   if (op.learned && op.precision != WS_PREC_MIXED)
     return fail(nullptr, WS_EINVAL, "the learned gate runs in mixed precision only");
-  if (op.eps <= 0.0) op.eps = op.precision == WS_PREC_FP64 ? 1e-40 : 1e-10;
+  if (op.eps <= 0.0) op.eps = op.weights == WS_W_JS ? 1e-6 : (op.precision == WS_PREC_FP64 ? 1e-40 : 1e-10);
   if (op.cfl <= 0.0) op.cfl = 0.5;
   if (op.learned) return fail(nullptr, WS_ENOTSUP, "the learned face gate is not built in this library");
 

@@ -1045,7 +1045,7 @@ static StageArgs stage_args(const GridDev& g, int stage, double* U, float* U32, 
   a.Lp = nullptr;
   a.mask_x = nullptr;
   a.mask_a = nullptr;
-  a.P = WenoParams{eps_rel, 1e-30f, weights};
+  a.P = weno_params(eps_rel, weights);
   a.mood = mood;
   a.nbad = nbad;
   a.mlp_frag = nullptr;

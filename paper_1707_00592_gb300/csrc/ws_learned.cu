@@ -258,7 +258,7 @@ __global__ void k_adam(float* __restrict__ p, float* __restrict__ m, float* __re
 
 void launch_face_samples(const GridDev& g, int d, const float* Q, int64_t stride, int64_t out0, int64_t max_out,
                          float* feats, uint8_t* labels, float eps_rel, int weights, cudaStream_t s) {
-  WenoParams P{eps_rel, 1e-30f, weights};
+  WenoParams P = weno_params(eps_rel, weights);
   int64_t ns = (g.nfaces[d] + stride - 1) / stride;
   int b = blocks_for(ns, 128);
   switch (g.ndim) {

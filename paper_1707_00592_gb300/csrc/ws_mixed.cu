@@ -318,7 +318,7 @@ void launch_prim32(const GridDev& g, const double* U, float* Q, cudaStream_t s) 
 
 void launch_face_mixed(const GridDev& g, int d, const float* Q, float* Fh, float* us, uint8_t* mask, float eps_rel,
                        int mood, int weights, cudaStream_t s) {
-  WenoParams P{eps_rel, 1e-30f, weights};
+  WenoParams P = weno_params(eps_rel, weights);
   int b = blocks_for(g.nfaces[d], 128);
   switch (g.ndim) {
     case 1: k_face32<1><<<b, 128, 0, s>>>(g, d, Q, Fh, us, mask, P, mood); break;

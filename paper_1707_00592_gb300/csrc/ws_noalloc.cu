@@ -70,9 +70,14 @@ extern "C" WS_API int ws_flux_divergence_noalloc(const ws_grid* grid, const ws_o
   if (!grid || !opts || !U || !L || U == L) return fail(WS_EINVAL, "bad pointers");
   const ws_grid& gr = *grid;
   if (gr.ntubes > 0) return fail(WS_ENOTSUP, "batched tubes are not supported");
-  if (opts->precision != WS_PREC_FP64) return fail(WS_ENOTSUP, "FP64 only");
-  if (opts->weights != WS_W_MODIFIED && opts->weights != WS_W_BASIC)
+  // the option checks of ws_init
+  if (opts->precision != WS_PREC_FP64 && opts->precision != WS_PREC_MIXED) return fail(WS_EINVAL, "bad precision");
+  if (opts->weights != WS_W_MODIFIED && opts->weights != WS_W_BASIC && opts->weights != WS_W_JS)
     return fail(WS_EINVAL, "bad weights");
+  if (opts->mood != 0 && opts->mood != 1) return fail(WS_EINVAL, "mood must be 0 or 1");
+  if (opts->learned && opts->precision != WS_PREC_MIXED)
+    return fail(WS_EINVAL, "the learned gate runs in mixed precision only");
+  if (opts->precision != WS_PREC_FP64) return fail(WS_ENOTSUP, "FP64 only");
   if (gr.ndim < 1 || gr.ndim > 3) return fail(WS_EINVAL, "ndim must be 1, 2 or 3");
   GridDev g{};
   g.ndim = gr.ndim;
@@ -128,7 +133,7 @@ extern "C" WS_API int ws_flux_divergence_noalloc(const ws_grid* grid, const ws_o
     off += round256(g.nfaces[d]);
   }
   cudaStream_t s = (cudaStream_t)stream;
-  double eps = opts->eps > 0.0 ? opts->eps : 1e-40;
+  double eps = opts->eps > 0.0 ? opts->eps : (opts->weights == WS_W_JS ? 1e-6 : 1e-40);
   for (int d = 0; d < g.ndim; ++d) launch_ghost(g, U, d, s);
   launch_prim(g, U, Q, s);
   for (int d = 0; d < g.ndim; ++d) launch_face_fp64(g, d, Q, Fh[d], us[d], nullptr, eps, opts->mood, opts->weights, s);

@@ -320,7 +320,7 @@ void launch_tubes_stage_mixed(const TubesDev& t, int config, int stage, double* 
   a.nitems = nitems;
   a.counter = counter;
   a.mask = mask;
-  a.P = WenoParams{eps_rel, 1e-30f, weights};
+  a.P = weno_params(eps_rel, weights);
   a.mood = mood;
   a.nbad = nbad;
   switch (config) {
