@@ -275,14 +275,55 @@ WS_API int ws_gate_eval(ws_ctx *ctx, double *U, uint8_t *smooth);
 WS_API int ws_gate_stats(ws_ctx *ctx, double out[6]);
 
 /* Chooses the kernel configuration of the context by timing each candidate
- * for `steps` CFL steps on a scratch copy of U (DEVICE; U itself is not
- * modified).  Batched tubes in mixed precision: the chunk of cells a CTA of
- * the persistent stage kernel processes and its thread count, from
- * (256, 128), (256, 256), (512, 256), (512, 512), (1024, 512).  *choice (HOST,
- * nullable) receives the index chosen, or -1 when the context has nothing to
- * tune.  Allocates a scratch state for the duration of the call.
- * Synchronises. */
+ * for `steps` CFL steps (after one warm-up step) on a scratch copy of U
+ * (DEVICE; U itself is not modified).  Every candidate gives bit-identical
+ * results; only the time differs.
+ *  - Fused 2D/3D mixed-precision stages (learned gate off): the tile of cells
+ *    a CTA owns and its thread count -- 32 x 15 cells on 512 threads (two CTAs
+ *    per SM), 32 x 31 on 1024 (one CTA per SM; 2D only: with 7 fields its
+ *    shared memory exceeds a CTA's limit) or 32 x 7 on 256 (four CTAs per SM)
+ *    -- and the launch schedule: 0 one launch per stage (per pass in 3D),
+ *    consecutive launches with programmatic dependent launch (the next
+ *    launch's CTAs wait on the device for the previous grid instead of being
+ *    launched after it); 1 the same launches without it.  Candidate index =
+ *    2 x tile + schedule; 2D tiles 0, 1, 2 = 32 x 15, 32 x 31, 32 x 7; 3D
+ *    tiles 0, 1 = 32 x 15, 32 x 7.  ws_get_stage_config reports the choice.
+ *  - Batched tubes in mixed precision: the chunk of cells a CTA of the
+ *    persistent stage kernel processes and its thread count, from (256, 128),
+ *    (256, 256), (512, 256), (512, 512), (1024, 512).
+ * *choice (HOST, nullable) receives the index chosen, or -1 when the context
+ * has nothing to tune.  Allocates a scratch state for the duration of the
+ * call.  Synchronises.  The choice stays with the context (a CUDA graph of
+ * ws_set_graph is captured again). */
 WS_API int ws_autotune(ws_ctx *ctx, const double *U, int steps, int *choice);
+
+/* Sets the fused stages' configuration to candidate `index` of ws_autotune
+ * (the default is 0 in 2D: 32 x 15 tiles, stage launches with programmatic
+ * dependent launch; 1 in 3D: 32 x 15 tiles, plain launches).  WS_EINVAL on a
+ * context without fused stages or an index that is not a candidate. */
+WS_API int ws_set_stage_config(ws_ctx *ctx, int index);
+
+/* The fused stages' configuration (HOST outs, each nullable): candidate
+ * index, tile width and height in cells, threads per CTA, schedule (0 or 1
+ * as in ws_autotune).  WS_EINVAL without fused stages. */
+WS_API int ws_get_stage_config(ws_ctx *ctx, int *index, int *tile_x, int *tile_y, int *threads, int *schedule);
+
+/* enable = 1 declares that U, the state of consecutive ws_step calls of this
+ * context, changes between them only through those calls.  The fused 2D
+ * mixed-precision stages then carry the FP32 image of the state (every field
+ * rounded to FP32, E - Pi formed in FP64 first) from one step's last stage to
+ * the next step's first: stage 2 writes the image of the new state, and the
+ * next step's stage 0 reads it instead of loading and converting the FP64
+ * state of its tiles and halos.  The results are the same, bit for bit.  The
+ * next step starts over from the FP64 state after a ws_step on another state
+ * or any other call that reads or writes the state (ws_prim_to_cons,
+ * ws_flux_divergence, ws_census_step, ws_run_host, ws_face_samples,
+ * ws_gate_eval, ws_autotune, ws_set_stage_config, ws_set_mlp) -- but not
+ * after a change the caller makes to U itself, which this promise rules out.
+ * Resident steps are not replayed from a CUDA graph (ws_set_graph).  Allocates
+ * two image buffers (nv FP32 fields each) on first use.  enable = 0: off (the
+ * default).  WS_ENOTSUP on a context without the fused 2D stages. */
+WS_API int ws_set_resident(ws_ctx *ctx, int enable);
 
 /* enable != 0: ws_step calls that take the CFL step (dt <= 0) replay one CUDA
  * graph holding the whole step (CFL reduction and the three RK stages)

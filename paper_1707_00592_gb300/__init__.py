@@ -81,6 +81,9 @@ def load():
         "ws_destroy": (None, [vp]),
         "ws_profile": (ctypes.c_int, [vp, ctypes.c_int]),
         "ws_set_graph": (ctypes.c_int, [vp, ctypes.c_int]),
+        "ws_set_stage_config": (ctypes.c_int, [vp, ctypes.c_int]),
+        "ws_set_resident": (ctypes.c_int, [vp, ctypes.c_int]),
+        "ws_get_stage_config": (ctypes.c_int, [vp] + [ctypes.POINTER(ctypes.c_int)] * 5),
         "ws_autotune": (ctypes.c_int, [vp, vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
         "ws_set_mlp": (ctypes.c_int, [vp, vp, ctypes.c_float, ctypes.c_int]),
         "ws_gate_eval": (ctypes.c_int, [vp, vp, vp]),
@@ -275,6 +278,20 @@ def ws_autotune(ctx, U, steps: int = 3) -> int:
     choice = ctypes.c_int(-1)
     _check(ctx, load().ws_autotune(ctx, _ptr(U), int(steps), ctypes.byref(choice)))
     return choice.value
+
+
+def ws_set_resident(ctx, enable: bool):
+    _check(ctx, load().ws_set_resident(ctx, int(bool(enable))))
+
+
+def ws_set_stage_config(ctx, index: int):
+    _check(ctx, load().ws_set_stage_config(ctx, int(index)))
+
+
+def ws_get_stage_config(ctx) -> dict:
+    v = [ctypes.c_int(0) for _ in range(5)]
+    _check(ctx, load().ws_get_stage_config(ctx, *[ctypes.byref(x) for x in v]))
+    return dict(zip(("index", "tile_x", "tile_y", "threads", "schedule"), (x.value for x in v)))
 
 
 def ws_set_graph(ctx, enable: bool):

@@ -42,12 +42,16 @@ __device__ __forceinline__ double weno_js(double qm2, double qm1, double q0, dou
 }
 
 // Sec. 3.3.1-3.3.2: left value at x_{i+1/2} from q_{i-2..i+2}.
-// order 5: all four candidates; order 3: d3 = d4 = 0.  WENO-JS at order 5
-// goes to weno_js; its 3rd-order MOOD level is the scheme's own (modified
-// weights).
+// order 5: all four candidates; order 3: d3 = d4 = 0.  JS (the WENO-JS
+// instantiation): order 5 goes to weno_js, and the 3rd-order MOOD level is
+// the scheme's own (modified weights).
+template <bool JS>
 __device__ __forceinline__ double weno_is(double qm2, double qm1, double q0, double qp1, double qp2, double eps,
                                           int order, int weights) {
-  if (weights == WS_W_JS && order == 5) return weno_js(qm2, qm1, q0, qp1, qp2, eps);
+  if (JS) {
+    if (order == 5) return weno_js(qm2, qm1, q0, qp1, qp2, eps);
+    weights = WS_W_MODIFIED;
+  }
   const double c13_12 = 13.0 / 12.0;
   // Eq. (candidates) as increments about q_i
   double delta1 = 0.5 * (qp1 - q0);
@@ -212,7 +216,7 @@ __device__ __forceinline__ void hllc(const double* ql, const double* qr, double*
 }
 
 // One face from the sweep-frame primitives of cells i-2..i+3.
-template <int NQ>
+template <int NQ, bool JS>
 __device__ __forceinline__ void face(const double (&qc)[6][NQ], const double (&cc)[6], double eps, int mood,
                                      int weights, double* Fhat, double& ustar, int& code_l, int& code_r) {
   double rho_bar = 0.5 * (qc[2][0] + qc[3][0]);
@@ -235,7 +239,7 @@ __device__ __forceinline__ void face(const double (&qc)[6][NQ], const double (&c
         double v[5];
 #pragma unroll
         for (int k = 0; k < 5; ++k) v[k] = project<NQ>(qc[side == 0 ? k : 5 - k], r, L01, L1p, L51);
-        wt[r] = weno_is(v[0], v[1], v[2], v[3], v[4], eps, order, weights);
+        wt[r] = weno_is<JS>(v[0], v[1], v[2], v[3], v[4], eps, order, weights);
       }
       back_project<NQ>(wt, R00, R10, R1l, q[side]);
       if (!mood || admissible<NQ>(q[side])) break;

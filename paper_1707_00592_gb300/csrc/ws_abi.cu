@@ -80,6 +80,8 @@ void free_all(ws_ctx* c) {
   cudaFree(c->S1);
   cudaFree(c->Q);
   cudaFree(c->Q32);
+  cudaFree(c->img[0]);
+  cudaFree(c->img[1]);
   cudaFree(c->Ka);
   cudaFree(c->Kb);
   cudaFree(c->Lp);
@@ -220,26 +222,47 @@ int fused_run3(ws_ctx* c, double* U, double dt, const GateArgs* gate, const int*
                unsigned long long* census = nullptr) {
   const GridDev& g = c->gd;
   if (!run_if) CK(c, cudaMemsetAsync(c->lmax, 0, sizeof(unsigned long long), c->stream));
-  // The plain 2D stages follow one another with programmatic dependent launch,
-  // so one pair of profiling events spans all three (events between them
-  // would serialise the launches); elsewhere each stage is timed on its own.
-  const bool one_scope = g.ndim == 2 && !gate && !run_if && !census;
+  // The plain stages may follow one another with programmatic dependent
+  // launch, so one pair of profiling events spans all of a step's stage
+  // launches (events between them would serialise the launches); the gated
+  // and census steps time each stage on its own.
+  const int per_stage = g.ndim == 3 ? 2 : 1;
+  const bool one_scope = !gate && !run_if && !census;
   std::optional<KScope> all;
-  if (one_scope) all.emplace(c, WS_K_FACE, 3);
+  if (one_scope) all.emplace(c, WS_K_FACE, 3 * per_stage);
+  // ws_set_resident: a plain 2D step on the state the previous step left
+  // starts from that step's FP32 image (stage 0 then skips the FP64 loads)
+  // and leaves the image of its own result in the other buffer
+  float* u32 = c->Q32;
+  bool img_in = false;
+  float* img_out = nullptr;
+  if (c->resident && one_scope && g.ndim == 2) {
+    if (c->img_cur >= 0 && c->img_U == U) {
+      u32 = c->img[c->img_cur];
+      img_in = true;
+    }
+    const int out = u32 == c->img[0] ? 1 : 0;
+    img_out = c->img[out];
+    c->img_cur = out;
+    c->img_U = U;
+  } else {
+    c->img_cur = -1;
+  }
   for (int s = 0; s < 3; ++s) {
     uint8_t* mb = c->mask + (int64_t)s * c->nmask;
     std::optional<KScope> k;
-    if (!one_scope) k.emplace(c, WS_K_FACE, g.ndim == 3 ? 2 : 1);
+    if (!one_scope) k.emplace(c, WS_K_FACE, per_stage);
     const float* Kin = s == 1 ? c->Ka : c->Kb;
     float* Kout = s == 0 ? c->Ka : c->Kb;
     if (g.ndim == 3)
       launch_stage3d(g, s, U, c->Q32, Kin, Kout, c->Lp, dt, c->opts.cfl, c->lmax, c->dt_dev, mb + c->mask_off[0],
                      mb + c->mask_off[1], mb + c->mask_off[2], (float)c->opts.eps, c->opts.mood, c->opts.weights,
-                     c->nbad, census, c->stream);
+                     c->nbad, census, c->stage_tile, c->stage_sched == 0, c->stream);
     else
-      launch_stage2d(g, s, U, c->Q32, Kin, Kout, dt, c->opts.cfl, c->lmax, c->dt_dev, mb + c->mask_off[0],
+      launch_stage2d(g, s, U, u32, Kin, Kout, dt, c->opts.cfl, c->lmax, c->dt_dev, mb + c->mask_off[0],
                      mb + c->mask_off[1], (float)c->opts.eps, c->opts.mood, c->opts.weights, c->nbad, gate, run_if,
-                     census, c->stream);
+                     census, c->stage_tile, c->stage_sched == 0, s == 0 && img_in, s == 2 ? img_out : nullptr,
+                     c->stream);
   }
   return check_launch(c, "fused stage");
 }
@@ -428,6 +451,7 @@ int ws_init(const ws_grid* grid, const ws_opts* opts, void* stream, ws_ctx** out
           goto bad;
         }
         c->fused = true;
+        c->stage_sched = 1;  // the 3D passes measured faster with plain launches
       }
       for (int d = 0; d < gr.ndim; ++d)
         if ((rc = dalloc(c, &c->Fh32[d], (int64_t)g.nv * g.nfaces[d])) ||
@@ -514,6 +538,7 @@ int64_t ws_mask_size(const ws_ctx* ctx) { return ctx ? ctx->nmask : -1; }
 
 int ws_prim_to_cons(ws_ctx* c, const double* Q, double* U) {
   if (!c || !Q || !U || Q == U) return fail(c, WS_EINVAL, "bad pointers");
+  c->img_cur = -1;  // the carried FP32 image no longer follows U
   GridDev g = c->gd;
   if (tubes(c)) {
     g.ndim = 1;
@@ -531,6 +556,7 @@ int ws_cons_to_prim(ws_ctx* c, const double* U, double* Q) {
 
 int ws_flux_divergence(ws_ctx* c, double* U, double* L) {
   if (!c || !U || !L || U == L) return fail(c, WS_EINVAL, "bad pointers");
+  c->img_cur = -1;  // the carried FP32 image no longer follows U
   if (tubes(c)) return fail(c, WS_ENOTSUP, "ws_flux_divergence is not available for batched tubes");
   int rc;
   if ((rc = rhs_faces(c, U)) || (rc = faces(c, 0)) || (rc = update(c, -1, U, U, L))) return rc;
@@ -682,7 +708,9 @@ int gated_step_graph(ws_ctx* c, double* U, double dt) {
 
 int ws_step(ws_ctx* c, double* U, double dt, double* dt_used) {
   if (!c || !U) return fail(c, WS_EINVAL, "bad pointers");
-  bool graph = c->graph_on && dt <= 0.0 && c->stream != nullptr && !c->prof_on && !c->learned_on;
+  // a captured step would replay one fixed pair of image buffers, so resident
+  // steps are launched directly
+  bool graph = c->graph_on && dt <= 0.0 && c->stream != nullptr && !c->prof_on && !c->learned_on && !c->resident;
   bool ggraph = c->learned_on && c->fused && c->stream != nullptr && !c->prof_on;
   int rc = ggraph ? gated_step_graph(c, U, dt) : graph ? step_graph(c, U) : step_device(c, U, dt);
   if (rc) return rc;
@@ -702,6 +730,7 @@ int ws_step(ws_ctx* c, double* U, double dt, double* dt_used) {
 
 int ws_census_step(ws_ctx* c, double* U, double dt, double* dt_used, int64_t counts[4]) {
   if (!c || !U || !counts) return fail(c, WS_EINVAL, "bad pointers");
+  c->img_cur = -1;  // the carried FP32 image no longer follows U
   if (!c->fused) return fail(c, WS_EINVAL, "the census needs a fused mixed-precision 2D or 3D context");
   CK(c, cudaMemsetAsync(c->census, 0, 4 * sizeof(unsigned long long), c->stream));
   CK(c, cudaMemsetAsync(c->nbad, 0, sizeof(unsigned long long), c->stream));
@@ -730,7 +759,7 @@ int ws_census_step(ws_ctx* c, double* U, double dt, double* dt_used, int64_t cou
 // computes.  The kernels and their arithmetic are those of ws_step.
 int run_host_banded(ws_ctx* c, double* U_host, int nsteps, double dt, double* dt_used) {
   const GridDev& g = c->gd;
-  const int TYv = fused2d_tile_height();
+  const int TYv = fused2d_tile_height(c->stage_tile);
   const int nrt = (g.n[1] + TYv - 1) / TYv;
   const int B = nrt < 8 ? nrt : 8;
   if (!c->cp_in) {
@@ -774,7 +803,7 @@ int run_host_banded(ws_ctx* c, double* U_host, int nsteps, double dt, double* dt
     float* Kout = st == 0 ? c->Ka : c->Kb;
     launch_stage2d_band(g, st, c->Uhost_dev, c->Q32, Kin, Kout, dt, c->opts.cfl, c->lmax, c->dt_dev,
                         mb + c->mask_off[0], mb + c->mask_off[1], (float)c->opts.eps, c->opts.mood, c->opts.weights,
-                        c->nbad, r0, nr, c->stream);
+                        c->nbad, r0, nr, c->stage_tile, c->stream);
   };
   // the copy streams start after the work already queued on the context's stream
   CK(c, cudaEventRecord(ev_start, c->stream));
@@ -827,6 +856,7 @@ int run_host_banded(ws_ctx* c, double* U_host, int nsteps, double dt, double* dt
 
 int ws_run_host(ws_ctx* c, double* U_host, int nsteps, double dt, double* dt_used) {
   if (!c || !U_host || nsteps < 0) return fail(c, WS_EINVAL, "bad arguments");
+  c->img_cur = -1;  // the carried FP32 image no longer follows U
   if (!c->Uhost_dev) {
     int rc = dalloc(c, &c->Uhost_dev, c->nstate);
     if (rc) return rc;
@@ -877,6 +907,7 @@ int ws_face_samples(ws_ctx* c, double* U, int64_t stride, int64_t max_out, float
                     int64_t* count) {
   if (!c || !U || !count || stride < 1 || max_out < 0 || (max_out > 0 && (!feats || !labels)))
     return fail(c, WS_EINVAL, "bad arguments");
+  c->img_cur = -1;  // the carried FP32 image no longer follows U
   if (tubes(c) || !mixed(c)) return fail(c, WS_ENOTSUP, "face samples need a mixed-precision grid context");
   const GridDev& g = c->gd;
   for (int d = 0; d < g.ndim; ++d) launch_ghost(g, U, d, c->stream);
@@ -922,6 +953,7 @@ static void build_frags(const float* W, int nout, int nin, int ksteps, int ntile
 
 int ws_set_mlp(ws_ctx* c, const float* params, float threshold, int flags) {
   if (!c) return fail(c, WS_EINVAL, "null context");
+  c->img_cur = -1;  // the carried FP32 image no longer follows U
   if (!params) {
     c->learned_on = false;
     if (c->ggraph_exec) {
@@ -979,9 +1011,10 @@ int ws_gate_eval(ws_ctx* c, double* U, uint8_t* smooth) {
   if (!c->learned_on) return fail(c, WS_EINVAL, "no gate set (ws_set_mlp)");
   GateArgs ga{c->mlp_frag, c->mlp_bias, c->mlp_thr, -1, c->S1, c->lstat, nullptr, nullptr};
   CK(c, cudaMemsetAsync(smooth, 0, (size_t)c->nmask, c->stream));
+  c->img_cur = -1;
   launch_stage2d(c->gd, 3, U, c->Q32, c->Ka, c->Kb, 0.0, c->opts.cfl, c->lmax, c->dt_dev, smooth,
                  smooth + c->mask_off[1], (float)c->opts.eps, c->opts.mood, c->opts.weights, c->nbad, &ga, nullptr,
-                 nullptr, c->stream);
+                 nullptr, 0, false, false, nullptr, c->stream);
   return check_launch(c, "gate eval");
 }
 
@@ -994,8 +1027,75 @@ int ws_gate_stats(ws_ctx* c, double out[6]) {
   return WS_OK;
 }
 
+// Fused stage configurations: index = 2 x tile slot + schedule (0 stage
+// launches with programmatic dependent launch, 1 plain stage launches).
+static bool stage_config_valid(const ws_ctx* c, int index) {
+  return index >= 0 && index < 2 * fused_num_tiles(c->gd.ndim);
+}
+
+static void set_stage_config(ws_ctx* c, int index) {
+  c->img_cur = -1;
+  c->stage_tile = fused_tile_index(c->gd.ndim, index / 2);
+  c->stage_sched = index % 2;
+  if (c->graph_exec) {
+    cudaGraphExecDestroy(c->graph_exec);
+    c->graph_exec = nullptr;
+  }
+}
+
+static int stage_config_index(const ws_ctx* c) {
+  int k = 0;
+  for (int j = 0; j < fused_num_tiles(c->gd.ndim); ++j)
+    if (fused_tile_index(c->gd.ndim, j) == c->stage_tile) k = j;
+  return 2 * k + c->stage_sched;
+}
+
+// The fused 2D/3D stages: every configuration steps a scratch copy of U for
+// `steps` CFL steps after one warm-up step; the fastest is kept.
+static int autotune_fused(ws_ctx* c, const double* U, int steps, int* choice) {
+  double* Ut = nullptr;
+  int rc = dalloc(c, &Ut, c->nstate);
+  if (rc) return rc;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  int bestk = -1;
+  const int keep = stage_config_index(c);
+  const bool prof = c->prof_on;
+  c->prof_on = false;
+  for (int k = 0; k < 2 * fused_num_tiles(c->gd.ndim) && rc == WS_OK; ++k) {
+    set_stage_config(c, k);
+    cudaMemcpyAsync(Ut, U, sizeof(double) * c->nstate, cudaMemcpyDeviceToDevice, c->stream);
+    if ((rc = step_device(c, Ut, 0.0))) break;  // warm-up
+    cudaEventRecord(e0, c->stream);
+    for (int s = 0; s < steps && rc == WS_OK; ++s) rc = step_device(c, Ut, 0.0);
+    cudaEventRecord(e1, c->stream);
+    if (cudaEventSynchronize(e1) != cudaSuccess) rc = fail(c, WS_ECUDA, "autotune step failed");
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (rc == WS_OK && ms < best) {
+      best = ms;
+      bestk = k;
+    }
+  }
+  c->prof_on = prof;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(Ut);
+  if (rc || bestk < 0) {
+    set_stage_config(c, keep);
+    return rc ? rc : fail(c, WS_ECUDA, "autotune found no configuration");
+  }
+  set_stage_config(c, bestk);
+  if (choice) *choice = bestk;
+  return WS_OK;
+}
+
 int ws_autotune(ws_ctx* c, const double* U, int steps, int* choice) {
   if (!c || !U || steps < 1) return fail(c, WS_EINVAL, "bad arguments");
+  c->img_cur = -1;  // the carried FP32 image no longer follows U
+  if (c->fused && !c->learned_on) return autotune_fused(c, U, steps, choice);
   if (!(tubes(c) && mixed(c))) {
     if (choice) *choice = -1;
     return WS_OK;  // nothing to tune
@@ -1037,6 +1137,41 @@ int ws_autotune(ws_ctx* c, const double* U, int steps, int* choice) {
     c->graph_exec = nullptr;
   }
   if (choice) *choice = bestc;
+  return WS_OK;
+}
+
+int ws_set_resident(ws_ctx* c, int enable) {
+  if (!c) return fail(c, WS_EINVAL, "null context");
+  c->img_cur = -1;
+  if (!enable) {
+    c->resident = false;
+    return WS_OK;
+  }
+  if (!(c->fused && c->gd.ndim == 2)) return fail(c, WS_ENOTSUP, "resident state needs the fused 2D stages");
+  for (int k = 0; k < 2; ++k) {
+    int rc;
+    if (!c->img[k] && (rc = dalloc(c, &c->img[k], (int64_t)c->gd.nv * c->gd.N))) return rc;
+  }
+  c->resident = true;
+  return WS_OK;
+}
+
+int ws_set_stage_config(ws_ctx* c, int index) {
+  if (!c) return fail(c, WS_EINVAL, "null context");
+  if (!c->fused) return fail(c, WS_EINVAL, "the context has no fused stage (2D/3D mixed precision)");
+  if (!stage_config_valid(c, index)) return fail(c, WS_EINVAL, "bad configuration %d", index);
+  set_stage_config(c, index);
+  return WS_OK;
+}
+
+int ws_get_stage_config(ws_ctx* c, int* index, int* tile_x, int* tile_y, int* threads, int* schedule) {
+  if (!c) return fail(c, WS_EINVAL, "null context");
+  if (!c->fused) return fail(c, WS_EINVAL, "the context has no fused stage (2D/3D mixed precision)");
+  if (index) *index = stage_config_index(c);
+  if (tile_x) *tile_x = 32;
+  if (tile_y) *tile_y = fused2d_tile_height(c->stage_tile);
+  if (threads) *threads = c->stage_tile == 1 ? 1024 : (c->stage_tile == 2 ? 256 : 512);
+  if (schedule) *schedule = c->stage_sched;
   return WS_OK;
 }
 

@@ -12,7 +12,7 @@ namespace {
 
 using namespace fp64;
 
-template <int NDIM>
+template <int NDIM, bool JS>
 __global__ void __launch_bounds__(128) k_face(GridDev g, int d, const double* __restrict__ Q, double* __restrict__ Fh,
                                               double* __restrict__ us, uint8_t* __restrict__ mask, double eps,
                                               int mood, int weights) {
@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(128) k_face(GridDev g, int d, const double* __
     }
     double Fhat[NQ], ustar;
     int cl, cr;
-    face<NQ>(qc, cc, eps, mood, weights, Fhat, ustar, cl, cr);
+    face<NQ, JS>(qc, cc, eps, mood, weights, Fhat, ustar, cl, cr);
     // fluxes stored in the global field order (rho, rho u_1.., E, Gamma, Pi)
 #pragma unroll
     for (int m = 0; m < NQ; ++m) Fh[(foff[m] / N) * nf + f] = Fhat[m];
@@ -71,10 +71,20 @@ void launch_face_fp64(const GridDev& g, int d, const double* Q, double* Fh, doub
   int64_t b = (nf + bs - 1) / bs;
   if (b > (1LL << 30)) b = 1LL << 30;
   if (b < 1) b = 1;
+  const bool js = weights == WS_W_JS;
   switch (g.ndim) {
-    case 1: k_face<1><<<(int)b, bs, 0, s>>>(g, d, Q, Fh, us, mask, eps, mood, weights); break;
-    case 2: k_face<2><<<(int)b, bs, 0, s>>>(g, d, Q, Fh, us, mask, eps, mood, weights); break;
-    default: k_face<3><<<(int)b, bs, 0, s>>>(g, d, Q, Fh, us, mask, eps, mood, weights); break;
+    case 1:
+      if (js) k_face<1, true><<<(int)b, bs, 0, s>>>(g, d, Q, Fh, us, mask, eps, mood, weights);
+      else k_face<1, false><<<(int)b, bs, 0, s>>>(g, d, Q, Fh, us, mask, eps, mood, weights);
+      break;
+    case 2:
+      if (js) k_face<2, true><<<(int)b, bs, 0, s>>>(g, d, Q, Fh, us, mask, eps, mood, weights);
+      else k_face<2, false><<<(int)b, bs, 0, s>>>(g, d, Q, Fh, us, mask, eps, mood, weights);
+      break;
+    default:
+      if (js) k_face<3, true><<<(int)b, bs, 0, s>>>(g, d, Q, Fh, us, mask, eps, mood, weights);
+      else k_face<3, false><<<(int)b, bs, 0, s>>>(g, d, Q, Fh, us, mask, eps, mood, weights);
+      break;
   }
 }
 

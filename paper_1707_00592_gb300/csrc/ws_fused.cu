@@ -57,15 +57,27 @@ namespace {
 
 using namespace fp32;
 
-constexpr int TX = 32, TY = 15;
-constexpr int HX = TX + 2 * NG, HY = TY + 2 * NG;
-constexpr int NFX = (TX + 1) * TY, NFY = TX * (TY + 1), NF = NFX + NFY;
-constexpr int NT = 512;
+// Tile shape and CTA size of a launch: TX x TY cells per CTA of NT threads.
+// The per-face arithmetic does not depend on the tile (faces on tile edges
+// are evaluated by both tiles, with the same operands), so every tile gives
+// bit-identical results; ws_autotune chooses among them.
+template <int TX_, int TY_, int NT_>
+struct Tile {
+  static constexpr int TX = TX_, TY = TY_, NT = NT_;
+  static constexpr int HX = TX + 2 * NG, HY = TY + 2 * NG;
+  static constexpr int NFX = (TX + 1) * TY, NFY = TX * (TY + 1), NF = NFX + NFY;
+  static constexpr int NMT = (NF + 15) / 16;  // 16-face M tiles of the gate's MLP
+};
+using TileA = Tile<32, 15, 512>;   // two CTAs per SM (the default)
+using TileB = Tile<32, 31, 1024>;  // one CTA per SM, 15 % fewer halo cells per cell
+using TileC = Tile<32, 7, 256>;    // four CTAs per SM
 
 // Per-pass constants.  NQ: fields (rho, velocities, E or p, Gamma, Pi), 6 in
 // 2D and 7 in 3D; the q tile holds them as primitives plus the sound speed.
-template <int NQ_, int MODE>
+template <int NQ_, int MODE, class TL>
 struct Tr {
+  static constexpr int TX = TL::TX, TY = TL::TY, NT = TL::NT, HX = TL::HX, HY = TL::HY;
+  static constexpr int NFX = TL::NFX, NFY = TL::NFY, NF = TL::NF;
   static constexpr int NQ = NQ_;
   static constexpr int ND = NQ - 4;                 // velocity components
   static constexpr int NTG = NQ - 5;                // tangential components at a face
@@ -83,14 +95,14 @@ struct Tr {
 // learned gate (2D): BF16 MMA fragments of the MLP weights (m16n8k16, 32 lanes)
 constexpr int NFRAG1 = 2 * 4, NFRAG2 = 2 * 4, NFRAG3 = 2;  // (k-step, n-tile) pairs per layer
 constexpr int NFRAG = NFRAG1 + NFRAG2 + NFRAG3;
-constexpr int NMT = (NF + 15) / 16;  // 16-face M tiles
 
 // GATE: 0 plain; 1 the learned gate evaluates the MLP in this launch; 2 the
 // launch applies decisions stored by an earlier stage of the same step; 3 a
 // plain launch that also counts the flat-stencil decisions (census).
-template <int GATE, int NQ_, int MODE>
+template <int GATE, int NQ_, int MODE, class TL>
 struct Smem {
-  using T = Tr<NQ_, MODE>;
+  using T = Tr<NQ_, MODE, TL>;
+  static constexpr int TX = TL::TX, TY = TL::TY, NT = TL::NT, HY = TL::HY, NF = TL::NF;
   static constexpr bool CACHE = GATE != 1 && T::RK;  // own cells staged for phase C
   float q[NQ_ + 1][HY][T::QW];                // primitives + sound speed of tile and halo
   float fx[T::XF ? NQ_ + 1 : 1][TY][TX + 1];  // x-face fluxes (global field order) + face velocity
@@ -108,7 +120,9 @@ struct Smem {
   float dt;                         // the step, broadcast from thread 0
 };
 
+template <class TL>
 struct SmemGate {
+  static constexpr int NT = TL::NT, NF = TL::NF;
   uint2 frag[NFRAG][32];            // weight fragments
   float b1[32], b2[32], b3;         // biases
   uint8_t smooth[NF];               // 1: the face takes the linear weights
@@ -147,6 +161,8 @@ struct StageArgs {
   uint8_t* gflags;         // nullable: per-tile gate decisions (NF bytes per tile), written when the
                            // MLP runs, read by launches that reuse them
   int row0;                // first tile row of the launch (a launch may cover a band of tile rows)
+  int img_in;              // stage 0: U32 already holds the FP32 image of U (carried from the previous step)
+  float* img_out;          // nullable, stage 2: receives the FP32 image of the new state (2D)
   unsigned long long* census;  // census launches: [0] face-variables, [1] those with a flat stencil,
                                // [2] warp passes over a variable, [3] those in which a face took WENO-IS
 };
@@ -175,8 +191,9 @@ __device__ __forceinline__ int map_bc(int x, int n, int lo, int hi, bool& flip) 
 // orientation: x faces 0..TX-1 of the TY rows, then the TY+1 rows of faces
 // along the 2nd axis, then the TY right-most x faces.  A pass without x
 // faces numbers only the 2nd-axis rows.
-template <bool XF>
+template <bool XF, class TL>
 __device__ __forceinline__ bool face_geom(int f, int x0, int y0, int nx, int n1, bool& isx, int& hx, int& hy) {
+  constexpr int TX = TL::TX, TY = TL::TY, NFY = TL::NFY;
   if (XF && (f < TX * TY || f >= TX * TY + NFY)) {
     int j, i;
     if (f < TX * TY) {
@@ -299,7 +316,7 @@ __device__ __noinline__ void drift_item(const float* qb, const FaceGeo<T::NTG> f
   float fl, fr;
   weno_item<T, R>(qb, fg, fa, P, fl, fr);
   acc[0] += fabsf(lin.x - fl) + fabsf(lin.y - fr);
-  acc[NT] += fabsf(fl) + fabsf(fr);
+  acc[T::NT] += fabsf(fl) + fabsf(fr);
   l5 = lin.x;
   r5 = lin.y;
 }
@@ -366,10 +383,10 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
 
 // gate inputs of one face (2D): w1, w2, w6, w_Gamma of the six stencil cells,
 // each normalised over the stencil (zero for a stencil flat to 1e-6)
-template <int D>
+template <int D, class TL>
 __device__ __forceinline__ void gate_features(const float* qb, __nv_bfloat16* out) {
-  constexpr int ST = D == 0 ? 1 : HX;
-  constexpr int FS = HY * HX;
+  constexpr int ST = D == 0 ? 1 : TL::HX;
+  constexpr int FS = TL::HY * TL::HX;
   constexpr int UN = D == 0 ? 1 : 2;
   float rho_bar = 0.5f * (qb[2 * ST] + qb[3 * ST]);
   float c_bar = 0.5f * (qb[6 * FS + 2 * ST] + qb[6 * FS + 3 * ST]);
@@ -414,10 +431,11 @@ __device__ __forceinline__ void cp_async8(void* dst, const void* src) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
-template <int GATE, int NQ_, int MODE>
-__global__ void __launch_bounds__(NT, 2) k_stage(StageArgs a) {
-  using T = Tr<NQ_, MODE>;
-  using SM = Smem<GATE, NQ_, MODE>;
+template <int GATE, int NQ_, int MODE, class TL>
+__global__ void __launch_bounds__(TL::NT, 1024 / TL::NT) k_stage(StageArgs a) {  // 64 registers
+  using T = Tr<NQ_, MODE, TL>;
+  using SM = Smem<GATE, NQ_, MODE, TL>;
+  constexpr int TX = TL::TX, TY = TL::TY, NT = TL::NT, NF = TL::NF, NMT = TL::NMT;
   constexpr bool LEARNED = GATE == 1 || GATE == 2;  // faces may take the linear weights by the gate's decision
   constexpr bool CENSUS = GATE == 3;
   constexpr int NQ = NQ_, ND = T::ND, FS = T::FS;
@@ -426,7 +444,7 @@ __global__ void __launch_bounds__(NT, 2) k_stage(StageArgs a) {
   constexpr int AX1 = MODE == 2 ? 2 : 1, AXP = MODE == 2 ? 1 : 2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SM& S = *reinterpret_cast<SM*>(smem_raw);
-  SmemGate& SG = *reinterpret_cast<SmemGate*>(smem_raw + sizeof(SM));
+  SmemGate<TL>& SG = *reinterpret_cast<SmemGate<TL>*>(smem_raw + sizeof(SM));
   // Launched with programmatic stream serialization (the plain 2D stage), a
   // CTA may become resident while the previous stage is still finishing: it
   // waits here until that grid has completed and its writes are visible, and
@@ -508,7 +526,10 @@ __global__ void __launch_bounds__(NT, 2) k_stage(StageArgs a) {
       fla[t] = fa;
       int64_t i = pbase + (int64_t)(g.G[AX1] + ma) * S1 + mx;
       own[t] = hx >= T::QX && hx < T::QX + TX && hy >= NG && hy < NG + TY && !outx && !outa;
-      if (a.stage == 0 || a.stage == 3) {
+      if (a.stage == 0 && a.img_in) {  // the image the previous step's stage 2 left
+#pragma unroll
+        for (int m = 0; m < NQ; ++m) ld[t][m] = __ldg(&a.U32[m * N + i]);
+      } else if (a.stage == 0 || a.stage == 3) {
         const double* U = a.U;
 #pragma unroll
         for (int m = 0; m < NQ; ++m) {
@@ -613,12 +634,12 @@ __global__ void __launch_bounds__(NT, 2) k_stage(StageArgs a) {
       bool isx;
       int hx, hy;
       SG.smooth[f] = 0;
-      if (!face_geom<true>(f, x0, y0, nx, n1, isx, hx, hy)) continue;
+      if (!face_geom<true, TL>(f, x0, y0, nx, n1, isx, hx, hy)) continue;
       const float* qb = &S.q[0][hy][hx];
       if (isx)
-        gate_features<0>(qb, S.feat[f]);
+        gate_features<0, TL>(qb, S.feat[f]);
       else
-        gate_features<1>(qb, S.feat[f]);
+        gate_features<1, TL>(qb, S.feat[f]);
     }
     __syncthreads();
     const int lane = tid & 31, warp = tid >> 5, g8 = lane >> 2, t4 = lane & 3;
@@ -677,7 +698,7 @@ __global__ void __launch_bounds__(NT, 2) k_stage(StageArgs a) {
       for (int f = tid; f < NF; f += NT) {
         bool isx;
         int hx, hy;
-        if (!face_geom<true>(f, x0, y0, nx, n1, isx, hx, hy)) continue;
+        if (!face_geom<true, TL>(f, x0, y0, nx, n1, isx, hx, hy)) continue;
         if (isx)
           a.mask_x[(int64_t)(y0 + hy - NG) * (nx + 1) + (x0 + hx)] = SG.smooth[f];
         else
@@ -699,7 +720,7 @@ __global__ void __launch_bounds__(NT, 2) k_stage(StageArgs a) {
   for (int f = tid; f < T::NFP; f += NT) {
     bool isx;
     int hx, hy;
-    if (!face_geom<T::XF>(f, x0, y0, nx, n1, isx, hx, hy)) continue;
+    if (!face_geom<T::XF, TL>(f, x0, y0, nx, n1, isx, hx, hy)) continue;
     const float* qb = q0 + hy * T::QW + hx;  // stencil cell 0 in the q tile
     const bool sm = LEARNED && SG.smooth[f];
     FaceGeo<T::NTG> fg;
@@ -822,7 +843,7 @@ __global__ void __launch_bounds__(NT, 2) k_stage(StageArgs a) {
     for (int f = tid; f < T::NFP; f += NT) {
       bool isx;
       int hx, hy;
-      if (!face_geom<T::XF>(f, x0, y0, nx, n1, isx, hx, hy)) continue;
+      if (!face_geom<T::XF, TL>(f, x0, y0, nx, n1, isx, hx, hy)) continue;
       nval += 1.0f;
       nsm += SG.smooth[f] ? 1.0f : 0.0f;
     }
@@ -897,12 +918,20 @@ __global__ void __launch_bounds__(NT, 2) k_stage(StageArgs a) {
       } else {
         // this cell's U^n is read only here, by this thread, so U is updated in place
         float d[NQ];
+        double uE = 0.0, uPi = 0.0;
 #pragma unroll
         for (int m = 0; m < NQ; ++m) {
           d[m] = dt * fmaf(1.0f / 6.0f, kin(m), (2.0f / 3.0f) * inc[m]);
           double u = CACHE ? S.own.u[m][j][i] : a.U[m * N + gi];
-          a.U[m * N + gi] = u + f32_to_f64(d[m]);  // FP64 accumulation
+          const double un = u + f32_to_f64(d[m]);  // FP64 accumulation
+          a.U[m * N + gi] = un;
+          if (m == NQ - 3) uE = un;
+          if (m == NQ - 1) uPi = un;
+          // the FP32 image of the new state for the next step's stage 0: the
+          // values its phase A would form from U (E - Pi in FP64), bit for bit
+          if (MODE == 0 && a.img_out && m != NQ - 3) a.img_out[m * N + gi] = f64_to_f32(un);
         }
+        if (MODE == 0 && a.img_out) a.img_out[(NQ - 3) * N + gi] = f64_to_f32(uE - uPi);
         // admissibility of the new state (rho > 0, Gamma > 0, (Gamma+1) p + Pi > 0)
         // from its FP32 image: a diagnostic, not part of the update
         auto v = [&](int m) { return CACHE ? S.own.v[m][j][i] : a.U32[m * N + gi]; };
@@ -965,56 +994,60 @@ void launch_restore(const int* redo, const double* src, double* dst, int64_t n, 
   k_restore<<<152 * 4, 256, 0, s>>>(redo, src, dst, n);
 }
 
-using SmPlain2 = Smem<0, 6, 0>;
-using SmGated2 = Smem<1, 6, 0>;
-using SmReuse2 = Smem<2, 6, 0>;
-using SmPass1 = Smem<0, 7, 1>;
-using SmPass2 = Smem<0, 7, 2>;
-using SmCensus2 = Smem<3, 6, 0>;
-using SmCensus3a = Smem<3, 7, 1>;
-using SmCensus3b = Smem<3, 7, 2>;
+// dynamic shared memory of each instantiation
+template <int GATE, int NQ, int MODE, class TL>
+constexpr int smem_of() {
+  return (int)(sizeof(Smem<GATE, NQ, MODE, TL>) + ((GATE == 1 || GATE == 2) ? sizeof(SmemGate<TL>) : 0));
+}
 
-int fused2d_smem_bytes() { return (int)(sizeof(SmGated2) + sizeof(SmemGate)); }
+template <int GATE, int NQ, int MODE, class TL>
+static cudaError_t allow_smem() {
+  return cudaFuncSetAttribute(k_stage<GATE, NQ, MODE, TL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              smem_of<GATE, NQ, MODE, TL>());
+}
+
+int fused2d_smem_bytes() { return smem_of<1, 6, 0, TileA>(); }
 
 cudaError_t fused2d_prepare() {
-  cudaError_t e = cudaFuncSetAttribute(k_stage<0, 6, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)sizeof(SmPlain2));
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_stage<1, 6, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)(sizeof(SmGated2) + sizeof(SmemGate)));
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_stage<3, 6, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(SmCensus2));
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_stage<2, 6, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)(sizeof(SmReuse2) + sizeof(SmemGate)));
+  cudaError_t e;
+  if ((e = allow_smem<0, 6, 0, TileA>()) || (e = allow_smem<1, 6, 0, TileA>()) || (e = allow_smem<2, 6, 0, TileA>()) ||
+      (e = allow_smem<3, 6, 0, TileA>()) || (e = allow_smem<0, 6, 0, TileB>()) || (e = allow_smem<3, 6, 0, TileB>()) ||
+      (e = allow_smem<0, 6, 0, TileC>()) || (e = allow_smem<3, 6, 0, TileC>()))
+    return e;
+  return cudaSuccess;
 }
 
 int64_t fused2d_gate_flag_bytes(const GridDev& g) {
-  return (int64_t)((g.n[0] + TX - 1) / TX) * ((g.n[1] + TY - 1) / TY) * NF;
+  return (int64_t)((g.n[0] + TileA::TX - 1) / TileA::TX) * ((g.n[1] + TileA::TY - 1) / TileA::TY) * TileA::NF;
 }
 
-int fused3d_smem_bytes() { return (int)(sizeof(SmPass1) > sizeof(SmPass2) ? sizeof(SmPass1) : sizeof(SmPass2)); }
+int fused3d_smem_bytes() {
+  int a = smem_of<0, 7, 1, TileA>(), b = smem_of<0, 7, 2, TileA>();
+  return a > b ? a : b;
+}
 
 cudaError_t fused3d_prepare() {
-  cudaError_t e = cudaFuncSetAttribute(k_stage<0, 7, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)sizeof(SmPass1));
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_stage<3, 7, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(SmCensus3a));
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_stage<3, 7, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(SmCensus3b));
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_stage<0, 7, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)sizeof(SmPass2));
+  cudaError_t e;
+  if ((e = allow_smem<0, 7, 1, TileA>()) || (e = allow_smem<0, 7, 2, TileA>()) || (e = allow_smem<3, 7, 1, TileA>()) ||
+      (e = allow_smem<3, 7, 2, TileA>()) || (e = allow_smem<0, 7, 1, TileC>()) || (e = allow_smem<0, 7, 2, TileC>()) ||
+      (e = allow_smem<3, 7, 1, TileC>()) || (e = allow_smem<3, 7, 2, TileC>()))
+    return e;
+  return cudaSuccess;
 }
 
-// Launch with programmatic stream serialization: the stage's CTAs may be
-// scheduled before the previous kernel on the stream has finished and wait in
-// griddepcontrol.wait, which hides the launch latency between the stages.
-template <class K>
-static cudaError_t launch_pdl(K kernel, dim3 grid, size_t smem, cudaStream_t s, const StageArgs& a) {
+// Launch with programmatic stream serialization (pdl): the stage's CTAs may
+// be scheduled before the previous kernel on the stream has finished and wait
+// in griddepcontrol.wait, which hides the launch latency between the stages.
+template <int GATE, int NQ, int MODE, class TL>
+static void launch_k(dim3 grid, bool pdl, cudaStream_t s, const StageArgs& a) {
+  constexpr int smem = smem_of<GATE, NQ, MODE, TL>();
+  if (!pdl) {
+    k_stage<GATE, NQ, MODE, TL><<<grid, TL::NT, smem, s>>>(a);
+    return;
+  }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = grid;
-  cfg.blockDim = dim3(NT);
+  cfg.blockDim = dim3(TL::NT);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
@@ -1022,7 +1055,12 @@ static cudaError_t launch_pdl(K kernel, dim3 grid, size_t smem, cudaStream_t s, 
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, kernel, a);
+  cudaLaunchKernelEx(&cfg, k_stage<GATE, NQ, MODE, TL>, a);
+}
+
+template <class TL>
+static dim3 grid2d(const GridDev& g, int nrows = -1) {
+  return dim3((g.n[0] + TL::TX - 1) / TL::TX, nrows >= 0 ? nrows : (g.n[1] + TL::TY - 1) / TL::TY);
 }
 
 static StageArgs stage_args(const GridDev& g, int stage, double* U, float* U32, const float* Kin, float* Kout,
@@ -1059,20 +1097,31 @@ static StageArgs stage_args(const GridDev& g, int stage, double* U, float* U32, 
   a.gflags = nullptr;
   a.row0 = 0;
   a.census = nullptr;
+  a.img_in = 0;
+  a.img_out = nullptr;
   return a;
 }
+
+// The stage configurations ws_autotune chooses among: tile (0 TileA, 1 TileB,
+// 2 TileC) and whether consecutive stages are launched with programmatic
+// dependent launch.  3D launches take TileA or TileC (TileB's shared memory
+// exceeds a CTA's limit with 7 fields).
+int fused_num_tiles(int ndim) { return ndim == 3 ? 2 : 3; }
+int fused_tile_index(int ndim, int k) { return ndim == 3 ? (k == 0 ? 0 : 2) : k; }
 
 void launch_stage2d(const GridDev& g, int stage, double* U, float* U32, const float* Kin, float* Kout,
                     double dt_fixed, double cfl, unsigned long long* lmax, double* dt_out, uint8_t* mask_x,
                     uint8_t* mask_y, float eps_rel, int mood, int weights, unsigned long long* nbad,
-                    const GateArgs* gate, const int* run_if, unsigned long long* census, cudaStream_t s) {
+                    const GateArgs* gate, const int* run_if, unsigned long long* census, int tile, bool pdl,
+                    bool img_in, float* img_out, cudaStream_t s) {
   StageArgs a = stage_args(g, stage, U, U32, Kin, Kout, dt_fixed, cfl, lmax, dt_out, eps_rel, mood, weights, nbad);
+  a.img_in = img_in ? 1 : 0;
+  a.img_out = img_out;
   a.mask_x = mask_x;
   a.mask_a = mask_y;
   a.run_if = run_if;
   a.census = census;
-  dim3 grid((g.n[0] + TX - 1) / TX, (g.n[1] + TY - 1) / TY);
-  if (gate) {
+  if (gate) {  // the learned gate runs on the default tile
     a.mlp_frag = gate->frag;
     a.mlp_bias = gate->bias;
     a.thr = gate->thr;
@@ -1082,57 +1131,77 @@ void launch_stage2d(const GridDev& g, int stage, double* U, float* U32, const fl
     a.lstat = gate->lstat;
     a.gflags = gate->flags;
     if (gate->flags && (stage == 1 || stage == 2))  // decisions of this step's stage 0
-      k_stage<2, 6, 0><<<grid, NT, sizeof(SmReuse2) + sizeof(SmemGate), s>>>(a);
+      launch_k<2, 6, 0, TileA>(grid2d<TileA>(g), false, s, a);
     else
-      k_stage<1, 6, 0><<<grid, NT, sizeof(SmGated2) + sizeof(SmemGate), s>>>(a);
-  } else if (census) {
-    k_stage<3, 6, 0><<<grid, NT, sizeof(SmCensus2), s>>>(a);
-  } else if (run_if) {  // inside a conditional graph body: a plain launch
-    k_stage<0, 6, 0><<<grid, NT, sizeof(SmPlain2), s>>>(a);
-  } else {
-    // 1.7 % faster per step on the 1024^2 shock-bubble; the 3D passes were
-    // measured 3 % slower with it and keep plain launches
-    launch_pdl(k_stage<0, 6, 0>, grid, sizeof(SmPlain2), s, a);
+      launch_k<1, 6, 0, TileA>(grid2d<TileA>(g), false, s, a);
+    return;
+  }
+  if (run_if) pdl = false;  // inside a conditional graph body: plain launches
+  if (census) {
+    switch (tile) {
+      case 1: launch_k<3, 6, 0, TileB>(grid2d<TileB>(g), false, s, a); break;
+      case 2: launch_k<3, 6, 0, TileC>(grid2d<TileC>(g), false, s, a); break;
+      default: launch_k<3, 6, 0, TileA>(grid2d<TileA>(g), false, s, a); break;
+    }
+    return;
+  }
+  switch (tile) {
+    case 1: launch_k<0, 6, 0, TileB>(grid2d<TileB>(g), pdl, s, a); break;
+    case 2: launch_k<0, 6, 0, TileC>(grid2d<TileC>(g), pdl, s, a); break;
+    default: launch_k<0, 6, 0, TileA>(grid2d<TileA>(g), pdl, s, a); break;
   }
 }
 
-int fused2d_tile_height() { return TY; }
+int fused2d_tile_height(int tile) { return tile == 1 ? TileB::TY : (tile == 2 ? TileC::TY : TileA::TY); }
 
 void launch_stage2d_band(const GridDev& g, int stage, double* U, float* U32, const float* Kin, float* Kout,
                          double dt_fixed, double cfl, unsigned long long* lmax, double* dt_out, uint8_t* mask_x,
                          uint8_t* mask_y, float eps_rel, int mood, int weights, unsigned long long* nbad, int row0,
-                         int nrows, cudaStream_t s) {
+                         int nrows, int tile, cudaStream_t s) {
   StageArgs a = stage_args(g, stage, U, U32, Kin, Kout, dt_fixed, cfl, lmax, dt_out, eps_rel, mood, weights, nbad);
   a.mask_x = mask_x;
   a.mask_a = mask_y;
   a.row0 = row0;
-  dim3 grid((g.n[0] + TX - 1) / TX, nrows);
-  k_stage<0, 6, 0><<<grid, NT, sizeof(SmPlain2), s>>>(a);
+  switch (tile) {
+    case 1: launch_k<0, 6, 0, TileB>(grid2d<TileB>(g, nrows), false, s, a); break;
+    case 2: launch_k<0, 6, 0, TileC>(grid2d<TileC>(g, nrows), false, s, a); break;
+    default: launch_k<0, 6, 0, TileA>(grid2d<TileA>(g, nrows), false, s, a); break;
+  }
+}
+
+template <class TL>
+static void stage3d_passes(const GridDev& g, const StageArgs& a0, uint8_t* mask_x, uint8_t* mask_y, uint8_t* mask_z,
+                           bool census, bool pdl, cudaStream_t s) {
+  StageArgs a = a0;
+  // pass 1: x and y faces of every z plane -> x + y part of the divergence
+  a.mask_x = mask_x;
+  a.mask_a = mask_y;
+  dim3 g1((g.n[0] + TL::TX - 1) / TL::TX, (g.n[1] + TL::TY - 1) / TL::TY, g.n[2]);
+  if (census)
+    launch_k<3, 7, 1, TL>(g1, false, s, a);
+  else
+    launch_k<0, 7, 1, TL>(g1, pdl, s, a);
+  // pass 2: z faces of every y plane, the whole divergence and the RK stage
+  a.mask_x = nullptr;
+  a.mask_a = mask_z;
+  dim3 g2((g.n[0] + TL::TX - 1) / TL::TX, (g.n[2] + TL::TY - 1) / TL::TY, g.n[1]);
+  if (census)
+    launch_k<3, 7, 2, TL>(g2, false, s, a);
+  else
+    launch_k<0, 7, 2, TL>(g2, pdl, s, a);
 }
 
 void launch_stage3d(const GridDev& g, int stage, double* U, float* U32, const float* Kin, float* Kout, float* Lp,
                     double dt_fixed, double cfl, unsigned long long* lmax, double* dt_out, uint8_t* mask_x,
                     uint8_t* mask_y, uint8_t* mask_z, float eps_rel, int mood, int weights, unsigned long long* nbad,
-                    unsigned long long* census, cudaStream_t s) {
+                    unsigned long long* census, int tile, bool pdl, cudaStream_t s) {
   StageArgs a = stage_args(g, stage, U, U32, Kin, Kout, dt_fixed, cfl, lmax, dt_out, eps_rel, mood, weights, nbad);
   a.Lp = Lp;
   a.census = census;
-  // pass 1: x and y faces of every z plane -> x + y part of the divergence
-  a.mask_x = mask_x;
-  a.mask_a = mask_y;
-  dim3 g1((g.n[0] + TX - 1) / TX, (g.n[1] + TY - 1) / TY, g.n[2]);
-  if (census)
-    k_stage<3, 7, 1><<<g1, NT, sizeof(SmCensus3a), s>>>(a);
+  if (tile == 2)
+    stage3d_passes<TileC>(g, a, mask_x, mask_y, mask_z, census != nullptr, pdl, s);
   else
-    k_stage<0, 7, 1><<<g1, NT, sizeof(SmPass1), s>>>(a);
-  // pass 2: z faces of every y plane, the whole divergence and the RK stage
-  a.mask_x = nullptr;
-  a.mask_a = mask_z;
-  dim3 g2((g.n[0] + TX - 1) / TX, (g.n[2] + TY - 1) / TY, g.n[1]);
-  if (census)
-    k_stage<3, 7, 2><<<g2, NT, sizeof(SmCensus3b), s>>>(a);
-  else
-    k_stage<0, 7, 2><<<g2, NT, sizeof(SmPass2), s>>>(a);
+    stage3d_passes<TileA>(g, a, mask_x, mask_y, mask_z, census != nullptr, pdl, s);
 }
 
 }  // namespace ws

@@ -56,6 +56,13 @@ struct ws_ctx {
   float* Kb = nullptr;          // fused: RK increments K1 (stage 1 -> 2)
   float* Lp = nullptr;          // fused 3D: x + y part of the divergence (first pass -> second)
   bool fused = false;           // fused mixed-precision stage kernels in use (2D or 3D)
+  int stage_tile = 0;           // fused: tile shape of the stage launches (ws_autotune)
+  int stage_sched = 0;          // fused: 0 stage launches with programmatic dependent launch, 1 plain
+                                // stage launches (ws_autotune)
+  bool resident = false;        // fused 2D: carry the FP32 image of U between steps (ws_set_resident)
+  float* img[2] = {nullptr, nullptr};  // the two image buffers (one read by a step, one written)
+  int img_cur = -1;             // image valid for the next step on img_U, or -1
+  const double* img_U = nullptr;
   double* Fh[3] = {nullptr, nullptr, nullptr};  // face fluxes per direction (nv fields)
   double* us[3] = {nullptr, nullptr, nullptr};  // face velocities per direction
   float* Fh32[3] = {nullptr, nullptr, nullptr}; // mixed precision face fluxes
@@ -153,17 +160,23 @@ struct GateArgs {
 };
 int64_t fused2d_gate_flag_bytes(const GridDev& g);
 // plain 2D stage over the tile rows [row0, row0 + nrows) only
-int fused2d_tile_height();
+// tile shapes of the fused stages (index 0, 1, 2: 32 x 15 cells per CTA of
+// 512 threads, 32 x 31 of 1024, 32 x 7 of 256); 3D takes 0 and 2
+int fused_num_tiles(int ndim);
+int fused_tile_index(int ndim, int k);
+int fused2d_tile_height(int tile);
+
 void launch_stage2d_band(const GridDev& g, int stage, double* U, float* U32, const float* Kin, float* Kout,
                          double dt_fixed, double cfl, unsigned long long* lmax, double* dt_out, uint8_t* mask_x,
                          uint8_t* mask_y, float eps_rel, int mood, int weights, unsigned long long* nbad, int row0,
-                         int nrows, cudaStream_t s);
+                         int nrows, int tile, cudaStream_t s);
 int fused2d_smem_bytes();
 cudaError_t fused2d_prepare();
 void launch_stage2d(const GridDev& g, int stage, double* U, float* U32, const float* Kin, float* Kout,
                     double dt_fixed, double cfl, unsigned long long* lmax, double* dt_out, uint8_t* mask_x,
                     uint8_t* mask_y, float eps_rel, int mood, int weights, unsigned long long* nbad,
-                    const GateArgs* gate, const int* run_if, unsigned long long* census, cudaStream_t s);
+                    const GateArgs* gate, const int* run_if, unsigned long long* census, int tile, bool pdl,
+                    bool img_in, float* img_out, cudaStream_t s);
 // census (nullable, without a gate): the same stage, also counting the
 // flat-stencil decisions into census[4] (face-variables, flat ones, warp
 // passes, warp passes that ran WENO-IS)
@@ -174,7 +187,7 @@ cudaError_t fused3d_prepare();
 void launch_stage3d(const GridDev& g, int stage, double* U, float* U32, const float* Kin, float* Kout, float* Lp,
                     double dt_fixed, double cfl, unsigned long long* lmax, double* dt_out, uint8_t* mask_x,
                     uint8_t* mask_y, uint8_t* mask_z, float eps_rel, int mood, int weights, unsigned long long* nbad,
-                    unsigned long long* census, cudaStream_t s);
+                    unsigned long long* census, int tile, bool pdl, cudaStream_t s);
 void launch_gate_decide(const float* lstat, unsigned long long* nbad, unsigned long long* lmax, int flags, int* redo,
                         double* stats, int* drift_dev, cudaGraphConditionalHandle cond, cudaStream_t s);
 void launch_restore(const int* redo, const double* src, double* dst, int64_t n, cudaStream_t s);

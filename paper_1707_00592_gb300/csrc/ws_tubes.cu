@@ -91,6 +91,7 @@ __global__ void k_tubes_cfl(TubesDev t, const double* __restrict__ Q, unsigned l
 
 // face i+1/2 of a tube stored at padded cell i (faces -1/2 .. len-1/2 sit on
 // the cells off+2 .. off+len+2); other cells get the mask byte 0xff.
+template <bool JS>
 __global__ void __launch_bounds__(128) k_tubes_face(TubesDev t, const double* __restrict__ Q, double* __restrict__ Fh,
                                                     double* __restrict__ us, uint8_t* __restrict__ mask, double eps,
                                                     int mood, int weights) {
@@ -112,7 +113,7 @@ __global__ void __launch_bounds__(128) k_tubes_face(TubesDev t, const double* __
     }
     double Fhat[5], ustar;
     int cl, cr;
-    face<5>(qc, cc, eps, mood, weights, Fhat, ustar, cl, cr);
+    face<5, JS>(qc, cc, eps, mood, weights, Fhat, ustar, cl, cr);
 #pragma unroll
     for (int m = 0; m < 5; ++m) Fh[m * N + i] = Fhat[m];
     us[i] = ustar;
@@ -178,7 +179,10 @@ void launch_tubes_cfl(const TubesDev& t, const double* Q, unsigned long long* lm
 }
 void launch_tubes_face_fp64(const TubesDev& t, const double* Q, double* Fh, double* us, uint8_t* mask, double eps,
                             int mood, int weights, cudaStream_t s) {
-  k_tubes_face<<<blocks_for(t.total, 128), 128, 0, s>>>(t, Q, Fh, us, mask, eps, mood, weights);
+  if (weights == WS_W_JS)
+    k_tubes_face<true><<<blocks_for(t.total, 128), 128, 0, s>>>(t, Q, Fh, us, mask, eps, mood, weights);
+  else
+    k_tubes_face<false><<<blocks_for(t.total, 128), 128, 0, s>>>(t, Q, Fh, us, mask, eps, mood, weights);
 }
 void launch_tubes_update(const TubesDev& t, int stage, const double* Un, const double* Us, double* Uout,
                          const double* Fh, const double* us, const double* dt_dev, unsigned long long* nbad,

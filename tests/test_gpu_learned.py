@@ -64,30 +64,51 @@ def test_adam_step():
 
 
 def oracle_face_features(qc, cc):
-    """FP64 features and label of one face from the oracle's own functions."""
+    """FP64 features and label of one face from the oracle's own functions,
+    and whether every decision behind the label clears the FP32 noise of the
+    kernel's evaluation.  The kernel's characteristic values carry about 3e-7
+    of the scale of the terms the projection adds (p and rho_bar c_bar u_n for
+    the acoustic variables, rho and p / c_bar^2 for the entropy variable; a few
+    FP32 ulps), and WENO-IS minus the linear-weight value about twice that; a
+    flatness test within 3e-7 of that scale of its threshold, a |WENO-IS -
+    linear| > 1e-6 range comparison within 6e-7 of it, or an admissibility test
+    within 1e-5 of its terms' scale of zero, counts as undecided."""
     nq = qc.shape[1]
     rho_bar = 0.5 * (qc[2, 0] + qc[3, 0])
     c_bar = 0.5 * (cc[2] + cc[3])
     Lm, Rm = oracle.char_matrices(nq, rho_bar, c_bar)
     w = qc @ Lm.T
+    ip = nq - 3
+    term = {0: 0.5 * np.max(np.abs(qc[:, ip]) + np.abs(rho_bar * c_bar * qc[:, 1])),
+            nq - 1: 0.5 * np.max(np.abs(qc[:, ip]) + np.abs(rho_bar * c_bar * qc[:, 1])),
+            1: np.max(np.abs(qc[:, 0]) + np.abs(qc[:, ip]) / (c_bar * c_bar))}
     feats = []
     rough = False
+    robust = True
     full = np.zeros((2, nq))
     flat_gamma = False
     for r in range(nq):
         col = w[:, r]
-        rng_ = col.max() - col.min() + 1e-30
-        flat_r = col.max() - col.min() <= 1e-6 * max(abs(col.max()), abs(col.min()))
-        if r == nq - 3:
+        span = col.max() - col.min()
+        mag = max(abs(col.max()), abs(col.min()))
+        eta = 3e-7 * max(term.get(r, mag), mag)
+        rng_ = span + 1e-30
+        flat_r = span <= 1e-6 * mag
+        shear = 2 <= r < ip
+        if not shear and span > 0.0 and abs(span - 1e-6 * mag) < eta:
+            robust = False
+        if r == ip:
             flat_gamma = flat_r
         for side in range(2):
             v = col[0:5] if side == 0 else col[5:0:-1]
             f, _ = oracle.weno_is(v)
             lin = v[2] + (2 * (v[0] - v[2]) - 13 * (v[1] - v[2]) + 27 * (v[3] - v[2]) - 3 * (v[4] - v[2])) / 60.0
-            flat = flat_r or (r == nq - 2 and flat_gamma)
-            shear = 2 <= r < nq - 3
-            if not shear and not flat and abs(f - lin) > 1e-6 * rng_:
-                rough = True
+            flat = flat_r or (r == ip + 1 and flat_gamma)
+            if not shear and not flat:
+                if abs(f - lin) > 1e-6 * rng_:
+                    rough = True
+                if abs(abs(f - lin) - 1e-6 * rng_) < 2 * eta:
+                    robust = False
             full[side, r] = f
     cond = []
     for r in (0, 1, nq - 1, nq - 3):
@@ -101,16 +122,31 @@ def oracle_face_features(qc, cc):
         q = Rm @ full[side]
         if not (q[0] > 0 and q[-2] > 0 and (q[-2] + 1) * q[-3] + q[-1] > 0):
             rough = True
-    return np.concatenate(feats), int(rough), np.concatenate(cond)
+        if abs(q[0]) < 1e-5 * np.abs(qc[:, 0]).max():
+            robust = False
+        if abs((q[-2] + 1) * q[-3] + q[-1]) < 1e-5 * (abs((q[-2] + 1) * q[-3]) + abs(q[-1])):
+            robust = False
+    return np.concatenate(feats), int(rough), np.concatenate(cond), robust
 
 
-def test_face_samples_match_oracle():
-    case = wl.random_state(2, (64, 48), seed=6, kind="two_phase")
+@pytest.mark.parametrize("kind,stride,least", [("shock_bubble", 3, 0.75), ("two_phase", 7, 0.25)])
+def test_face_samples_match_oracle(kind, stride, least):
+    """Features and labels of the sampled faces against the FP64 scheme
+    oracle: every label whose decisions clear the FP32 noise band agrees
+    exactly.  On the shock-bubble (15 steps in) most faces are decided; on a
+    random two-phase state, with a jump at nearly every face, far fewer."""
+    if kind == "shock_bubble":
+        case = wl.shock_bubble_2d(96)
+        g = oracle.Grid(2, case.n, case.dx, case.bc)
+        Uo = oracle.prim_to_cons(2, case.Q)
+        for _ in range(15):
+            Uo, _, _ = oracle.step(g, Uo)
+    else:
+        case = wl.random_state(2, (64, 48), seed=6, kind=kind)
+        Uo = oracle.prim_to_cons(2, case.Q)
     s = ws.Solver(2, case.n, case.dx, case.bc, precision="mixed")
-    Uo = oracle.prim_to_cons(2, case.Q)
     U = s.tensor(Uo)
-    stride = 7
-    nmax = 2000
+    nmax = 8000
     feats = torch.empty((nmax, 24), dtype=torch.float32, device="cuda")
     labels = torch.empty(nmax, dtype=torch.uint8, device="cuda")
     n = ws.ws_face_samples(s.ctx, U, stride, nmax, feats, labels)
@@ -119,8 +155,7 @@ def test_face_samples_match_oracle():
     Uf = oracle.fill_ghosts(oracle.Grid(2, case.n, case.dx, case.bc), Uo)
     Q = oracle.cons_to_prim(2, Uf)
     nx, ny = case.n[0], case.n[1]
-    agree = 0
-    checked = 0
+    decided = 0
     out = 0
     for d in range(2):
         fe = [nx + (d == 0), ny + (d == 1)]
@@ -139,14 +174,15 @@ def test_face_samples_match_oracle():
             perm = [0, 1 + d, 2 - d, 3, 4, 5]
             qc = cells[:, perm]
             cc = np.array([oracle.sound_speed(q[0], q[3], q[4], q[5]) for q in qc])
-            feat, lab, cond = oracle_face_features(qc, cc)
+            feat, lab, cond, robust = oracle_face_features(qc, cc)
             # features of stencils flat to < 1e-3 of their magnitude carry FP32 noise
             np.testing.assert_allclose(F[out][cond], feat[cond], atol=2e-3)
-            agree += int(Lb[out] == lab)
-            checked += 1
+            if robust:
+                assert Lb[out] == lab, (d, f)
+                decided += 1
             out += 1
     assert out == n
-    assert agree >= 0.97 * checked
+    assert decided >= least * n, (decided, n)
 
 
 def _shock_bubble_state(n):
@@ -158,10 +194,33 @@ def _shock_bubble_state(n):
     return case, s, U
 
 
-def test_tensor_core_gate_matches_fp32_mlp():
+def bf16(a):
+    """Round to the nearest BF16 value (ties to even), as FP64."""
+    b = np.asarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    r = ((b + 0x7FFF + ((b >> 16) & 1)) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def bf16_logits(p, X):
+    """The MLP oracle's forward pass with the roundings of the tensor-core
+    gate: BF16 features, weights and hidden activations, exact products,
+    biases in FP32 (accumulation in FP64 here, FP32 on the GPU)."""
+    w = mo.unpack(p)
+    h1 = bf16(np.maximum(bf16(X) @ bf16(w["W1"]).T + w["b1"].astype(np.float32), 0.0))
+    h2 = bf16(np.maximum(h1 @ bf16(w["W2"]).T + w["b2"].astype(np.float32), 0.0))
+    return h2 @ bf16(w["W3"]) + np.float32(w["b3"][0]), h2
+
+
+def test_tensor_core_gate_matches_mlp_oracle():
     """The gate's decisions inside the fused stage kernel (BF16 features and
-    weights on the tensor cores) agree with the FP32 MLP on the same faces,
-    except for faces whose logit lies within BF16 rounding of the threshold."""
+    weights on the tensor cores, FP32 accumulation) against the FP64 MLP oracle
+    on the sampled features of the same faces.  A face is exempt when BF16
+    rounding decides it: the oracle logit and the logit with the kernel's BF16
+    roundings lie on different sides of the threshold, or the rounded logit is
+    within reach of the threshold for a one-step change in the BF16 rounding of
+    its most influential feature (the two feature computations differ in the
+    last FP32 bits) plus FP32 accumulation noise.  Every other face agrees
+    exactly, and they are nearly all the faces."""
     from paper_1707_00592_gb300 import learned
     case, s, U = _shock_bubble_state(96)
     P = torch.tensor(learned.init_params(7), dtype=torch.float32, device="cuda")
@@ -170,17 +229,27 @@ def test_tensor_core_gate_matches_fp32_mlp():
     labels = torch.empty(nf, dtype=torch.uint8, device="cuda")
     n = ws.ws_face_samples(s.ctx, U, 1, nf, feats, labels)
     assert n == nf
-    z = learned.logits(P, feats).cpu().numpy()
-    thr = float(np.median(z))
+    X = feats.cpu().numpy().astype(np.float64)
+    p64 = P.cpu().numpy().astype(np.float64)
+    z, _ = mo.forward(p64, X)
+    # the threshold: the median logit of the faces with non-zero features
+    # (every flat face has the same logit, which must not sit on the threshold)
+    thr = float(np.median(z[np.abs(X).max(axis=1) > 0]))
     ws.ws_set_mlp(s.ctx, P, thr)
     smooth = torch.empty(nf, dtype=torch.uint8, device="cuda")
     ws.ws_gate_eval(s.ctx, U, smooth)
     torch.cuda.synchronize()
     got = smooth.cpu().numpy().astype(bool)
-    expect = z < thr
-    bad = got != expect
-    assert bad.mean() < 0.01
-    assert np.all(np.abs(z[bad] - thr) < 0.05 * (np.abs(z).max() + 1e-30))
+    zb, h2 = bf16_logits(p64, X)
+    w = mo.unpack(p64)
+    influence = np.abs(w["W3"]) @ np.abs(w["W2"]) @ np.abs(w["W1"])  # first-order d z / d x_k bound
+    reach = 2.0 ** -8 * np.max(np.abs(X) * influence[None, :], axis=1)
+    reach += 1e-5 * (np.abs(h2) @ np.abs(bf16(w["W3"])) + abs(w["b3"][0]))
+    decided = (np.sign(z - thr) == np.sign(zb - thr)) & (np.abs(zb - thr) > reach)
+    assert np.array_equal(got[decided], (z < thr)[decided])
+    nonflat = np.abs(X).max(axis=1) > 0
+    assert decided.mean() > 0.95, decided.mean()
+    assert decided[nonflat].mean() > 0.85, decided[nonflat].mean()
     s.close()
 
 

@@ -517,3 +517,96 @@ def test_run_host_unbanded_matches_device_steps(kind):
     s2.close()
     assert np.array_equal(Uh.numpy(), U.cpu().numpy())
     assert np.array_equal(dt_used[:nt], np.atleast_1d(dts))
+
+
+@pytest.mark.parametrize("ndim,n,bc", [(2, (70, 47), "transmissive"), (2, (33, 65), "periodic"),
+                                       (2, (40, 31), "reflective"), (3, (37, 19, 17), "transmissive"),
+                                       (3, (16, 20, 33), "periodic")])
+def test_stage_configs_bit_identical(ndim, n, bc):
+    """Every fused-stage configuration ws_autotune chooses among (tile shape,
+    CTA size, launch mode) gives the same state, dt and MOOD record bit for
+    bit: the per-face arithmetic does not depend on the tile.  ws_autotune
+    then keeps one of them and reports it."""
+    kind = "two_phase"
+    case = wl.random_state(ndim, n, seed=23, kind=kind)
+    bcs = tuple((bc, bc) for _ in range(ndim))
+    stream = torch.cuda.Stream()
+    ref = None
+    s = ws.Solver(ndim, case.n, case.dx, bcs, precision="mixed", stream=stream)
+    cands = list(range(6)) if ndim == 2 else list(range(4))
+    with torch.cuda.stream(stream):
+        U0 = s.prim_to_cons(s.tensor(case.Q))
+        with pytest.raises(ws.WsError):
+            ws.ws_set_stage_config(s.ctx, len(cands))
+        for k in cands:
+            ws.ws_set_stage_config(s.ctx, k)
+            cfg = ws.ws_get_stage_config(s.ctx)
+            assert cfg["index"] == k and cfg["schedule"] == k % 2
+            U = U0.clone()
+            dts = [s.step(U, want_dt=True) for _ in range(3)]
+            _, mask = s.mood(with_mask=True)
+            got = (U.cpu().numpy(), dts, mask.cpu().numpy())
+            if ref is None:
+                ref = got
+            else:
+                assert np.array_equal(got[0], ref[0]), cfg
+                assert got[1] == ref[1], cfg
+                assert np.array_equal(got[2], ref[2]), cfg
+        choice = ws.ws_autotune(s.ctx, U0, 2)
+        assert choice in cands
+        assert ws.ws_get_stage_config(s.ctx)["index"] == choice
+        U = U0.clone()
+        for _ in range(3):
+            s.step(U)
+        assert np.array_equal(U.cpu().numpy(), ref[0])
+    s.close()
+
+
+@pytest.mark.parametrize("n,bc,cfg", [((96, 96), "transmissive", 0), ((70, 47), "periodic", 1),
+                                      ((65, 40), "reflective", 4)])
+def test_resident_steps_bit_identical(n, bc, cfg):
+    """ws_set_resident: the FP32 image of the state carried from one step's
+    stage 2 to the next step's stage 0 gives the same states, time steps and
+    MOOD record, bit for bit, as converting the FP64 state every step; calls
+    in between that touch the state (a census step on another state, a flux
+    divergence) make the next step start over from the FP64 state."""
+    if n == (96, 96):
+        case = wl.shock_bubble_2d(96)
+        bcs = case.bc
+    else:
+        case = wl.random_state(2, n, seed=31, kind="two_phase")
+        bcs = ((bc, bc), (bc, bc))
+    stream = torch.cuda.Stream()
+    out = []
+    with torch.cuda.stream(stream):
+        for resident in (False, True):
+            s = ws.Solver(2, case.n, case.dx, bcs, precision="mixed", stream=stream)
+            ws.ws_set_stage_config(s.ctx, cfg)
+            if resident:
+                ws.ws_set_resident(s.ctx, True)
+            U = s.prim_to_cons(s.tensor(case.Q))
+            rec = []
+            for k in range(12):
+                if k == 5:  # calls on the context between steps
+                    V = U.clone()
+                    s.census_step(V)
+                    s.flux_divergence(U.clone())
+                dt = s.step(U, want_dt=True)
+                _, mask = s.mood(with_mask=True)
+                rec.append((dt, mask.cpu().numpy()))
+            out.append((U.cpu().numpy(), rec))
+            s.close()
+    (a, ra), (b, rb) = out
+    assert np.array_equal(a, b)
+    for (dta, ma), (dtb, mb) in zip(ra, rb):
+        assert dta == dtb
+        assert np.array_equal(ma, mb)
+
+
+def test_resident_needs_fused_2d():
+    case = wl.random_state(3, (12, 10, 14), seed=2, kind="two_phase")
+    s = ws.Solver(3, case.n, case.dx, case.bc, precision="mixed")
+    with pytest.raises(ws.WsError) as ei:
+        ws.ws_set_resident(s.ctx, True)
+    assert ei.value.code == ws.WS_ENOTSUP
+    s.close()
