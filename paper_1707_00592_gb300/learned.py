@@ -37,10 +37,13 @@ def _collect(solver, U, stride, budget, feats_out, labels_out):
     return n
 
 
-def sample_faces(total: int = 4_000_000, seed: int = 0, sizes=(400, 384, 48), steps=(150, 400, 40),
-                 snapshots: int = 8, share=(0.1, 0.7, 0.2)):
-    """Labelled faces from plain mixed-precision runs of the three workloads.
-    Returns (feats [n, 24] FP32 CUDA tensor, labels [n] uint8 CUDA tensor)."""
+def sample_faces(total: int = 10_000_000, seed: int = 0, sizes=(200, 1024, 96), steps=(255, 2000, 100),
+                 snapshots: int = 8, share=(0.02, 0.68, 0.3)):
+    """Labelled faces from plain mixed-precision runs of the three workloads
+    (the gas-water tube, the shock-bubble and the water drop at the given
+    sizes, each over its run of `steps` steps, sampled at `snapshots` evenly
+    spaced states).  Returns (feats [n, 24] FP32 CUDA tensor, labels [n] uint8
+    CUDA tensor)."""
     import torch
     cases = [wl.gas_water_tube(sizes[0]), wl.shock_bubble_2d(sizes[1]), wl.drop_3d(sizes[2], seed=seed)]
     feats = torch.empty((total, MLP_NIN), dtype=torch.float32, device="cuda")
@@ -117,7 +120,7 @@ def choose_threshold(P, feats, labels, recall: float = 0.999) -> float:
     return float(thr)
 
 
-def train_gate(total: int = 4_000_000, epochs: int = 4, recall: float = 0.999, seed: int = 0, log=None):
+def train_gate(total: int = 10_000_000, epochs: int = 4, recall: float = 0.999, seed: int = 0, log=None):
     """Sample, train, and pick the threshold.  Returns (params CUDA tensor,
     threshold, report dict)."""
     import torch

@@ -1,7 +1,8 @@
 """The bench's flop bookkeeping: the per-face count of the method (setup,
 projection, WENO-IS on every variable and side, back-projection, MOOD test,
-HLLC) and the count the fused kernel executes when flat stencils take the
-linear weights (13 flops a side instead of WENO-IS's 100)."""
+HLLC; counted by the op-counting build of the oracle, tests/test_flop_count.py)
+and the count the fused kernel executes when flat stencils take the linear
+weights (13 flops a side instead of WENO-IS's 99)."""
 import os
 import sys
 
@@ -12,9 +13,9 @@ import bench  # noqa: E402
 
 
 def test_method_counts_per_face():
-    assert bench.face_flops(1) == 12 + 48 + 200 * 5 + 16 + 6 + 114 + 55
-    assert bench.face_flops(2) == 1470
-    assert bench.face_flops(3) == 1689
+    assert [bench.face_flops(d) for d in (1, 2, 3)] == [1251, 1469, 1687]
+    # one RK stage of the 1024^2 grid: 2 x 1024 x 1025 faces, 1024^2 cells
+    assert bench.stage_flops(2, (1024, 1024)) == 2 * 1024 * 1025 * 1469 + 1024 * 1024 * (16 + 46)
 
 
 @pytest.mark.parametrize("ndim", [1, 2, 3])
@@ -22,8 +23,8 @@ def test_executed_counts(ndim):
     nq = ndim + 4
     full = bench.face_flops(ndim)
     assert bench.executed_face_flops(ndim, 0.0) == full
-    # every variable flat: WENO-IS (100 a side) replaced by the linear weights (13)
-    assert bench.executed_face_flops(ndim, 1.0) == full - 2 * nq * 87
+    # every variable flat: WENO-IS (99 a side) replaced by the linear weights (13)
+    assert bench.executed_face_flops(ndim, 1.0) == full - 2 * nq * 86
     a, b = bench.executed_face_flops(ndim, 0.3), bench.executed_face_flops(ndim, 0.7)
     assert full > a > b > bench.executed_face_flops(ndim, 1.0)
 
