@@ -107,11 +107,14 @@ def cell_update_bytes(ndim: int) -> int:
 
 
 # DRAM bytes moved by one launch of the fused 2D mixed stage on the 1024^2
-# shock-bubble at mid-run (ncu, 50.72 MB read + 2.37 MB written; the stage's
-# FP32 scratch mostly stays in the 129 MB L2 between launches)
-STAGE2D_DRAM_BYTES = 53.09e6
-STAGE2D_DRAM_SOURCE = ("dram__bytes_read.sum + dram__bytes_write.sum of one fused-stage launch "
-                       "(1024^2, step ~300, stage 1), bytes per launch")
+# shock-bubble (ncu, one resident step at step 10 of a 60-step run): stage 0
+# reads the carried FP32 image (25.40 MB read, 0.02 MB written), stage 1 the
+# image and K0 (50.72 + 0.34 MB), stage 2 also the FP64 state it updates
+# (101.43 + 24.63 MB; the rest of its writes are still in L2 at the end); the
+# mean over the three launches
+STAGE2D_DRAM_BYTES = (25.417728 + 51.052288 + 126.05568) / 3 * 1e6
+STAGE2D_DRAM_SOURCE = ("dram__bytes_read.sum + dram__bytes_write.sum per fused-stage launch, mean of the three "
+                       "stages of one resident step (1024^2, step 10 of 60; ncu)")
 
 
 def load_peaks():
@@ -297,6 +300,21 @@ def time_fp64(ws, case, stream, steps):
     return {"value": case.cells * steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps, "steps": steps}
 
 
+def inadmissible_tubes(off, U):
+    """{tube: number of interior cells with rho <= 0, Gamma <= 0 or p + P_inf
+    <= 0 (or not finite)} of a host copy of the tubes' conservative state."""
+    rho, mu, E, G, P = U
+    with np.errstate(all="ignore"):
+        pe = E - 0.5 * mu * mu / rho - P  # Gamma p
+        ok = (rho > 0) & (G > 0) & ((G + 1.0) * pe / G + P > 0) & np.isfinite(pe)
+    out = {}
+    for t in range(len(off) - 1):
+        k = int(np.count_nonzero(~ok[off[t] + 3:off[t + 1] - 3]))
+        if k:
+            out[t] = k
+    return out
+
+
 def time_tubes(ws, stream, steps, seed=0, run_steps=1000, sample=64):
     """The batched configuration: 4096 independent 1D Riemann tubes of 256..8192
     cells (log-uniform) in one persistent launch per RK stage, mixed precision,
@@ -340,21 +358,36 @@ def time_tubes(ws, stream, steps, seed=0, run_steps=1000, sample=64):
         Um = U.cpu().numpy()
     s.close()
     del U, flush
+    bad_tubes = inadmissible_tubes(off, Um)
+
+    def fp64_alone(pick):
+        """The FP64 path on the picked tubes alone, run_steps per-tube CFL steps."""
+        lens = np.array([off[t + 1] - off[t] for t in pick])
+        soff = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+        Qs = np.concatenate([Q[:, off[t]:off[t + 1]] for t in pick], axis=1)
+        s64 = ws.Solver(1, (1,), (1.0,), tube_offsets=soff, precision="fp64", stream=stream)
+        with torch.cuda.stream(stream):
+            U64 = s64.prim_to_cons(s64.tensor(Qs))
+            ws.ws_set_graph(s64.ctx, True)
+            for _ in range(run_steps):
+                s64.step(U64)
+            bad64 = s64.nonphysical()
+            U64 = U64.cpu().numpy()
+        s64.close()
+        return U64, soff, lens, bad64
+
+    # the tubes the mixed run left with an inadmissible cell, run again alone
+    # on the FP64 path (bit-identical to the oracle): does the scheme itself
+    # fail on them?
+    same = None
+    if bad_tubes:
+        _, _, _, bad_same = fp64_alone(sorted(bad_tubes))
+        same = {"tubes": len(bad_tubes), "mixed_nonphysical_cells": int(sum(bad_tubes.values())),
+                "fp64_nonphysical_cells": bad_same}
     # the seeded sample, alone, in FP64
     rng = np.random.default_rng(seed + 1)
     pick = np.sort(rng.choice(len(off) - 1, size=sample, replace=False))
-    lens = np.array([off[t + 1] - off[t] for t in pick])
-    soff = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
-    Qs = np.concatenate([Q[:, off[t]:off[t + 1]] for t in pick], axis=1)
-    s64 = ws.Solver(1, (1,), (1.0,), tube_offsets=soff, precision="fp64", stream=stream)
-    with torch.cuda.stream(stream):
-        U64 = s64.prim_to_cons(s64.tensor(Qs))
-        ws.ws_set_graph(s64.ctx, True)
-        for _ in range(run_steps):
-            s64.step(U64)
-        bad64 = s64.nonphysical()
-        U64 = U64.cpu().numpy()
-    s64.close()
+    U64, soff, lens, bad64 = fp64_alone(pick)
     num = den = 0.0
     for k, t in enumerate(pick):
         a = Um[0, off[t] + 3:off[t + 1] - 3]
@@ -363,6 +396,7 @@ def time_tubes(ws, stream, steps, seed=0, run_steps=1000, sample=64):
         den += float(np.abs(b).sum())
     return {"value": cells * steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps, "tubes": 4096,
             "cells": cells, "chunk_config": choice, "graph": True, "nonphysical_cells": bad,
+            "nonphysical_tubes": len(bad_tubes), "nonphysical_tubes_fp64_alone": same,
             "run_steps": run_steps, "timed_steps": f"{steps} spread evenly over the {run_steps}-step run",
             "workload": "4096 Riemann tubes, lengths log-uniform in [256, 8192], per-tube CFL, mixed precision",
             "l1_density_vs_fp64": {"value": num / den, "tubes": int(sample), "cells": int(lens.sum() - 6 * sample),
@@ -432,11 +466,17 @@ def time_drop3d(ws, stream, steps, probe, n=256, run_steps=500, l1_n=128, l1_ste
         del case
         ws.ws_autotune(s.ctx, U, 2)
         stage_cfg = ws.ws_get_stage_config(s.ctx)
+        ws.ws_set_resident(s.ctx, True)  # consecutive steps carry the FP32 image
         for _ in range(warm):
             s.step(U)
         done = warm
         census = {k: 0 for k in ws.CENSUS_KEYS}
         Uc = torch.empty_like(U)
+        # census replays in a context of their own, so that the timed context's
+        # steps follow one another undisturbed
+        sc = ws.Solver(3, (n, n, n), (1.0 / n,) * 3, (("periodic", "periodic"),) * 3, precision="mixed",
+                       stream=stream)
+        ws.ws_set_stage_config(sc.ctx, stage_cfg["index"])
         ms = 0.0
         ws.ws_profile(s.ctx, True)
         for k in range(steps):
@@ -447,7 +487,7 @@ def time_drop3d(ws, stream, steps, probe, n=256, run_steps=500, l1_n=128, l1_ste
             # census of the reconstruction's evaluations on a copy of the state
             # the timed step starts from
             Uc.copy_(U)
-            c = s.census_step(Uc)
+            c = sc.census_step(Uc)
             for key in ws.CENSUS_KEYS:
                 census[key] += c[key]
             ws.ws_profile(s.ctx, True, reset=False)
@@ -461,6 +501,7 @@ def time_drop3d(ws, stream, steps, probe, n=256, run_steps=500, l1_n=128, l1_ste
         face_ms, face_n = ws.ws_profile_read(s.ctx)["face"]
         ws.ws_profile(s.ctx, False)
         del Uc
+        sc.close()
         while done < run_steps:
             s.step(U)
             done += 1

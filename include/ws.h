@@ -309,8 +309,8 @@ WS_API int ws_set_stage_config(ws_ctx *ctx, int index);
 WS_API int ws_get_stage_config(ws_ctx *ctx, int *index, int *tile_x, int *tile_y, int *threads, int *schedule);
 
 /* enable = 1 declares that U, the state of consecutive ws_step calls of this
- * context, changes between them only through those calls.  The fused 2D
- * mixed-precision stages then carry the FP32 image of the state (every field
+ * context, changes between them only through those calls.  The fused 2D and
+ * 3D mixed-precision stages then carry the FP32 image of the state (every field
  * rounded to FP32, E - Pi formed in FP64 first) from one step's last stage to
  * the next step's first: stage 2 writes the image of the new state, and the
  * next step's stage 0 reads it instead of loading and converting the FP64
@@ -322,7 +322,8 @@ WS_API int ws_get_stage_config(ws_ctx *ctx, int *index, int *tile_x, int *tile_y
  * after a change the caller makes to U itself, which this promise rules out.
  * Resident steps are not replayed from a CUDA graph (ws_set_graph).  Allocates
  * two image buffers (nv FP32 fields each) on first use.  enable = 0: off (the
- * default).  WS_ENOTSUP on a context without the fused 2D stages. */
+ * default).  WS_ENOTSUP on a context without the fused stages (FP64, 1D,
+ * batched tubes). */
 WS_API int ws_set_resident(ws_ctx *ctx, int enable);
 
 /* enable != 0: ws_step calls that take the CFL step (dt <= 0) replay one CUDA

@@ -236,7 +236,7 @@ int fused_run3(ws_ctx* c, double* U, double dt, const GateArgs* gate, const int*
   float* u32 = c->Q32;
   bool img_in = false;
   float* img_out = nullptr;
-  if (c->resident && one_scope && g.ndim == 2) {
+  if (c->resident && one_scope) {
     if (c->img_cur >= 0 && c->img_U == U) {
       u32 = c->img[c->img_cur];
       img_in = true;
@@ -255,9 +255,10 @@ int fused_run3(ws_ctx* c, double* U, double dt, const GateArgs* gate, const int*
     const float* Kin = s == 1 ? c->Ka : c->Kb;
     float* Kout = s == 0 ? c->Ka : c->Kb;
     if (g.ndim == 3)
-      launch_stage3d(g, s, U, c->Q32, Kin, Kout, c->Lp, dt, c->opts.cfl, c->lmax, c->dt_dev, mb + c->mask_off[0],
+      launch_stage3d(g, s, U, u32, Kin, Kout, c->Lp, dt, c->opts.cfl, c->lmax, c->dt_dev, mb + c->mask_off[0],
                      mb + c->mask_off[1], mb + c->mask_off[2], (float)c->opts.eps, c->opts.mood, c->opts.weights,
-                     c->nbad, census, c->stage_tile, c->stage_sched == 0, c->stream);
+                     c->nbad, census, c->stage_tile, c->stage_sched == 0, s == 0 && img_in, s == 2 ? img_out : nullptr,
+                     c->stream);
     else
       launch_stage2d(g, s, U, u32, Kin, Kout, dt, c->opts.cfl, c->lmax, c->dt_dev, mb + c->mask_off[0],
                      mb + c->mask_off[1], (float)c->opts.eps, c->opts.mood, c->opts.weights, c->nbad, gate, run_if,
@@ -1147,7 +1148,7 @@ int ws_set_resident(ws_ctx* c, int enable) {
     c->resident = false;
     return WS_OK;
   }
-  if (!(c->fused && c->gd.ndim == 2)) return fail(c, WS_ENOTSUP, "resident state needs the fused 2D stages");
+  if (!c->fused) return fail(c, WS_ENOTSUP, "resident state needs the fused 2D/3D stages");
   for (int k = 0; k < 2; ++k) {
     int rc;
     if (!c->img[k] && (rc = dalloc(c, &c->img[k], (int64_t)c->gd.nv * c->gd.N))) return rc;
@@ -1170,7 +1171,7 @@ int ws_get_stage_config(ws_ctx* c, int* index, int* tile_x, int* tile_y, int* th
   if (index) *index = stage_config_index(c);
   if (tile_x) *tile_x = 32;
   if (tile_y) *tile_y = fused2d_tile_height(c->stage_tile);
-  if (threads) *threads = c->stage_tile == 1 ? 1024 : (c->stage_tile == 2 ? 256 : 512);
+  if (threads) *threads = fused_tile_threads(c->stage_tile);
   if (schedule) *schedule = c->stage_sched;
   return WS_OK;
 }

@@ -162,7 +162,7 @@ struct StageArgs {
                            // MLP runs, read by launches that reuse them
   int row0;                // first tile row of the launch (a launch may cover a band of tile rows)
   int img_in;              // stage 0: U32 already holds the FP32 image of U (carried from the previous step)
-  float* img_out;          // nullable, stage 2: receives the FP32 image of the new state (2D)
+  float* img_out;          // nullable, stage 2 (the pass that ends it): receives the FP32 image of the new state
   unsigned long long* census;  // census launches: [0] face-variables, [1] those with a flat stencil,
                                // [2] warp passes over a variable, [3] those in which a face took WENO-IS
 };
@@ -929,9 +929,9 @@ __global__ void __launch_bounds__(TL::NT, 1024 / TL::NT) k_stage(StageArgs a) { 
           if (m == NQ - 1) uPi = un;
           // the FP32 image of the new state for the next step's stage 0: the
           // values its phase A would form from U (E - Pi in FP64), bit for bit
-          if (MODE == 0 && a.img_out && m != NQ - 3) a.img_out[m * N + gi] = f64_to_f32(un);
+          if (a.img_out && m != NQ - 3) a.img_out[m * N + gi] = f64_to_f32(un);
         }
-        if (MODE == 0 && a.img_out) a.img_out[(NQ - 3) * N + gi] = f64_to_f32(uE - uPi);
+        if (a.img_out) a.img_out[(NQ - 3) * N + gi] = f64_to_f32(uE - uPi);
         // admissibility of the new state (rho > 0, Gamma > 0, (Gamma+1) p + Pi > 0)
         // from its FP32 image: a diagnostic, not part of the update
         auto v = [&](int m) { return CACHE ? S.own.v[m][j][i] : a.U32[m * N + gi]; };
@@ -1152,7 +1152,15 @@ void launch_stage2d(const GridDev& g, int stage, double* U, float* U32, const fl
   }
 }
 
-int fused2d_tile_height(int tile) { return tile == 1 ? TileB::TY : (tile == 2 ? TileC::TY : TileA::TY); }
+int fused2d_tile_height(int tile) {
+  const int ty[3] = {TileA::TY, TileB::TY, TileC::TY};
+  return ty[tile >= 0 && tile < 3 ? tile : 0];
+}
+
+int fused_tile_threads(int tile) {
+  const int nt[3] = {TileA::NT, TileB::NT, TileC::NT};
+  return nt[tile >= 0 && tile < 3 ? tile : 0];
+}
 
 void launch_stage2d_band(const GridDev& g, int stage, double* U, float* U32, const float* Kin, float* Kout,
                          double dt_fixed, double cfl, unsigned long long* lmax, double* dt_out, uint8_t* mask_x,
@@ -1194,10 +1202,12 @@ static void stage3d_passes(const GridDev& g, const StageArgs& a0, uint8_t* mask_
 void launch_stage3d(const GridDev& g, int stage, double* U, float* U32, const float* Kin, float* Kout, float* Lp,
                     double dt_fixed, double cfl, unsigned long long* lmax, double* dt_out, uint8_t* mask_x,
                     uint8_t* mask_y, uint8_t* mask_z, float eps_rel, int mood, int weights, unsigned long long* nbad,
-                    unsigned long long* census, int tile, bool pdl, cudaStream_t s) {
+                    unsigned long long* census, int tile, bool pdl, bool img_in, float* img_out, cudaStream_t s) {
   StageArgs a = stage_args(g, stage, U, U32, Kin, Kout, dt_fixed, cfl, lmax, dt_out, eps_rel, mood, weights, nbad);
   a.Lp = Lp;
   a.census = census;
+  a.img_in = img_in ? 1 : 0;
+  a.img_out = img_out;
   if (tile == 2)
     stage3d_passes<TileC>(g, a, mask_x, mask_y, mask_z, census != nullptr, pdl, s);
   else

@@ -59,7 +59,7 @@ struct ws_ctx {
   int stage_tile = 0;           // fused: tile shape of the stage launches (ws_autotune)
   int stage_sched = 0;          // fused: 0 stage launches with programmatic dependent launch, 1 plain
                                 // stage launches (ws_autotune)
-  bool resident = false;        // fused 2D: carry the FP32 image of U between steps (ws_set_resident)
+  bool resident = false;        // fused 2D/3D: carry the FP32 image of U between steps (ws_set_resident)
   float* img[2] = {nullptr, nullptr};  // the two image buffers (one read by a step, one written)
   int img_cur = -1;             // image valid for the next step on img_U, or -1
   const double* img_U = nullptr;
@@ -165,6 +165,7 @@ int64_t fused2d_gate_flag_bytes(const GridDev& g);
 int fused_num_tiles(int ndim);
 int fused_tile_index(int ndim, int k);
 int fused2d_tile_height(int tile);
+int fused_tile_threads(int tile);
 
 void launch_stage2d_band(const GridDev& g, int stage, double* U, float* U32, const float* Kin, float* Kout,
                          double dt_fixed, double cfl, unsigned long long* lmax, double* dt_out, uint8_t* mask_x,
@@ -187,7 +188,7 @@ cudaError_t fused3d_prepare();
 void launch_stage3d(const GridDev& g, int stage, double* U, float* U32, const float* Kin, float* Kout, float* Lp,
                     double dt_fixed, double cfl, unsigned long long* lmax, double* dt_out, uint8_t* mask_x,
                     uint8_t* mask_y, uint8_t* mask_z, float eps_rel, int mood, int weights, unsigned long long* nbad,
-                    unsigned long long* census, int tile, bool pdl, cudaStream_t s);
+                    unsigned long long* census, int tile, bool pdl, bool img_in, float* img_out, cudaStream_t s);
 void launch_gate_decide(const float* lstat, unsigned long long* nbad, unsigned long long* lmax, int flags, int* redo,
                         double* stats, int* drift_dev, cudaGraphConditionalHandle cond, cudaStream_t s);
 void launch_restore(const int* redo, const double* src, double* dst, int64_t n, cudaStream_t s);

@@ -319,10 +319,14 @@ def riemann_tubes(ntubes: int = 4096, lmin: int = 256, lmax: int = 8192, seed: i
     """Independent 1D Riemann tubes: lengths log-uniform in [lmin, lmax]; each side
     rho log-uniform in [1, 1000], p log-uniform in [1e5, 1e9], u uniform in
     [-100, 100], air or water with equal odds; interface at the tube's midpoint.
-    A pair whose two rarefactions would open a vacuum (velocity spread above half
-    the sum of 2 c/(gamma-1) over both sides, with c from p + P_inf) has its
-    velocities redrawn.  Returns (offsets, Q) with tube t on padded cells
-    [offsets[t], offsets[t+1]) of every field (3 ghosts each end)."""
+    A pair whose two rarefactions would come near a vacuum has its velocities
+    redrawn: the velocity spread u_R - u_L must stay below half the sum of the
+    two sides' rarefaction velocity gains down to the floor pressure p_f, the
+    lowest pressure both materials admit (max(-P_inf,L, -P_inf,R): 0 when
+    either side is air).  A side's gain is the isentropic rarefaction velocity
+    2 c/(gamma-1) [1 - ((p_f + P_inf)/(p + P_inf))^((gamma-1)/(2 gamma))] with
+    c^2 = gamma (p + P_inf)/rho.  Returns (offsets, Q) with tube t on padded
+    cells [offsets[t], offsets[t+1]) of every field (3 ghosts each end)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     lens = np.exp(rng.uniform(math.log(lmin), math.log(lmax), size=ntubes))
     lens = np.clip(np.rint(lens).astype(np.int64), lmin, lmax)
@@ -338,13 +342,14 @@ def riemann_tubes(ntubes: int = 4096, lmin: int = 256, lmax: int = 8192, seed: i
             p = math.exp(rng.uniform(math.log(1.0e5), math.log(1.0e9)))
             m = mats[int(rng.integers(0, 2))]
             side.append([rho, 0.0, p, m])
+        p_floor = max(-side[0][3][1], -side[1][3][1])
+        cap = 0.0
+        for s in side:
+            g, pinf = s[3]
+            c = math.sqrt(g * (s[2] + pinf) / s[0])
+            cap += 2.0 * c / (g - 1.0) * (1.0 - ((p_floor + pinf) / (s[2] + pinf)) ** ((g - 1.0) / (2.0 * g)))
         while True:
             uL, uR = rng.uniform(-100.0, 100.0, size=2)
-            cap = 0.0
-            for s in side:
-                g, pinf = s[3]
-                c = math.sqrt(g * (s[2] + pinf) / s[0])
-                cap += 2.0 * c / (g - 1.0)
             if uR - uL < 0.5 * cap:
                 break
         side[0][1], side[1][1] = uL, uR

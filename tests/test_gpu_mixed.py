@@ -603,10 +603,31 @@ def test_resident_steps_bit_identical(n, bc, cfg):
         assert np.array_equal(ma, mb)
 
 
-def test_resident_needs_fused_2d():
-    case = wl.random_state(3, (12, 10, 14), seed=2, kind="two_phase")
-    s = ws.Solver(3, case.n, case.dx, case.bc, precision="mixed")
-    with pytest.raises(ws.WsError) as ei:
-        ws.ws_set_resident(s.ctx, True)
-    assert ei.value.code == ws.WS_ENOTSUP
-    s.close()
+@pytest.mark.parametrize("n,bc,cfg", [((37, 19, 17), "transmissive", 1), ((16, 20, 33), "periodic", 2)])
+def test_resident_steps_bit_identical_3d(n, bc, cfg):
+    """The carried image in 3D: written by the second pass of stage 2, read by
+    both passes of the next stage 0; bit-identical to ordinary steps."""
+    case = wl.random_state(3, n, seed=32, kind="two_phase")
+    bcs = tuple((bc, bc) for _ in range(3))
+    out = []
+    for resident in (False, True):
+        s = ws.Solver(3, case.n, case.dx, bcs, precision="mixed")
+        ws.ws_set_stage_config(s.ctx, cfg)
+        if resident:
+            ws.ws_set_resident(s.ctx, True)
+        U = s.prim_to_cons(s.tensor(case.Q))
+        dts = [s.step(U, want_dt=True) for _ in range(6)]
+        out.append((U.cpu().numpy(), dts))
+        s.close()
+    assert np.array_equal(out[0][0], out[1][0])
+    assert out[0][1] == out[1][1]
+
+
+def test_resident_needs_fused_stages():
+    for prec, ndim, n in (("fp64", 2, (20, 20)), ("mixed", 1, (40,))):
+        case = wl.random_state(ndim, n, seed=2, kind="two_phase")
+        s = ws.Solver(ndim, case.n, case.dx, case.bc, precision=prec)
+        with pytest.raises(ws.WsError) as ei:
+            ws.ws_set_resident(s.ctx, True)
+        assert ei.value.code == ws.WS_ENOTSUP
+        s.close()

@@ -137,6 +137,29 @@ def test_shock_bubble_2d_small_bitwise():
         assert same(mask[2], flat_masks(mo[2]))
 
 
+def test_shock_bubble_2d_long_trajectory_bitwise():
+    """The 128^2 shock-bubble over 300 CFL steps, in which the shock crosses
+    the bubble: the FP64 path stays bit for bit on the oracle's trajectory --
+    every step's dt, and every 50 steps the state and that step's MOOD
+    record."""
+    case = wl.shock_bubble_2d(128)
+    s = solver_for(case)
+    g = ogrid(case)
+    Uo = oracle.prim_to_cons(2, case.Q)
+    U = s.tensor(Uo)
+    sl = wl.interior(2, case.n)
+    for k in range(1, 301):
+        dt = s.step(U, want_dt=True)
+        Uo, dto, mo = oracle.step(g, Uo, with_mask=(k % 50 == 0))
+        assert dt == dto, k
+        if k % 50 == 0:
+            assert same(U.cpu().numpy()[sl], Uo[sl]), k
+            _, mask = s.mood(with_mask=True)
+            mask = mask.cpu().numpy().reshape(3, -1)
+            for st in range(3):
+                assert same(mask[st], flat_masks(mo[st])), k
+
+
 def test_drop_3d_small_bitwise():
     """Down-sized 3D periodic drop with density noise (20^3): 3 steps."""
     case = wl.drop_3d(20, seed=0)

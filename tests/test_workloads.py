@@ -62,3 +62,25 @@ def test_shock_droplet_states_and_geometry():
     frac = Q[5] / Pw
     assert frac.sum() * 1e-8 == pytest.approx(math.pi * 0.004 ** 2, rel=1e-2)
     assert Q[0].max() == pytest.approx(1000.0)
+
+
+def test_riemann_tubes_keep_clear_of_vacuum():
+    """Every tube of the batched configuration (seed 0) has a star state of the
+    exact stiffened-gas Riemann solution with both sides' p* + P_inf > 0, and
+    its velocity spread stays below half of what would open a vacuum at the
+    floor pressure (the exact solver's own wave functions at that pressure)."""
+    from oracle import exact_riemann as er
+    off, Q = wl.riemann_tubes(ntubes=4096, lmin=256, lmax=8192, seed=0)
+    for t in range(len(off) - 1):
+        a, b = off[t] + wl.NG, off[t + 1] - wl.NG - 1
+        sides = []
+        for i in (a, b):
+            rho, u, p, G, P = Q[:, i]
+            gamma = 1.0 + 1.0 / G
+            sides.append(er.Side(rho, u, p, gamma, P / (G + 1.0)))
+        L, R = sides
+        floor = max(-L.pinf, -R.pinf)
+        gain = -(er._f(floor, L)[0] + er._f(floor, R)[0])
+        assert R.u - L.u < 0.5 * gain, t
+        ps, _ = er.star_state(L, R)
+        assert ps > floor, t
