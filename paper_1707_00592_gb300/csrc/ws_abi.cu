@@ -1,5 +1,6 @@
 // Host side of the C ABI declared in include/ws.h: validation, scratch
 // ownership and the stream-ordered launch sequence of an SSP-RK3 step.
+#include <algorithm>
 #include <optional>
 #include <cuda_runtime.h>
 #include <stdarg.h>
@@ -36,6 +37,25 @@ int check_launch(ws_ctx* c, const char* what) {
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(c, WS_ECUDA, "%s launch failed: %s", what, cudaGetErrorString(e));
   return WS_OK;
+}
+
+// fused 2D: TMA descriptors of the FP32 buffers for the current tile shape
+void encode_maps(ws_ctx* c) {
+  c->tmap_ok = 0;
+  if (!c->fused || c->gd.ndim != 2) return;
+  const float* bufs[5] = {c->Ka, c->Kb, c->Q32, c->img[0], c->img[1]};
+  for (int k = 0; k < 5; ++k)
+    if (bufs[k] && fused2d_encode_map(c->gd, c->stage_tile, bufs[k], &c->tmap[k])) c->tmap_ok |= 1u << k;
+}
+
+// the descriptors of a launch's K and image buffers, or null (then every tile
+// loads cell by cell)
+const CUtensorMap* map_of(const ws_ctx* c, const float* buf) {
+  if (!c->stage_tma) return nullptr;
+  const float* bufs[5] = {c->Ka, c->Kb, c->Q32, c->img[0], c->img[1]};
+  for (int k = 0; k < 5; ++k)
+    if (buf && bufs[k] == buf) return (c->tmap_ok >> k & 1u) ? &c->tmap[k] : nullptr;
+  return nullptr;
 }
 
 template <typename T>
@@ -259,11 +279,14 @@ int fused_run3(ws_ctx* c, double* U, double dt, const GateArgs* gate, const int*
                      mb + c->mask_off[1], mb + c->mask_off[2], (float)c->opts.eps, c->opts.mood, c->opts.weights,
                      c->nbad, census, c->stage_tile, c->stage_sched == 0, s == 0 && img_in, s == 2 ? img_out : nullptr,
                      c->stream);
-    else
+    else {
+      const CUtensorMap *tmk = map_of(c, Kin), *tmv = map_of(c, u32);
+      if (!tmk || !tmv) tmk = tmv = nullptr;
       launch_stage2d(g, s, U, u32, Kin, Kout, dt, c->opts.cfl, c->lmax, c->dt_dev, mb + c->mask_off[0],
                      mb + c->mask_off[1], (float)c->opts.eps, c->opts.mood, c->opts.weights, c->nbad, gate, run_if,
-                     census, c->stage_tile, c->stage_sched == 0, s == 0 && img_in, s == 2 ? img_out : nullptr,
-                     c->stream);
+                     census, c->stage_tile, c->stage_sched == 0, s == 0 && img_in, s == 2 ? img_out : nullptr, tmk,
+                     tmv, c->stream);
+    }
   }
   return check_launch(c, "fused stage");
 }
@@ -418,6 +441,8 @@ int ws_init(const ws_grid* grid, const ws_opts* opts, void* stream, ws_ctx** out
     g.st[1] = g.P[0];
     g.st[2] = g.P[0] * g.P[1];
     g.N = g.P[0] * g.P[1] * g.P[2];
+    for (int d = 0; d < 3; ++d) g.st32[d] = g.st[d];
+    g.N32 = g.N;
     g.ncell = (int64_t)g.n[0] * g.n[1] * g.n[2];
     int64_t off = 0;
     for (int d = 0; d < 3; ++d) {
@@ -432,9 +457,15 @@ int ws_init(const ws_grid* grid, const ws_opts* opts, void* stream, ws_ctx** out
         (rc = dalloc(c, &c->dt_dev, 1)) || (rc = dalloc(c, &c->lmax, 1)) || (rc = dalloc(c, &c->nbad, 1)))
       goto bad;
     if (op.precision == WS_PREC_MIXED) {
-      if ((rc = dalloc(c, &c->Q32, (int64_t)(g.nv + 1) * g.N))) goto bad;
-      if (gr.ndim == 2 && !getenv("WS_NO_FUSED")) {
-        if ((rc = dalloc(c, &c->Ka, (int64_t)g.nv * g.N)) || (rc = dalloc(c, &c->Kb, (int64_t)g.nv * g.N)) ||
+      const bool fused2d = gr.ndim == 2 && !getenv("WS_NO_FUSED");
+      if (fused2d) {  // FP32 rows padded to a multiple of four floats (TMA boxes)
+        g.st32[1] = (g.P[0] + 3) / 4 * 4;
+        g.st32[2] = g.st32[1] * g.P[1];
+        g.N32 = g.st32[2];
+      }
+      if ((rc = dalloc(c, &c->Q32, std::max((int64_t)(g.nv + 1) * g.N, (int64_t)g.nv * g.N32)))) goto bad;
+      if (fused2d) {
+        if ((rc = dalloc(c, &c->Ka, (int64_t)g.nv * g.N32)) || (rc = dalloc(c, &c->Kb, (int64_t)g.nv * g.N32)) ||
             (rc = dalloc(c, &c->census, 4)))
           goto bad;
         if (fused2d_prepare() != cudaSuccess) {
@@ -442,6 +473,8 @@ int ws_init(const ws_grid* grid, const ws_opts* opts, void* stream, ws_ctx** out
           goto bad;
         }
         c->fused = true;
+        encode_maps(c);
+        c->stage_tma = c->tmap_ok == 0x7u ? 1 : 0;
       }
       if (gr.ndim == 3 && !getenv("WS_NO_FUSED")) {
         if ((rc = dalloc(c, &c->Ka, (int64_t)g.nv * g.N)) || (rc = dalloc(c, &c->Kb, (int64_t)g.nv * g.N)) ||
@@ -487,6 +520,9 @@ int ws_init(const ws_grid* grid, const ws_opts* opts, void* stream, ws_ctx** out
     g.n[0] = 1;  // unused in tube mode
     g.n[1] = g.n[2] = 1;
     g.N = total;
+    g.N32 = total;
+    g.st32[0] = 1;
+    g.st32[1] = g.st32[2] = total;
     g.nv = 5;
     c->nstate = 5 * total;
     c->nmask = total;  // one byte per padded cell: face i+1/2 stored at cell i (faces -1/2 .. len-1/2)
@@ -802,9 +838,11 @@ int run_host_banded(ws_ctx* c, double* U_host, int nsteps, double dt, double* dt
     uint8_t* mb = c->mask + (int64_t)st * c->nmask;
     const float* Kin = st == 1 ? c->Ka : c->Kb;
     float* Kout = st == 0 ? c->Ka : c->Kb;
+    const CUtensorMap *tmk = map_of(c, Kin), *tmv = map_of(c, c->Q32);
+    if (!tmk || !tmv) tmk = tmv = nullptr;
     launch_stage2d_band(g, st, c->Uhost_dev, c->Q32, Kin, Kout, dt, c->opts.cfl, c->lmax, c->dt_dev,
                         mb + c->mask_off[0], mb + c->mask_off[1], (float)c->opts.eps, c->opts.mood, c->opts.weights,
-                        c->nbad, r0, nr, c->stage_tile, c->stream);
+                        c->nbad, r0, nr, c->stage_tile, tmk, tmv, c->stream);
   };
   // the copy streams start after the work already queued on the context's stream
   CK(c, cudaEventRecord(ev_start, c->stream));
@@ -1015,7 +1053,7 @@ int ws_gate_eval(ws_ctx* c, double* U, uint8_t* smooth) {
   c->img_cur = -1;
   launch_stage2d(c->gd, 3, U, c->Q32, c->Ka, c->Kb, 0.0, c->opts.cfl, c->lmax, c->dt_dev, smooth,
                  smooth + c->mask_off[1], (float)c->opts.eps, c->opts.mood, c->opts.weights, c->nbad, &ga, nullptr,
-                 nullptr, 0, false, false, nullptr, c->stream);
+                 nullptr, 0, false, false, nullptr, nullptr, nullptr, c->stream);
   return check_launch(c, "gate eval");
 }
 
@@ -1030,14 +1068,23 @@ int ws_gate_stats(ws_ctx* c, double out[6]) {
 
 // Fused stage configurations: index = 2 x tile slot + schedule (0 stage
 // launches with programmatic dependent launch, 1 plain stage launches).
+// Stage configurations: index = (2 x tile + loads) x 2 + schedule in 2D
+// (loads: 0 cell by cell, 1 TMA boxes for interior tiles), 2 x tile +
+// schedule in 3D.
+static int stage_load_modes(const ws_ctx* c) { return c->gd.ndim == 2 ? 2 : 1; }
+
 static bool stage_config_valid(const ws_ctx* c, int index) {
-  return index >= 0 && index < 2 * fused_num_tiles(c->gd.ndim);
+  return index >= 0 && index < 2 * stage_load_modes(c) * fused_num_tiles(c->gd.ndim);
 }
 
 static void set_stage_config(ws_ctx* c, int index) {
   c->img_cur = -1;
-  c->stage_tile = fused_tile_index(c->gd.ndim, index / 2);
+  const int nl = stage_load_modes(c);
+  c->stage_tile = fused_tile_index(c->gd.ndim, index / (2 * nl));
+  c->stage_tma = nl == 2 ? (index / 2) % 2 : 0;
   c->stage_sched = index % 2;
+  encode_maps(c);
+  if (c->stage_tma && (c->tmap_ok & 0x7u) != 0x7u) c->stage_tma = 0;  // the driver refused a descriptor
   if (c->graph_exec) {
     cudaGraphExecDestroy(c->graph_exec);
     c->graph_exec = nullptr;
@@ -1048,7 +1095,8 @@ static int stage_config_index(const ws_ctx* c) {
   int k = 0;
   for (int j = 0; j < fused_num_tiles(c->gd.ndim); ++j)
     if (fused_tile_index(c->gd.ndim, j) == c->stage_tile) k = j;
-  return 2 * k + c->stage_sched;
+  const int nl = stage_load_modes(c);
+  return (nl * k + (nl == 2 ? c->stage_tma : 0)) * 2 + c->stage_sched;
 }
 
 // The fused 2D/3D stages: every configuration steps a scratch copy of U for
@@ -1065,7 +1113,7 @@ static int autotune_fused(ws_ctx* c, const double* U, int steps, int* choice) {
   const int keep = stage_config_index(c);
   const bool prof = c->prof_on;
   c->prof_on = false;
-  for (int k = 0; k < 2 * fused_num_tiles(c->gd.ndim) && rc == WS_OK; ++k) {
+  for (int k = 0; stage_config_valid(c, k) && rc == WS_OK; ++k) {
     set_stage_config(c, k);
     cudaMemcpyAsync(Ut, U, sizeof(double) * c->nstate, cudaMemcpyDeviceToDevice, c->stream);
     if ((rc = step_device(c, Ut, 0.0))) break;  // warm-up
@@ -1151,8 +1199,9 @@ int ws_set_resident(ws_ctx* c, int enable) {
   if (!c->fused) return fail(c, WS_ENOTSUP, "resident state needs the fused 2D/3D stages");
   for (int k = 0; k < 2; ++k) {
     int rc;
-    if (!c->img[k] && (rc = dalloc(c, &c->img[k], (int64_t)c->gd.nv * c->gd.N))) return rc;
+    if (!c->img[k] && (rc = dalloc(c, &c->img[k], (int64_t)c->gd.nv * c->gd.N32))) return rc;
   }
+  encode_maps(c);
   c->resident = true;
   return WS_OK;
 }
@@ -1165,7 +1214,7 @@ int ws_set_stage_config(ws_ctx* c, int index) {
   return WS_OK;
 }
 
-int ws_get_stage_config(ws_ctx* c, int* index, int* tile_x, int* tile_y, int* threads, int* schedule) {
+int ws_get_stage_config(ws_ctx* c, int* index, int* tile_x, int* tile_y, int* threads, int* schedule, int* tma) {
   if (!c) return fail(c, WS_EINVAL, "null context");
   if (!c->fused) return fail(c, WS_EINVAL, "the context has no fused stage (2D/3D mixed precision)");
   if (index) *index = stage_config_index(c);
@@ -1173,6 +1222,7 @@ int ws_get_stage_config(ws_ctx* c, int* index, int* tile_x, int* tile_y, int* th
   if (tile_y) *tile_y = fused2d_tile_height(c->stage_tile);
   if (threads) *threads = fused_tile_threads(c->stage_tile);
   if (schedule) *schedule = c->stage_sched;
+  if (tma) *tma = c->stage_tma;
   return WS_OK;
 }
 

@@ -44,6 +44,18 @@
 // the FP32 increments K; stage 2 adds its increment to U in FP64, in place,
 // since no tile reads U's FP64 values after stage 0.  K0 and K1 live in
 // separate buffers because neighbouring tiles read K in their halos.
+//
+// The FP32 buffers (image, K) have a layout of their own (GridDev st32, N32):
+// in 2D their rows are padded to a multiple of four floats, so that the halo
+// of every tile starts on a 16-byte boundary (padded column x0 - 3 + 3 = x0,
+// a multiple of 32).  A 2D tile whose halo lies inside the grid then loads
+// the image and K of tile and halo as two TMA boxes (cp.async.bulk.tensor,
+// completion on an mbarrier) straight into shared memory, with no per-cell
+// address arithmetic; tiles on the boundary, the FP64 loads of a first
+// stage 0 and the 3D passes load cell by cell and apply the boundary
+// conditions while loading.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <cuda_bf16.h>
@@ -65,6 +77,7 @@ template <int TX_, int TY_, int NT_>
 struct Tile {
   static constexpr int TX = TX_, TY = TY_, NT = NT_;
   static constexpr int HX = TX + 2 * NG, HY = TY + 2 * NG;
+  static constexpr int HXP = (HX + 7) / 8 * 8;  // row pitch of the halo tile in shared memory (a TMA box row)
   static constexpr int NFX = (TX + 1) * TY, NFY = TX * (TY + 1), NF = NFX + NFY;
   static constexpr int NMT = (NF + 15) / 16;  // 16-face M tiles of the gate's MLP
 };
@@ -83,9 +96,10 @@ struct Tr {
   static constexpr int NTG = NQ - 5;                // tangential components at a face
   static constexpr bool XF = MODE != 2;             // the pass has x faces (and an x halo)
   static constexpr int QW = XF ? HX : TX;           // row width of the q tile
+  static constexpr int QP = XF ? TL::HXP : TX;      // row pitch of the q tile
   static constexpr int QX = XF ? NG : 0;            // q column of the tile's first cell
   static constexpr int NH = QW * HY;                // q tile cells
-  static constexpr int FS = NH;                     // field stride in the q tile
+  static constexpr int FS = QP * HY;                // field stride in the q tile
   static constexpr int NFP = (XF ? NFX : 0) + NFY;  // faces of the pass
   static constexpr int HPT = (NH + NT - 1) / NT;    // q tile cells per thread in phase A
   static constexpr int IP = NQ - 3, IG = NQ - 2, IPI = NQ - 1, IC = NQ;  // q fields p, Gamma, Pi, c
@@ -104,21 +118,34 @@ struct Smem {
   using T = Tr<NQ_, MODE, TL>;
   static constexpr int TX = TL::TX, TY = TL::TY, NT = TL::NT, HY = TL::HY, NF = TL::NF;
   static constexpr bool CACHE = GATE != 1 && T::RK;  // own cells staged for phase C
-  float q[NQ_ + 1][HY][T::QW];                // primitives + sound speed of tile and halo
-  float fx[T::XF ? NQ_ + 1 : 1][TY][TX + 1];  // x-face fluxes (global field order) + face velocity
+  // primitives + sound speed of tile and halo; in a TMA load, fields 0..NQ-1
+  // first receive the stage's FP32 image, converted in place
+  alignas(128) float q[NQ_ + 1][HY][T::QP];
+  // x-face fluxes (global field order) + face velocity; in a TMA load, fx and
+  // fy first receive the increments K of tile and halo (read in phase A)
+  alignas(128) float fx[T::XF ? NQ_ + 1 : 1][TY][TX + 1];
   float fy[NQ_ + 1][TY + 1][TX];              // fluxes + face velocity of the faces along the tile's 2nd axis
   union {
     struct {                                     // this tile's own cells, for phase C
       double u[CACHE ? NQ_ : 1][TY][TX];         // stage 2: FP64 state, copied in asynchronously from the start
       float k[CACHE ? NQ_ : 1][TY][TX];          // stages 1, 2: accumulated increments (kept from the phase-A loads)
       float v[CACHE ? NQ_ : 1][TY][TX];          // stage 2: FP32 image of U^n (kept from the phase-A loads)
-      float l[MODE == 2 ? NQ_ : 1][TY][TX];      // 3D second pass: x + y part of the divergence (asynchronous copy)
+      // 3D second pass: x + y part of the divergence (asynchronous copy)
+      float l[MODE == 2 ? NQ_ : 1][MODE == 2 ? TY : 1][MODE == 2 ? TX : 1];
     } own;
     __nv_bfloat16 feat[GATE == 1 ? NF : 1][24];  // gate inputs (read before the reconstruction)
   };
   unsigned long long red[NT / 32];  // per-warp CFL maxima
+  unsigned long long mbar;          // completion of the TMA loads
   float dt;                         // the step, broadcast from thread 0
 };
+
+// Two 2D stage CTAs of the default tile, with the 1 KiB the hardware keeps
+// per CTA, fit the 196 KiB shared-memory carveout of an SM: the next larger
+// carveout would leave the halo loads of boundary tiles 28 KiB of L1 instead
+// of 60 (measured: 10 % slower per-thread loads).
+static_assert(2 * (sizeof(Smem<0, 6, 0, Tile<32, 15, 512>>) + 1024) <= 196 * 1024,
+              "the default 2D stage no longer leaves room for L1");
 
 template <class TL>
 struct SmemGate {
@@ -165,6 +192,12 @@ struct StageArgs {
   float* img_out;          // nullable, stage 2 (the pass that ends it): receives the FP32 image of the new state
   unsigned long long* census;  // census launches: [0] face-variables, [1] those with a flat stencil,
                                // [2] warp passes over a variable, [3] those in which a face took WENO-IS
+  // 2D: TMA descriptors of the stage's K (Kin) and FP32 image (U32) over the
+  // FP32 layout, boxes of one tile's halo (all fields); tma = 0: every tile
+  // loads cell by cell
+  int tma;
+  alignas(64) CUtensorMap tm_k;
+  alignas(64) CUtensorMap tm_v;
 };
 
 // interior index along an axis of n cells for a (possibly out-of-range)
@@ -385,8 +418,8 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
 // each normalised over the stencil (zero for a stencil flat to 1e-6)
 template <int D, class TL>
 __device__ __forceinline__ void gate_features(const float* qb, __nv_bfloat16* out) {
-  constexpr int ST = D == 0 ? 1 : TL::HX;
-  constexpr int FS = TL::HY * TL::HX;
+  constexpr int ST = D == 0 ? 1 : TL::HXP;
+  constexpr int FS = TL::HY * TL::HXP;
   constexpr int UN = D == 0 ? 1 : 2;
   float rho_bar = 0.5f * (qb[2 * ST] + qb[3 * ST]);
   float c_bar = 0.5f * (qb[6 * FS + 2 * ST] + qb[6 * FS + 3 * ST]);
@@ -431,8 +464,42 @@ __device__ __forceinline__ void cp_async8(void* dst, const void* src) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
+// TMA: a tiled 3D box (x, row, field) of an FP32 buffer into shared memory,
+// completing on an mbarrier that expects its bytes
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  unsigned b = (unsigned)__cvta_generic_to_shared(bar);
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(b), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+  unsigned b = (unsigned)__cvta_generic_to_shared(bar);
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(b), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int f,
+                                            unsigned long long* bar) {
+  unsigned d = (unsigned)__cvta_generic_to_shared(dst), b = (unsigned)__cvta_generic_to_shared(bar);
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cta.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];\n" ::"r"(d),
+      "l"(map), "r"(x), "r"(y), "r"(f), "r"(b)
+      : "memory");
+}
+// Waits for phase 0 of the barrier, at most `limit` polls; false if it gave up.
+__device__ __forceinline__ bool mbar_wait0(unsigned long long* bar, unsigned limit) {
+  unsigned b = (unsigned)__cvta_generic_to_shared(bar);
+  for (unsigned k = 0; k < limit; ++k) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(b)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
 template <int GATE, int NQ_, int MODE, class TL>
-__global__ void __launch_bounds__(TL::NT, 1024 / TL::NT) k_stage(StageArgs a) {  // 64 registers
+__global__ void __launch_bounds__(TL::NT, 1024 / TL::NT) k_stage(const __grid_constant__ StageArgs a) {  // 64 registers
   using T = Tr<NQ_, MODE, TL>;
   using SM = Smem<GATE, NQ_, MODE, TL>;
   constexpr int TX = TL::TX, TY = TL::TY, NT = TL::NT, NF = TL::NF, NMT = TL::NMT;
@@ -442,8 +509,13 @@ __global__ void __launch_bounds__(TL::NT, 1024 / TL::NT) k_stage(StageArgs a) { 
   constexpr bool CACHE = SM::CACHE;
   // axes: x, the tile's 2nd axis (y; z in pass 2), the plane axis (z; y in pass 2; none in 2D)
   constexpr int AX1 = MODE == 2 ? 2 : 1, AXP = MODE == 2 ? 1 : 2;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   SM& S = *reinterpret_cast<SM*>(smem_raw);
+  // a TMA load stages K of tile and halo in fx and fy, and the image in q
+  static_assert(MODE != 0 || (sizeof(S.fx) + sizeof(S.fy) >= sizeof(float) * NQ_ * T::HY * T::QP &&
+                              offsetof(SM, fy) == offsetof(SM, fx) + sizeof(S.fx)),
+                "the K box does not fit the flux arrays");
+  static_assert(T::QP * sizeof(float) % 16 == 0, "TMA box rows are multiples of 16 bytes");
   SmemGate<TL>& SG = *reinterpret_cast<SmemGate<TL>*>(smem_raw + sizeof(SM));
   // Launched with programmatic stream serialization (the plain 2D stage), a
   // CTA may become resident while the previous stage is still finishing: it
@@ -461,6 +533,31 @@ __global__ void __launch_bounds__(TL::NT, 1024 / TL::NT) k_stage(StageArgs a) { 
   const int64_t N = g.N, S1 = g.st[AX1];
   const int64_t pbase = (int64_t)(g.G[AXP] + plane) * g.st[AXP] + g.G[0];  // cell (x, a) at pbase + (G1 + a) S1 + x
   const int tid = threadIdx.x;
+  // index in the FP32 buffers (image, K, the 3D partial divergence) of cell
+  // (x, a) of the tile's plane, computed where it is used; in 3D the FP32
+  // layout is the state's own (st32 = st, N32 = N)
+  auto idx32 = [&](int a_, int x_) -> int64_t {
+    if constexpr (MODE != 0)
+      return pbase + (int64_t)(g.G[AX1] + a_) * S1 + x_;
+    else
+      return (int64_t)(g.G[1] + a_) * g.st32[1] + g.G[0] + x_;
+  };
+  const int64_t N32 = MODE != 0 ? N : g.N32;
+  // A 2D tile whose halo lies inside the grid, in a stage that reads the FP32
+  // image (and K), takes both as TMA boxes: no boundary mapping, one
+  // instruction per array.  They are issued first thing and land while the
+  // CTA sets up; the barrier below publishes the mbarrier to all threads.
+  const bool tma = MODE == 0 && a.tma && (a.stage == 1 || a.stage == 2 || (a.stage == 0 && a.img_in)) &&
+                   x0 >= NG && x0 + TX + NG <= nx && y0 >= NG && y0 + TY + NG <= n1;
+  if (tma && tid == 0) {
+    mbar_init(&S.mbar, 1);
+    // boxes of the halo: padded column x0 - NG + NG, padded row y0, all fields
+    constexpr unsigned box = (unsigned)(NQ_ * T::HY * T::QP * sizeof(float));
+    mbar_expect_tx(&S.mbar, a.stage == 0 ? box : 2 * box);
+    tma_load_3d(&S.q[0][0][0], &a.tm_v, x0, y0, 0, &S.mbar);
+    if (a.stage != 0) tma_load_3d(&S.fx[0][0][0], &a.tm_k, x0, y0, 0, &S.mbar);
+  }
+  if (tma && a.stage == 0) __syncthreads();
   if (a.stage == 1 || a.stage == 2) {
     if (tid == 0) {  // one FP64 division per CTA
       double d = a.dt_fixed > 0.0 ? a.dt_fixed : (double)a.cfl / __longlong_as_double((long long)*a.lmax);
@@ -481,9 +578,10 @@ __global__ void __launch_bounds__(TL::NT, 1024 / TL::NT) k_stage(StageArgs a) { 
 #pragma unroll
         for (int m = 0; m < NQ; ++m) cp_async8(&S.own.u[m][j][i], &a.U[m * N + gi]);
       }
-      if (MODE == 2) {
+      if constexpr (MODE == 2) {
+        const int64_t gf = idx32(y0 + j, x0 + i);
 #pragma unroll
-        for (int m = 0; m < NQ; ++m) cp_async4(&S.own.l[m][j][i], &a.Lp[m * N + gi]);
+        for (int m = 0; m < NQ; ++m) cp_async4(&S.own.l[m][j][i], &a.Lp[m * N32 + gf]);
       }
     }
     cp_async_commit();
@@ -504,11 +602,35 @@ __global__ void __launch_bounds__(TL::NT, 1024 / TL::NT) k_stage(StageArgs a) { 
   // ---- phase A: stage-state primitives of tile + halo ----
   // A thread owns up to HPT q-tile cells; all their global loads are issued
   // before any of them is used, so that a CTA has its whole halo in flight.
+  // A TMA tile (above) reads both from shared memory once its boxes land.
   {
     float ld[T::HPT][NQ];
     float rk[T::HPT][NQ], rv[T::HPT][NQ];  // stages 1, 2: increment and FP32 image as loaded
     int hh[T::HPT];
     bool flx[T::HPT], fla[T::HPT], own[T::HPT];
+    if (tma) {
+      // a copy that never lands is reported as an impossible count of
+      // inadmissible cells (the results of the launch are then void)
+      if (!mbar_wait0(&S.mbar, 1u << 24) && (tid & 31) == 0) atomicAdd(a.nbad, 1ULL << 40);
+      const float* kst = &S.fx[0][0][0];  // K of tile and halo, [field][row][column] like q
+#pragma unroll
+      for (int t = 0; t < T::HPT; ++t) {
+        int h = tid + t * NT;
+        int hy = h / T::QW, hx = h - hy * T::QW;
+        hh[t] = h < T::NH ? h : -1;
+        flx[t] = fla[t] = false;
+        own[t] = hx >= T::QX && hx < T::QX + TX && hy >= NG && hy < NG + TY;
+        if (h >= T::NH) continue;
+#pragma unroll
+        for (int m = 0; m < NQ; ++m) {
+          rv[t][m] = S.q[m][hy][hx];
+          if (a.stage == 0)
+            ld[t][m] = rv[t][m];
+          else
+            rk[t][m] = kst[(m * T::HY + hy) * T::QP + hx];
+        }
+      }
+    } else {
 #pragma unroll
     for (int t = 0; t < T::HPT; ++t) {
       int h = tid + t * NT;
@@ -524,12 +646,13 @@ __global__ void __launch_bounds__(TL::NT, 1024 / TL::NT) k_stage(StageArgs a) { 
       int ma = map_bc(ga, n1, g.bc[AX1][0], g.bc[AX1][1], fa);
       flx[t] = fx;
       fla[t] = fa;
-      int64_t i = pbase + (int64_t)(g.G[AX1] + ma) * S1 + mx;
       own[t] = hx >= T::QX && hx < T::QX + TX && hy >= NG && hy < NG + TY && !outx && !outa;
       if (a.stage == 0 && a.img_in) {  // the image the previous step's stage 2 left
+        const int64_t i32 = idx32(ma, mx);
 #pragma unroll
-        for (int m = 0; m < NQ; ++m) ld[t][m] = __ldg(&a.U32[m * N + i]);
+        for (int m = 0; m < NQ; ++m) ld[t][m] = __ldg(&a.U32[m * N32 + i32]);
       } else if (a.stage == 0 || a.stage == 3) {
+        const int64_t i = pbase + (int64_t)(g.G[AX1] + ma) * S1 + mx;  // FP64 state
         const double* U = a.U;
 #pragma unroll
         for (int m = 0; m < NQ; ++m) {
@@ -543,16 +666,19 @@ __global__ void __launch_bounds__(TL::NT, 1024 / TL::NT) k_stage(StageArgs a) { 
 #pragma unroll
             for (int m = 0; m < NQ; ++m) a.Ubackup[m * N + i] = U[m * N + i];
           }
+          const int64_t i32 = idx32(ma, mx);
 #pragma unroll
-          for (int m = 0; m < NQ; ++m) a.U32[m * N + i] = ld[t][m];
+          for (int m = 0; m < NQ; ++m) a.U32[m * N32 + i32] = ld[t][m];
         }
       } else {
+        const int64_t i32 = idx32(ma, mx);
 #pragma unroll
         for (int m = 0; m < NQ; ++m) {
-          rk[t][m] = __ldg(&a.Kin[m * N + i]);
-          rv[t][m] = __ldg(&a.U32[m * N + i]);
+          rk[t][m] = __ldg(&a.Kin[m * N32 + i32]);
+          rv[t][m] = __ldg(&a.U32[m * N32 + i32]);
         }
       }
+    }
     }
     if (a.stage == 1 || a.stage == 2) {
 #pragma unroll
@@ -721,11 +847,11 @@ __global__ void __launch_bounds__(TL::NT, 1024 / TL::NT) k_stage(StageArgs a) { 
     bool isx;
     int hx, hy;
     if (!face_geom<T::XF, TL>(f, x0, y0, nx, n1, isx, hx, hy)) continue;
-    const float* qb = q0 + hy * T::QW + hx;  // stencil cell 0 in the q tile
+    const float* qb = q0 + hy * T::QP + hx;  // stencil cell 0 in the q tile
     const bool sm = LEARNED && SG.smooth[f];
     FaceGeo<T::NTG> fg;
     {
-      const int st = isx ? 1 : T::QW;
+      const int st = isx ? 1 : T::QP;
 #pragma unroll
       for (int k = 0; k < 6; ++k) fg.off[k] = k * st;
       fg.un = isx ? 1 : 1 + AX1;
@@ -875,7 +1001,8 @@ __global__ void __launch_bounds__(TL::NT, 1024 / TL::NT) k_stage(StageArgs a) { 
   for (int c = tid; c < TX * TY; c += NT) {
     int j = c / TX, i = c - j * TX;
     if (x0 + i >= nx || y0 + j >= n1) continue;
-    const int64_t gi = pbase + (int64_t)(g.G[AX1] + y0 + j) * S1 + x0 + i;
+    const int64_t gi = pbase + (int64_t)(g.G[AX1] + y0 + j) * S1 + x0 + i;  // FP64 state
+    const int64_t gf = idx32(y0 + j, x0 + i);                              // FP32 buffers
     const int qj = j + NG, qi = i + T::QX;
     float inc[NQ];
     auto fy2 = [&](int m, int jj) { return make_float2(S.fy[m][jj][i], S.fy[m + 1][jj][i]); };
@@ -906,15 +1033,15 @@ __global__ void __launch_bounds__(TL::NT, 1024 / TL::NT) k_stage(StageArgs a) { 
     }
     if constexpr (MODE == 1) {
 #pragma unroll
-      for (int m = 0; m < NQ; ++m) a.Lp[m * N + gi] = inc[m];
+      for (int m = 0; m < NQ; ++m) a.Lp[m * N32 + gf] = inc[m];
     } else {
-      auto kin = [&](int m) { return CACHE ? S.own.k[m][j][i] : a.Kin[m * N + gi]; };
+      auto kin = [&](int m) { return CACHE ? S.own.k[m][j][i] : a.Kin[m * N32 + gf]; };
       if (a.stage == 0) {
 #pragma unroll
-        for (int m = 0; m < NQ; ++m) a.Kout[m * N + gi] = inc[m];
+        for (int m = 0; m < NQ; ++m) a.Kout[m * N32 + gf] = inc[m];
       } else if (a.stage == 1) {
 #pragma unroll
-        for (int m = 0; m < NQ; ++m) a.Kout[m * N + gi] = kin(m) + inc[m];
+        for (int m = 0; m < NQ; ++m) a.Kout[m * N32 + gf] = kin(m) + inc[m];
       } else {
         // this cell's U^n is read only here, by this thread, so U is updated in place
         float d[NQ];
@@ -929,12 +1056,12 @@ __global__ void __launch_bounds__(TL::NT, 1024 / TL::NT) k_stage(StageArgs a) { 
           if (m == NQ - 1) uPi = un;
           // the FP32 image of the new state for the next step's stage 0: the
           // values its phase A would form from U (E - Pi in FP64), bit for bit
-          if (a.img_out && m != NQ - 3) a.img_out[m * N + gi] = f64_to_f32(un);
+          if (a.img_out && m != NQ - 3) a.img_out[m * N32 + gf] = f64_to_f32(un);
         }
-        if (a.img_out) a.img_out[(NQ - 3) * N + gi] = f64_to_f32(uE - uPi);
+        if (a.img_out) a.img_out[(NQ - 3) * N32 + gf] = f64_to_f32(uE - uPi);
         // admissibility of the new state (rho > 0, Gamma > 0, (Gamma+1) p + Pi > 0)
         // from its FP32 image: a diagnostic, not part of the update
-        auto v = [&](int m) { return CACHE ? S.own.v[m][j][i] : a.U32[m * N + gi]; };
+        auto v = [&](int m) { return CACHE ? S.own.v[m][j][i] : a.U32[m * N32 + gf]; };
         float rho = v(0) + d[0];
         float msq = 0.0f;
 #pragma unroll
@@ -1086,6 +1213,7 @@ static StageArgs stage_args(const GridDev& g, int stage, double* U, float* U32, 
   a.P = weno_params(eps_rel, weights);
   a.mood = mood;
   a.nbad = nbad;
+  a.tma = 0;
   a.mlp_frag = nullptr;
   a.mlp_bias = nullptr;
   a.thr = 0.0f;
@@ -1113,8 +1241,13 @@ void launch_stage2d(const GridDev& g, int stage, double* U, float* U32, const fl
                     double dt_fixed, double cfl, unsigned long long* lmax, double* dt_out, uint8_t* mask_x,
                     uint8_t* mask_y, float eps_rel, int mood, int weights, unsigned long long* nbad,
                     const GateArgs* gate, const int* run_if, unsigned long long* census, int tile, bool pdl,
-                    bool img_in, float* img_out, cudaStream_t s) {
+                    bool img_in, float* img_out, const CUtensorMap* tmk, const CUtensorMap* tmv, cudaStream_t s) {
   StageArgs a = stage_args(g, stage, U, U32, Kin, Kout, dt_fixed, cfl, lmax, dt_out, eps_rel, mood, weights, nbad);
+  if (tmk && tmv && !gate) {
+    a.tma = 1;
+    a.tm_k = *tmk;
+    a.tm_v = *tmv;
+  }
   a.img_in = img_in ? 1 : 0;
   a.img_out = img_out;
   a.mask_x = mask_x;
@@ -1152,6 +1285,51 @@ void launch_stage2d(const GridDev& g, int stage, double* U, float* U32, const fl
   }
 }
 
+// cuTensorMapEncodeTiled, from the driver through the runtime (the library
+// does not link the driver library itself)
+static PFN_cuTensorMapEncodeTiled_v12000 encode_tiled() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+template <class TL>
+static bool encode_map(const GridDev& g, const float* buf, CUtensorMap* out) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = encode_tiled();
+  if (!enc || !buf) return false;
+  // (padded column, padded row, field); a box is the q tile of one CTA:
+  // HXP columns (the halo's HX and the pitch's padding) x HY rows x all fields
+  const cuuint64_t dims[3] = {(cuuint64_t)g.st32[1], (cuuint64_t)g.P[1], (cuuint64_t)g.nv};
+  const cuuint64_t strides[2] = {(cuuint64_t)g.st32[1] * sizeof(float), (cuuint64_t)g.N32 * sizeof(float)};
+  const cuuint32_t box[3] = {(cuuint32_t)TL::HXP, (cuuint32_t)TL::HY, (cuuint32_t)g.nv};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = enc(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(buf), dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+bool fused2d_encode_map(const GridDev& g, int tile, const float* buf, CUtensorMap* out) {
+  // the 16-byte rules of TMA: row and field pitches, and the first column of
+  // every box (x0 - NG + NG = x0, a multiple of 32) as a multiple of 4 floats
+  if (g.ndim != 2 || g.G[0] != NG || g.st32[1] % 4 != 0 || g.N32 % 4 != 0 ||
+      reinterpret_cast<uintptr_t>(buf) % 16 != 0)
+    return false;
+  switch (tile) {
+    case 1: return encode_map<TileB>(g, buf, out);
+    case 2: return encode_map<TileC>(g, buf, out);
+    default: return encode_map<TileA>(g, buf, out);
+  }
+}
+
 int fused2d_tile_height(int tile) {
   const int ty[3] = {TileA::TY, TileB::TY, TileC::TY};
   return ty[tile >= 0 && tile < 3 ? tile : 0];
@@ -1165,8 +1343,13 @@ int fused_tile_threads(int tile) {
 void launch_stage2d_band(const GridDev& g, int stage, double* U, float* U32, const float* Kin, float* Kout,
                          double dt_fixed, double cfl, unsigned long long* lmax, double* dt_out, uint8_t* mask_x,
                          uint8_t* mask_y, float eps_rel, int mood, int weights, unsigned long long* nbad, int row0,
-                         int nrows, int tile, cudaStream_t s) {
+                         int nrows, int tile, const CUtensorMap* tmk, const CUtensorMap* tmv, cudaStream_t s) {
   StageArgs a = stage_args(g, stage, U, U32, Kin, Kout, dt_fixed, cfl, lmax, dt_out, eps_rel, mood, weights, nbad);
+  if (tmk && tmv) {
+    a.tma = 1;
+    a.tm_k = *tmk;
+    a.tm_v = *tmv;
+  }
   a.mask_x = mask_x;
   a.mask_a = mask_y;
   a.row0 = row0;

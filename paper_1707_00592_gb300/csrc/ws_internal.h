@@ -2,12 +2,13 @@
 // installed; the public surface is include/ws.h).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include <vector>
 
-#include "../../include/ws.h"
+#include "ws.h"
 
 namespace ws {
 
@@ -22,6 +23,12 @@ struct GridDev {
   int64_t P[3];      // padded extents
   int64_t st[3];     // strides of x, y, z in a field
   int64_t N;         // padded cells per field
+  // layout of the fused path's FP32 buffers (stage image, increments K, 3D
+  // partial divergence): the same ghost offsets G, strides and cells per
+  // field of their own (2D: rows padded to a multiple of four floats, so that
+  // TMA boxes of tile halos start on 16-byte boundaries; otherwise st, N)
+  int64_t st32[3];
+  int64_t N32;
   double dx[3];
   int bc[3][2];
   int64_t fe[3][3];  // face-array extents per direction: n[e], n[d]+1 along d
@@ -59,6 +66,11 @@ struct ws_ctx {
   int stage_tile = 0;           // fused: tile shape of the stage launches (ws_autotune)
   int stage_sched = 0;          // fused: 0 stage launches with programmatic dependent launch, 1 plain
                                 // stage launches (ws_autotune)
+  int stage_tma = 0;            // fused 2D: 1 interior tiles load image and K as TMA boxes (ws_autotune)
+  // fused 2D: TMA descriptors of Ka, Kb, Q32, img[0], img[1] for the current
+  // tile shape; tmap_ok bit k: descriptor k is valid
+  CUtensorMap tmap[5];
+  unsigned tmap_ok = 0;
   bool resident = false;        // fused 2D/3D: carry the FP32 image of U between steps (ws_set_resident)
   float* img[2] = {nullptr, nullptr};  // the two image buffers (one read by a step, one written)
   int img_cur = -1;             // image valid for the next step on img_U, or -1
@@ -170,14 +182,20 @@ int fused_tile_threads(int tile);
 void launch_stage2d_band(const GridDev& g, int stage, double* U, float* U32, const float* Kin, float* Kout,
                          double dt_fixed, double cfl, unsigned long long* lmax, double* dt_out, uint8_t* mask_x,
                          uint8_t* mask_y, float eps_rel, int mood, int weights, unsigned long long* nbad, int row0,
-                         int nrows, int tile, cudaStream_t s);
+                         int nrows, int tile, const CUtensorMap* tmk, const CUtensorMap* tmv, cudaStream_t s);
 int fused2d_smem_bytes();
 cudaError_t fused2d_prepare();
 void launch_stage2d(const GridDev& g, int stage, double* U, float* U32, const float* Kin, float* Kout,
                     double dt_fixed, double cfl, unsigned long long* lmax, double* dt_out, uint8_t* mask_x,
                     uint8_t* mask_y, float eps_rel, int mood, int weights, unsigned long long* nbad,
                     const GateArgs* gate, const int* run_if, unsigned long long* census, int tile, bool pdl,
-                    bool img_in, float* img_out, cudaStream_t s);
+                    bool img_in, float* img_out, const CUtensorMap* tmk, const CUtensorMap* tmv, cudaStream_t s);
+// tmk, tmv (nullable, both or neither; plain and census launches): TMA
+// descriptors of Kin and U32 from fused2d_encode_map for the launch's tile;
+// interior tiles then load both as boxes.
+// Describes an FP32 buffer of the fused 2D layout (g.st32, g.N32, g.nv
+// fields) with boxes of one tile's halo; false if the driver refuses.
+bool fused2d_encode_map(const GridDev& g, int tile, const float* buf, CUtensorMap* out);
 // census (nullable, without a gate): the same stage, also counting the
 // flat-stencil decisions into census[4] (face-variables, flat ones, warp
 // passes, warp passes that ran WENO-IS)

@@ -520,20 +520,24 @@ def test_run_host_unbanded_matches_device_steps(kind):
 
 
 @pytest.mark.parametrize("ndim,n,bc", [(2, (70, 47), "transmissive"), (2, (33, 65), "periodic"),
-                                       (2, (40, 31), "reflective"), (3, (37, 19, 17), "transmissive"),
+                                       (2, (40, 31), "reflective"), (2, (100, 64), "periodic"),
+                                       (2, (104, 50), "reflective"), (3, (37, 19, 17), "transmissive"),
                                        (3, (16, 20, 33), "periodic")])
 def test_stage_configs_bit_identical(ndim, n, bc):
     """Every fused-stage configuration ws_autotune chooses among (tile shape,
-    CTA size, launch mode) gives the same state, dt and MOOD record bit for
-    bit: the per-face arithmetic does not depend on the tile.  ws_autotune
-    then keeps one of them and reports it."""
+    CTA size, loads cell by cell or as TMA boxes, launch mode) gives the same
+    state, dt and MOOD record bit for bit: the per-face arithmetic does not
+    depend on the tile, and a TMA box holds the values the cell-by-cell loads
+    read (the larger 2D grids have tiles whose halo lies inside the grid, the
+    ones that load by TMA).  ws_autotune then keeps one of them and reports
+    it."""
     kind = "two_phase"
     case = wl.random_state(ndim, n, seed=23, kind=kind)
     bcs = tuple((bc, bc) for _ in range(ndim))
     stream = torch.cuda.Stream()
     ref = None
     s = ws.Solver(ndim, case.n, case.dx, bcs, precision="mixed", stream=stream)
-    cands = list(range(6)) if ndim == 2 else list(range(4))
+    cands = list(range(12)) if ndim == 2 else list(range(4))
     with torch.cuda.stream(stream):
         U0 = s.prim_to_cons(s.tensor(case.Q))
         with pytest.raises(ws.WsError):
@@ -542,6 +546,7 @@ def test_stage_configs_bit_identical(ndim, n, bc):
             ws.ws_set_stage_config(s.ctx, k)
             cfg = ws.ws_get_stage_config(s.ctx)
             assert cfg["index"] == k and cfg["schedule"] == k % 2
+            assert cfg["tma"] == ((k // 2) % 2 if ndim == 2 else 0)
             U = U0.clone()
             dts = [s.step(U, want_dt=True) for _ in range(3)]
             _, mask = s.mood(with_mask=True)
@@ -562,8 +567,8 @@ def test_stage_configs_bit_identical(ndim, n, bc):
     s.close()
 
 
-@pytest.mark.parametrize("n,bc,cfg", [((96, 96), "transmissive", 0), ((70, 47), "periodic", 1),
-                                      ((65, 40), "reflective", 4)])
+@pytest.mark.parametrize("n,bc,cfg", [((96, 96), "transmissive", 2), ((70, 47), "periodic", 1),
+                                      ((100, 64), "periodic", 3), ((65, 40), "reflective", 10)])
 def test_resident_steps_bit_identical(n, bc, cfg):
     """ws_set_resident: the FP32 image of the state carried from one step's
     stage 2 to the next step's stage 0 gives the same states, time steps and
