@@ -260,7 +260,7 @@ __device__ __forceinline__ float sound_speed2(float rho, float p, float Gam, flo
 __device__ __forceinline__ bool pressure_admissible(float Gam, float p, float Pi) {
   float g1 = Gam + 1.0f;
   float t = fmaf(g1, p, Pi);
-  float bound = 4.0e-7f * (fabsf(g1 * p) + fabsf(Pi)) + 1e-37f;
+  float bound = fmaf(4.0e-7f, fabsf(g1 * p) + fabsf(Pi), 1e-37f);
   if (t > bound) return true;
   if (t < -bound) return false;
   double e = ((double)Gam + 1.0) * (double)p + (double)Pi;
@@ -270,6 +270,28 @@ __device__ __forceinline__ bool pressure_admissible(float Gam, float p, float Pi
 template <int NQ>
 __device__ __forceinline__ bool admissible(const float* q) {
   return (q[0] > 0.0f) && (q[NQ - 2] > 0.0f) && pressure_admissible(q[NQ - 2], q[NQ - 3], q[NQ - 1]);
+}
+
+// admissible<NQ> of both sides of a face at once (sweep-frame primitives,
+// x: left state, y: right state): the pressure test as paired FP32 and
+// without branches; only a side within the rounding bound goes to FP64.
+// The verdicts are those of admissible<NQ> on each side.
+template <int NQ>
+__device__ __forceinline__ void admissible_pair(const float2 (&Q)[NQ], bool& ok0, bool& ok1) {
+  const float2 p = Q[NQ - 3], G = Q[NQ - 2], Pi = Q[NQ - 1];
+  const float2 g1 = add2(G, f2(1.0f));
+  const float2 t = fma2(g1, p, Pi);
+  const float2 gp = mul2(g1, p);
+  const float b0 = fmaf(4.0e-7f, fabsf(gp.x) + fabsf(Pi.x), 1e-37f);
+  const float b1 = fmaf(4.0e-7f, fabsf(gp.y) + fabsf(Pi.y), 1e-37f);
+  bool s0 = t.x > b0, s1 = t.y > b1;
+  const bool u0 = !s0 && !(t.x < -b0), u1 = !s1 && !(t.y < -b1);  // within the bound, or NaN
+  if (u0 || u1) {
+    if (u0) s0 = ((double)G.x + 1.0) * (double)p.x + (double)Pi.x > 0.0;
+    if (u1) s1 = ((double)G.y + 1.0) * (double)p.y + (double)Pi.y > 0.0;
+  }
+  ok0 = (Q[0].x > 0.0f) & (G.x > 0.0f) & s0;
+  ok1 = (Q[0].y > 0.0f) & (G.y > 0.0f) & s1;
 }
 
 // Characteristic variable r of the sweep-frame primitive q (Eq. eigen-vectors).

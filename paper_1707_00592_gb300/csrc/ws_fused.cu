@@ -889,13 +889,8 @@ __global__ void __launch_bounds__(TL::NT, 1024 / TL::NT) k_stage(const __grid_co
     back_project_pair<NQ>(W, ic2, irc, Q);
     int code[2] = {0, 0};
     if (a.mood) {
-      float qs[2][NQ];
-#pragma unroll
-      for (int r = 0; r < NQ; ++r) {
-        qs[0][r] = Q[r].x;
-        qs[1][r] = Q[r].y;
-      }
-      const bool ok0 = admissible<NQ>(qs[0]), ok1 = admissible<NQ>(qs[1]);
+      bool ok0, ok1;
+      admissible_pair<NQ>(Q, ok0, ok1);
       if (!ok0 || !ok1) {  // MOOD cascade of the failing side(s): rare
 #pragma unroll 1
         for (int side = 0; side < 2; ++side) {
