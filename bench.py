@@ -108,11 +108,11 @@ def cell_update_bytes(ndim: int) -> int:
 
 # DRAM bytes moved by one launch of the fused 2D mixed stage on the 1024^2
 # shock-bubble (ncu, one resident step at step 10 of a 60-step run): stage 0
-# reads the carried FP32 image (25.40 MB read, 0.02 MB written), stage 1 the
-# image and K0 (50.72 + 0.34 MB), stage 2 also the FP64 state it updates
-# (101.43 + 24.63 MB; the rest of its writes are still in L2 at the end); the
+# reads the carried FP32 image (25.45 MB read, 0.02 MB written), stage 1 the
+# image and K0 (50.85 + 0.45 MB), stage 2 also the FP64 state it updates
+# (101.54 + 24.28 MB; the rest of its writes are still in L2 at the end); the
 # mean over the three launches
-STAGE2D_DRAM_BYTES = (25.417728 + 51.052288 + 126.05568) / 3 * 1e6
+STAGE2D_DRAM_BYTES = (25.468928 + 51.297792 + 125.819136) / 3 * 1e6
 STAGE2D_DRAM_SOURCE = ("dram__bytes_read.sum + dram__bytes_write.sum per fused-stage launch, mean of the three "
                        "stages of one resident step (1024^2, step 10 of 60; ncu)")
 
