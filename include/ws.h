@@ -227,7 +227,11 @@ WS_API int ws_mlp_forward(const float *params, const float *X, int64_t n, float 
 
 /* Gradient (DEVICE, WS_MLP_NPARAM FP32, overwritten) and *loss (DEVICE FP32,
  * overwritten) of the mean binary cross-entropy over n samples, positives
- * weighted by pos_weight.  Enqueued on `stream`. */
+ * weighted by pos_weight.  Enqueued on `stream`.  The sums are formed in 64-bit
+ * fixed point (units of 2^-48, each contribution rounded once), so the result
+ * does not depend on the order of the threads: the same inputs give the same
+ * bits on every run.  They use one accumulator per device inside the library:
+ * calls on different streams must not run at the same time. */
 WS_API int ws_mlp_grad(const float *params, const float *X, const uint8_t *y, int64_t n, float pos_weight,
                        float *grad, float *loss, void *stream);
 

@@ -182,19 +182,45 @@ __global__ void k_mlp_forward(const float* __restrict__ params, const float* __r
   }
 }
 
+// The gradient is summed in 64-bit fixed point (units of 2^-48): integer
+// additions commute, so the sums -- within a block through shared-memory
+// atomics, across blocks through global ones -- do not depend on the order in
+// which threads arrive, and a gradient is the same on every run.  Each
+// contribution is rounded to the unit once (|contributions| < 3e4).
+constexpr float kFixScale = 281474976710656.0f;  // 2^48
+__device__ unsigned long long g_mlp_acc[NPARAM + 1];  // the sums; [NPARAM]: the loss
+
+__device__ __forceinline__ void fix_add(unsigned long long* a, float v) {
+  float s = fminf(fmaxf(v * kFixScale, -9.0e18f), 9.0e18f);  // exact scaling by a power of two
+  atomicAdd(a, (unsigned long long)__float2ll_rn(s));
+}
+
+__global__ void k_mlp_acc_zero() {
+  for (int i = threadIdx.x; i <= NPARAM; i += blockDim.x) g_mlp_acc[i] = 0ULL;
+}
+
+__global__ void k_mlp_acc_out(float* __restrict__ grad, float* __restrict__ loss) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i <= NPARAM; i += gridDim.x * blockDim.x) {
+    float v = (float)((double)(long long)g_mlp_acc[i] * (1.0 / 281474976710656.0));
+    if (i < NPARAM)
+      grad[i] = v;
+    else
+      *loss = v;
+  }
+}
+
 // mean binary cross-entropy (positives weighted by pos_weight) and its
-// gradient over n samples; grad and loss must be zeroed by the caller
+// gradient over n samples, into g_mlp_acc (zeroed before the launch)
 __global__ void k_mlp_grad(const float* __restrict__ params, const float* __restrict__ X,
-                           const uint8_t* __restrict__ y, int64_t n, float pos_weight, float inv_n,
-                           float* __restrict__ grad, float* __restrict__ loss) {
+                           const uint8_t* __restrict__ y, int64_t n, float pos_weight, float inv_n) {
   __shared__ float W[NPARAM];
-  __shared__ float G[NPARAM];
-  __shared__ float Ls;
+  __shared__ unsigned long long G[NPARAM];
+  __shared__ unsigned long long Ls;
   for (int i = threadIdx.x; i < NPARAM; i += blockDim.x) {
     W[i] = params[i];
-    G[i] = 0.0f;
+    G[i] = 0ULL;
   }
-  if (threadIdx.x == 0) Ls = 0.0f;
+  if (threadIdx.x == 0) Ls = 0ULL;
   __syncthreads();
   for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
     float x[NIN], h1[NH], h2[NH], z;
@@ -205,41 +231,41 @@ __global__ void k_mlp_grad(const float* __restrict__ params, const float* __rest
     float wgt = (y[s] ? pos_weight : 1.0f) * inv_n;
     // BCE with logits: softplus(z) - t z, computed stably
     float sp = fmaxf(z, 0.0f) + log1pf(expf(-fabsf(z)));
-    atomicAdd(&Ls, wgt * (sp - t * z));
+    fix_add(&Ls, wgt * (sp - t * z));
     float p = 1.0f / (1.0f + expf(-z));
     float dz = wgt * (p - t);
     float dh2[NH];
 #pragma unroll
     for (int k = 0; k < NH; ++k) {
-      atomicAdd(&G[OW3 + k], dz * h2[k]);
+      fix_add(&G[OW3 + k], dz * h2[k]);
       dh2[k] = h2[k] > 0.0f ? dz * W[OW3 + k] : 0.0f;
     }
-    atomicAdd(&G[OB3], dz);
+    fix_add(&G[OB3], dz);
     float dh1[NH];
 #pragma unroll
     for (int k = 0; k < NH; ++k) dh1[k] = 0.0f;
     for (int j = 0; j < NH; ++j) {
       float g2 = dh2[j];
       if (g2 == 0.0f) continue;
-      atomicAdd(&G[OB2 + j], g2);
+      fix_add(&G[OB2 + j], g2);
 #pragma unroll
       for (int k = 0; k < NH; ++k) {
-        atomicAdd(&G[OW2 + j * NH + k], g2 * h1[k]);
+        fix_add(&G[OW2 + j * NH + k], g2 * h1[k]);
         dh1[k] = fmaf(W[OW2 + j * NH + k], g2, dh1[k]);
       }
     }
     for (int j = 0; j < NH; ++j) {
       float g1 = h1[j] > 0.0f ? dh1[j] : 0.0f;
       if (g1 == 0.0f) continue;
-      atomicAdd(&G[OB1 + j], g1);
+      fix_add(&G[OB1 + j], g1);
 #pragma unroll
-      for (int k = 0; k < NIN; ++k) atomicAdd(&G[OW1 + j * NIN + k], g1 * x[k]);
+      for (int k = 0; k < NIN; ++k) fix_add(&G[OW1 + j * NIN + k], g1 * x[k]);
     }
   }
   __syncthreads();
   for (int i = threadIdx.x; i < NPARAM; i += blockDim.x)
-    if (G[i] != 0.0f) atomicAdd(&grad[i], G[i]);
-  if (threadIdx.x == 0) atomicAdd(loss, Ls);
+    if (G[i] != 0ULL) atomicAdd(&g_mlp_acc[i], G[i]);
+  if (threadIdx.x == 0) atomicAdd(&g_mlp_acc[NPARAM], Ls);
 }
 
 __global__ void k_adam(float* __restrict__ p, float* __restrict__ m, float* __restrict__ v,
@@ -285,12 +311,11 @@ extern "C" WS_API int ws_mlp_grad(const float* params, const float* X, const uin
                                   float* grad, float* loss, void* stream) {
   if (n <= 0 || !params || !X || !y || !grad || !loss) return WS_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
-  if (cudaMemsetAsync(grad, 0, sizeof(float) * NPARAM, s) != cudaSuccess ||
-      cudaMemsetAsync(loss, 0, sizeof(float), s) != cudaSuccess)
-    return WS_ECUDA;
   int b = blocks_for(n, 256);
   if (b > 152 * 2) b = 152 * 2;
-  k_mlp_grad<<<b, 256, 0, s>>>(params, X, y, n, pos_weight, 1.0f / (float)n, grad, loss);
+  k_mlp_acc_zero<<<1, 1024, 0, s>>>();
+  k_mlp_grad<<<b, 256, 0, s>>>(params, X, y, n, pos_weight, 1.0f / (float)n);
+  k_mlp_acc_out<<<(NPARAM + 256) / 256, 256, 0, s>>>(grad, loss);
   return cudaGetLastError() == cudaSuccess ? WS_OK : WS_ECUDA;
 }
 

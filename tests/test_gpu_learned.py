@@ -51,6 +51,30 @@ def test_gradient_matches_oracle():
     assert loss.item() == pytest.approx(mo.loss(p32, X32, y, 2.5), rel=1e-4)
 
 
+def test_gradient_is_deterministic():
+    """The gradient and loss sums are formed in fixed point, so the order in
+    which threads and blocks add their contributions does not change a bit:
+    repeated calls (with enough samples to fill every block) agree exactly,
+    and with the oracle as above."""
+    rng = np.random.default_rng(5)
+    p = mo.init(6)
+    X = rng.normal(size=(200_000, mo.NIN))
+    y = (rng.random(200_000) < 0.25).astype(np.uint8)
+    P, Xd, yd = cuda(p, torch.float32), cuda(X, torch.float32), cuda(y, torch.uint8)
+    out = []
+    for _ in range(4):
+        grad = torch.empty(mo.NPARAM, dtype=torch.float32, device="cuda")
+        loss = torch.empty(1, dtype=torch.float32, device="cuda")
+        ws.ws_mlp_grad(P, Xd, yd, 3.0, grad, loss)
+        torch.cuda.synchronize()
+        out.append((grad.cpu().numpy(), loss.item()))
+    for g, l in out[1:]:
+        assert np.array_equal(g, out[0][0])
+        assert l == out[0][1]
+    g64 = mo.grad(p.astype(np.float32).astype(np.float64), X.astype(np.float32).astype(np.float64), y, 3.0)
+    assert np.abs(out[0][0] - g64).max() <= 2e-4 * np.abs(g64).max()
+
+
 def test_adam_step():
     rng = np.random.default_rng(2)
     p = rng.normal(size=mo.NPARAM)
