@@ -100,6 +100,7 @@ void free_all(ws_ctx* c) {
   cudaFree(c->S1);
   cudaFree(c->Q);
   cudaFree(c->Q32);
+  cudaFree(c->chain);
   cudaFree(c->img[0]);
   cudaFree(c->img[1]);
   cudaFree(c->Ka);
@@ -241,13 +242,26 @@ int tube_rhs(ws_ctx* c, double* Us, int stage_slot, bool cfl) {
 int fused_run3(ws_ctx* c, double* U, double dt, const GateArgs* gate, const int* run_if,
                unsigned long long* census = nullptr) {
   const GridDev& g = c->gd;
-  if (!run_if) CK(c, cudaMemsetAsync(c->lmax, 0, sizeof(unsigned long long), c->stream));
   // The plain stages may follow one another with programmatic dependent
   // launch, so one pair of profiling events spans all of a step's stage
   // launches (events between them would serialise the launches); the gated
   // and census steps time each stage on its own.
   const int per_stage = g.ndim == 3 ? 2 : 1;
   const bool one_scope = !gate && !run_if && !census;
+  // plain steps take the chained slots (no memset before the step); the
+  // others, and a step captured into a graph, use the context's own counters
+  unsigned long long *lmax = c->lmax, *nbad = c->nbad, *clr0 = nullptr, *clr1 = nullptr;
+  if (one_scope && !c->capturing && c->chain) {
+    const int64_t n = c->chain_n++;
+    lmax = c->chain + (n & 1);
+    nbad = c->chain + 2 + (n & 1);
+    clr0 = c->chain + ((n + 1) & 1);
+    clr1 = c->chain + 2 + ((n + 1) & 1);
+  } else {
+    if (!run_if) CK(c, cudaMemsetAsync(c->lmax, 0, sizeof(unsigned long long), c->stream));
+    if (one_scope) CK(c, cudaMemsetAsync(c->nbad, 0, sizeof(unsigned long long), c->stream));
+  }
+  c->nbad_last = nbad;
   std::optional<KScope> all;
   if (one_scope) all.emplace(c, WS_K_FACE, 3 * per_stage);
   // ws_set_resident: a plain 2D step on the state the previous step left
@@ -275,17 +289,17 @@ int fused_run3(ws_ctx* c, double* U, double dt, const GateArgs* gate, const int*
     const float* Kin = s == 1 ? c->Ka : c->Kb;
     float* Kout = s == 0 ? c->Ka : c->Kb;
     if (g.ndim == 3)
-      launch_stage3d(g, s, U, u32, Kin, Kout, c->Lp, dt, c->opts.cfl, c->lmax, c->dt_dev, mb + c->mask_off[0],
-                     mb + c->mask_off[1], mb + c->mask_off[2], (float)c->opts.eps, c->opts.mood, c->opts.weights,
-                     c->nbad, census, c->stage_tile, c->stage_sched == 0, s == 0 && img_in, s == 2 ? img_out : nullptr,
-                     c->stream);
+      launch_stage3d(g, s, U, u32, Kin, Kout, c->Lp, dt, c->opts.cfl, lmax, c->dt_dev, mb + c->mask_off[0],
+                     mb + c->mask_off[1], mb + c->mask_off[2], (float)c->opts.eps, c->opts.mood, c->opts.weights, nbad,
+                     census, c->stage_tile, c->stage_sched == 0, s == 0 && img_in, s == 2 ? img_out : nullptr,
+                     s == 2 ? clr0 : nullptr, s == 2 ? clr1 : nullptr, c->stream);
     else {
       const CUtensorMap *tmk = map_of(c, Kin), *tmv = map_of(c, u32);
       if (!tmk || !tmv) tmk = tmv = nullptr;
-      launch_stage2d(g, s, U, u32, Kin, Kout, dt, c->opts.cfl, c->lmax, c->dt_dev, mb + c->mask_off[0],
-                     mb + c->mask_off[1], (float)c->opts.eps, c->opts.mood, c->opts.weights, c->nbad, gate, run_if,
+      launch_stage2d(g, s, U, u32, Kin, Kout, dt, c->opts.cfl, lmax, c->dt_dev, mb + c->mask_off[0],
+                     mb + c->mask_off[1], (float)c->opts.eps, c->opts.mood, c->opts.weights, nbad, gate, run_if,
                      census, c->stage_tile, c->stage_sched == 0, s == 0 && img_in, s == 2 ? img_out : nullptr, tmk,
-                     tmv, c->stream);
+                     tmv, s == 2 ? clr0 : nullptr, s == 2 ? clr1 : nullptr, c->stream);
     }
   }
   return check_launch(c, "fused stage");
@@ -299,7 +313,9 @@ GateArgs gate_args(ws_ctx* c) {
 int step_device(ws_ctx* c, double* U, double dt) {
   const GridDev& g = c->gd;
   int rc;
-  CK(c, cudaMemsetAsync(c->nbad, 0, sizeof(unsigned long long), c->stream));
+  c->nbad_last = c->nbad;
+  // a plain fused step clears (or rotates) its own counter
+  if (!(c->fused && !c->learned_on)) CK(c, cudaMemsetAsync(c->nbad, 0, sizeof(unsigned long long), c->stream));
   if (tubes(c) && mixed(c)) {
     const int64_t nt = c->td.ntubes;
     CK(c, cudaMemsetAsync(c->lmax, 0, sizeof(unsigned long long) * nt, c->stream));
@@ -339,6 +355,7 @@ int step_device(ws_ctx* c, double* U, double dt) {
     } else {
       // gated step, then on the device: keep or redo it without the gate
       // (restored from the backup taken in stage 0), with no host round trip
+      CK(c, cudaMemsetAsync(c->nbad, 0, sizeof(unsigned long long), c->stream));
       GateArgs ga = gate_args(c);
       CK(c, cudaMemsetAsync(c->lstat, 0, 8 * sizeof(float), c->stream));
       if ((rc = fused_run3(c, U, dt, &ga, nullptr))) return rc;
@@ -486,6 +503,13 @@ int ws_init(const ws_grid* grid, const ws_opts* opts, void* stream, ws_ctx** out
         }
         c->fused = true;
         c->stage_sched = 1;  // the 3D passes measured faster with plain launches
+      }
+      if (c->fused) {  // slots of consecutive plain steps, cleared once here
+        if ((rc = dalloc(c, &c->chain, 4))) goto bad;
+        if (cudaMemset(c->chain, 0, 4 * sizeof(unsigned long long)) != cudaSuccess) {
+          rc = fail(c, WS_ECUDA, "cannot clear the step counters");
+          goto bad;
+        }
       }
       for (int d = 0; d < gr.ndim; ++d)
         if ((rc = dalloc(c, &c->Fh32[d], (int64_t)g.nv * g.nfaces[d])) ||
@@ -638,7 +662,9 @@ int step_graph(ws_ctx* c, double* U) {
       c->graph_exec = nullptr;
     }
     CK(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    c->capturing = true;
     int rc = step_device(c, U, 0.0);
+    c->capturing = false;
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
     if (rc) {
@@ -745,6 +771,7 @@ int gated_step_graph(ws_ctx* c, double* U, double dt) {
 
 int ws_step(ws_ctx* c, double* U, double dt, double* dt_used) {
   if (!c || !U) return fail(c, WS_EINVAL, "bad pointers");
+  c->nbad_last = c->nbad;
   // a captured step would replay one fixed pair of image buffers, so resident
   // steps are launched directly
   bool graph = c->graph_on && dt <= 0.0 && c->stream != nullptr && !c->prof_on && !c->learned_on && !c->resident;
@@ -758,7 +785,7 @@ int ws_step(ws_ctx* c, double* U, double dt, double* dt_used) {
   }
   if (c->opts.check) {
     unsigned long long nb = 0;
-    CK(c, cudaMemcpyAsync(&nb, c->nbad, sizeof nb, cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaMemcpyAsync(&nb, c->nbad_last ? c->nbad_last : c->nbad, sizeof nb, cudaMemcpyDeviceToHost, c->stream));
     CK(c, cudaStreamSynchronize(c->stream));
     if (nb) return fail(c, WS_ENONPHYS, "%llu inadmissible cells after the step", nb);
   }
@@ -896,6 +923,7 @@ int run_host_banded(ws_ctx* c, double* U_host, int nsteps, double dt, double* dt
 int ws_run_host(ws_ctx* c, double* U_host, int nsteps, double dt, double* dt_used) {
   if (!c || !U_host || nsteps < 0) return fail(c, WS_EINVAL, "bad arguments");
   c->img_cur = -1;  // the carried FP32 image no longer follows U
+  c->nbad_last = c->nbad;
   if (!c->Uhost_dev) {
     int rc = dalloc(c, &c->Uhost_dev, c->nstate);
     if (rc) return rc;
@@ -936,7 +964,7 @@ int ws_get_mood(ws_ctx* c, uint8_t* mask, int64_t counts[9]) {
 int ws_nonphysical(ws_ctx* c, int64_t* count) {
   if (!c || !count) return fail(c, WS_EINVAL, "bad pointers");
   unsigned long long nb = 0;
-  CK(c, cudaMemcpyAsync(&nb, c->nbad, sizeof nb, cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaMemcpyAsync(&nb, c->nbad_last ? c->nbad_last : c->nbad, sizeof nb, cudaMemcpyDeviceToHost, c->stream));
   CK(c, cudaStreamSynchronize(c->stream));
   *count = (int64_t)nb;
   return WS_OK;
@@ -1053,7 +1081,7 @@ int ws_gate_eval(ws_ctx* c, double* U, uint8_t* smooth) {
   c->img_cur = -1;
   launch_stage2d(c->gd, 3, U, c->Q32, c->Ka, c->Kb, 0.0, c->opts.cfl, c->lmax, c->dt_dev, smooth,
                  smooth + c->mask_off[1], (float)c->opts.eps, c->opts.mood, c->opts.weights, c->nbad, &ga, nullptr,
-                 nullptr, 0, false, false, nullptr, nullptr, nullptr, c->stream);
+                 nullptr, 0, false, false, nullptr, nullptr, nullptr, nullptr, nullptr, c->stream);
   return check_launch(c, "gate eval");
 }
 

@@ -198,6 +198,11 @@ struct StageArgs {
   int tma;
   alignas(64) CUtensorMap tm_k;
   alignas(64) CUtensorMap tm_v;
+  // nullable: slots block (0, 0, 0) clears once the previous grid has
+  // completed (a step's last launch clears the next step's CFL maximum and
+  // inadmissible-cell count, so consecutive steps need no memset between them)
+  unsigned long long* clear0;
+  unsigned long long* clear1;
 };
 
 // interior index along an axis of n cells for a (possibly out-of-range)
@@ -525,6 +530,10 @@ __global__ void __launch_bounds__(TL::NT, 1024 / TL::NT) k_stage(const __grid_co
   asm volatile("griddepcontrol.wait;" ::: "memory");
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   if (a.run_if && *a.run_if == 0) return;  // a conditional redo that is not needed
+  if (a.clear0 && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0) {
+    *a.clear0 = 0ULL;
+    if (a.clear1) *a.clear1 = 0ULL;
+  }
   const GridDev& g = a.g;
   const int nx = g.n[0], n1 = g.n[AX1];
   const int trow = blockIdx.y + a.row0;  // tile row
@@ -1209,6 +1218,7 @@ static StageArgs stage_args(const GridDev& g, int stage, double* U, float* U32, 
   a.mood = mood;
   a.nbad = nbad;
   a.tma = 0;
+  a.clear0 = a.clear1 = nullptr;
   a.mlp_frag = nullptr;
   a.mlp_bias = nullptr;
   a.thr = 0.0f;
@@ -1236,8 +1246,11 @@ void launch_stage2d(const GridDev& g, int stage, double* U, float* U32, const fl
                     double dt_fixed, double cfl, unsigned long long* lmax, double* dt_out, uint8_t* mask_x,
                     uint8_t* mask_y, float eps_rel, int mood, int weights, unsigned long long* nbad,
                     const GateArgs* gate, const int* run_if, unsigned long long* census, int tile, bool pdl,
-                    bool img_in, float* img_out, const CUtensorMap* tmk, const CUtensorMap* tmv, cudaStream_t s) {
+                    bool img_in, float* img_out, const CUtensorMap* tmk, const CUtensorMap* tmv,
+                    unsigned long long* clear0, unsigned long long* clear1, cudaStream_t s) {
   StageArgs a = stage_args(g, stage, U, U32, Kin, Kout, dt_fixed, cfl, lmax, dt_out, eps_rel, mood, weights, nbad);
+  a.clear0 = clear0;
+  a.clear1 = clear1;
   if (tmk && tmv && !gate) {
     a.tma = 1;
     a.tm_k = *tmk;
@@ -1362,6 +1375,7 @@ static void stage3d_passes(const GridDev& g, const StageArgs& a0, uint8_t* mask_
   // pass 1: x and y faces of every z plane -> x + y part of the divergence
   a.mask_x = mask_x;
   a.mask_a = mask_y;
+  a.clear0 = a.clear1 = nullptr;  // the stage's last pass clears
   dim3 g1((g.n[0] + TL::TX - 1) / TL::TX, (g.n[1] + TL::TY - 1) / TL::TY, g.n[2]);
   if (census)
     launch_k<3, 7, 1, TL>(g1, false, s, a);
@@ -1370,6 +1384,8 @@ static void stage3d_passes(const GridDev& g, const StageArgs& a0, uint8_t* mask_
   // pass 2: z faces of every y plane, the whole divergence and the RK stage
   a.mask_x = nullptr;
   a.mask_a = mask_z;
+  a.clear0 = a0.clear0;
+  a.clear1 = a0.clear1;
   dim3 g2((g.n[0] + TL::TX - 1) / TL::TX, (g.n[2] + TL::TY - 1) / TL::TY, g.n[1]);
   if (census)
     launch_k<3, 7, 2, TL>(g2, false, s, a);
@@ -1380,8 +1396,11 @@ static void stage3d_passes(const GridDev& g, const StageArgs& a0, uint8_t* mask_
 void launch_stage3d(const GridDev& g, int stage, double* U, float* U32, const float* Kin, float* Kout, float* Lp,
                     double dt_fixed, double cfl, unsigned long long* lmax, double* dt_out, uint8_t* mask_x,
                     uint8_t* mask_y, uint8_t* mask_z, float eps_rel, int mood, int weights, unsigned long long* nbad,
-                    unsigned long long* census, int tile, bool pdl, bool img_in, float* img_out, cudaStream_t s) {
+                    unsigned long long* census, int tile, bool pdl, bool img_in, float* img_out,
+                    unsigned long long* clear0, unsigned long long* clear1, cudaStream_t s) {
   StageArgs a = stage_args(g, stage, U, U32, Kin, Kout, dt_fixed, cfl, lmax, dt_out, eps_rel, mood, weights, nbad);
+  a.clear0 = clear0;
+  a.clear1 = clear1;
   a.Lp = Lp;
   a.census = census;
   a.img_in = img_in ? 1 : 0;

@@ -67,6 +67,14 @@ struct ws_ctx {
   int stage_sched = 0;          // fused: 0 stage launches with programmatic dependent launch, 1 plain
                                 // stage launches (ws_autotune)
   int stage_tma = 0;            // fused 2D: 1 interior tiles load image and K as TMA boxes (ws_autotune)
+  // fused plain steps: CFL maxima [0, 1] and inadmissible-cell counts [2, 3]
+  // of two consecutive steps (step n uses slots n % 2 and clears those of
+  // step n + 1 in its last launch, so steps follow one another with no
+  // memset); the step count; the counter the last step used
+  unsigned long long* chain = nullptr;
+  int64_t chain_n = 0;
+  unsigned long long* nbad_last = nullptr;
+  bool capturing = false;       // a step is being captured into a graph (no chained slots)
   // fused 2D: TMA descriptors of Ka, Kb, Q32, img[0], img[1] for the current
   // tile shape; tmap_ok bit k: descriptor k is valid
   CUtensorMap tmap[5];
@@ -189,7 +197,10 @@ void launch_stage2d(const GridDev& g, int stage, double* U, float* U32, const fl
                     double dt_fixed, double cfl, unsigned long long* lmax, double* dt_out, uint8_t* mask_x,
                     uint8_t* mask_y, float eps_rel, int mood, int weights, unsigned long long* nbad,
                     const GateArgs* gate, const int* run_if, unsigned long long* census, int tile, bool pdl,
-                    bool img_in, float* img_out, const CUtensorMap* tmk, const CUtensorMap* tmv, cudaStream_t s);
+                    bool img_in, float* img_out, const CUtensorMap* tmk, const CUtensorMap* tmv,
+                    unsigned long long* clear0, unsigned long long* clear1, cudaStream_t s);
+// clear0, clear1 (nullable): device slots the launch sets to zero once the
+// previous grid has completed (before any of its CTAs reads them)
 // tmk, tmv (nullable, both or neither; plain and census launches): TMA
 // descriptors of Kin and U32 from fused2d_encode_map for the launch's tile;
 // interior tiles then load both as boxes.
@@ -206,7 +217,8 @@ cudaError_t fused3d_prepare();
 void launch_stage3d(const GridDev& g, int stage, double* U, float* U32, const float* Kin, float* Kout, float* Lp,
                     double dt_fixed, double cfl, unsigned long long* lmax, double* dt_out, uint8_t* mask_x,
                     uint8_t* mask_y, uint8_t* mask_z, float eps_rel, int mood, int weights, unsigned long long* nbad,
-                    unsigned long long* census, int tile, bool pdl, bool img_in, float* img_out, cudaStream_t s);
+                    unsigned long long* census, int tile, bool pdl, bool img_in, float* img_out,
+                    unsigned long long* clear0, unsigned long long* clear1, cudaStream_t s);
 void launch_gate_decide(const float* lstat, unsigned long long* nbad, unsigned long long* lmax, int flags, int* redo,
                         double* stats, int* drift_dev, cudaGraphConditionalHandle cond, cudaStream_t s);
 void launch_restore(const int* redo, const double* src, double* dst, int64_t n, cudaStream_t s);
