@@ -286,17 +286,17 @@ WS_API int ws_gate_stats(ws_ctx *ctx, double out[6]);
  *    a CTA owns and its thread count -- 32 x 15 cells on 512 threads (two CTAs
  *    per SM), 32 x 31 on 1024 (one CTA per SM; 2D only: with 7 fields its
  *    shared memory exceeds a CTA's limit) or 32 x 7 on 256 (four CTAs per SM)
- *    -- the loads (2D): 0 every CTA loads its tile and 3-cell halo cell by
- *    cell, applying the boundary conditions; 1 a CTA whose halo lies inside
- *    the grid loads the stage's FP32 image and increments as two TMA boxes
- *    (the others as with 0) -- and the launch schedule: 0 one launch per
+ *    -- the loads: 0 every CTA loads its tile and 3-cell halo cell by cell,
+ *    applying the boundary conditions; 1 a CTA whose halo lies inside the
+ *    grid loads the stage's FP32 image and increments as two TMA boxes (the
+ *    others as with 0; in 3D the first pass, of x and y faces) -- and the
+ *    launch schedule: 0 one launch per
  *    stage (per pass in 3D), consecutive launches with programmatic
  *    dependent launch (the next launch's CTAs wait on the device for the
  *    previous grid instead of being launched after it); 1 the same launches
- *    without it.  Candidate index = 4 x tile + 2 x loads + schedule in 2D
- *    (tiles 0, 1, 2 = 32 x 15, 32 x 31, 32 x 7), 2 x tile + schedule in 3D
- *    (tiles 0, 1 = 32 x 15, 32 x 7).  ws_get_stage_config reports the
- *    choice.
+ *    without it.  Candidate index = 4 x tile + 2 x loads + schedule; tiles
+ *    0, 1, 2 = 32 x 15, 32 x 31, 32 x 7 in 2D, 0, 1 = 32 x 15, 32 x 7 in 3D.
+ *    ws_get_stage_config reports the choice.
  *  - Batched tubes in mixed precision: the chunk of cells a CTA of the
  *    persistent stage kernel processes and its thread count, from (256, 128),
  *    (256, 256), (512, 256), (512, 512), (1024, 512).
@@ -309,7 +309,8 @@ WS_API int ws_autotune(ws_ctx *ctx, const double *U, int steps, int *choice);
 /* Sets the fused stages' configuration to candidate `index` of ws_autotune
  * (the default is 2 in 2D: 32 x 15 tiles, TMA loads, stage launches with
  * programmatic dependent launch -- 0 if the driver cannot describe the
- * buffers for TMA; 1 in 3D: 32 x 15 tiles, plain launches).  A TMA candidate
+ * buffers for TMA; 3 in 3D: 32 x 15 tiles, TMA loads, plain launches -- 1
+ * without TMA).  A TMA candidate
  * falls back to cell-by-cell loads when the driver refuses a descriptor
  * (ws_get_stage_config then reports loads 0).  WS_EINVAL on a context without
  * fused stages or an index that is not a candidate. */

@@ -39,10 +39,11 @@ int check_launch(ws_ctx* c, const char* what) {
   return WS_OK;
 }
 
-// fused 2D: TMA descriptors of the FP32 buffers for the current tile shape
+// fused 2D and 3D: TMA descriptors of the FP32 buffers for the current tile
+// shape (3D: of the first pass)
 void encode_maps(ws_ctx* c) {
   c->tmap_ok = 0;
-  if (!c->fused || c->gd.ndim != 2) return;
+  if (!c->fused) return;
   const float* bufs[5] = {c->Ka, c->Kb, c->Q32, c->img[0], c->img[1]};
   for (int k = 0; k < 5; ++k)
     if (bufs[k] && fused2d_encode_map(c->gd, c->stage_tile, bufs[k], &c->tmap[k])) c->tmap_ok |= 1u << k;
@@ -288,12 +289,14 @@ int fused_run3(ws_ctx* c, double* U, double dt, const GateArgs* gate, const int*
     if (!one_scope) k.emplace(c, WS_K_FACE, per_stage);
     const float* Kin = s == 1 ? c->Ka : c->Kb;
     float* Kout = s == 0 ? c->Ka : c->Kb;
-    if (g.ndim == 3)
+    if (g.ndim == 3) {
+      const CUtensorMap *tmk = map_of(c, Kin), *tmv = map_of(c, u32);
+      if (!tmk || !tmv) tmk = tmv = nullptr;
       launch_stage3d(g, s, U, u32, Kin, Kout, c->Lp, dt, c->opts.cfl, lmax, c->dt_dev, mb + c->mask_off[0],
                      mb + c->mask_off[1], mb + c->mask_off[2], (float)c->opts.eps, c->opts.mood, c->opts.weights, nbad,
                      census, c->stage_tile, c->stage_sched == 0, s == 0 && img_in, s == 2 ? img_out : nullptr,
-                     s == 2 ? clr0 : nullptr, s == 2 ? clr1 : nullptr, c->stream);
-    else {
+                     s == 2 ? clr0 : nullptr, s == 2 ? clr1 : nullptr, tmk, tmv, c->stream);
+    } else {
       const CUtensorMap *tmk = map_of(c, Kin), *tmv = map_of(c, u32);
       if (!tmk || !tmv) tmk = tmv = nullptr;
       launch_stage2d(g, s, U, u32, Kin, Kout, dt, c->opts.cfl, lmax, c->dt_dev, mb + c->mask_off[0],
@@ -475,10 +478,11 @@ int ws_init(const ws_grid* grid, const ws_opts* opts, void* stream, ws_ctx** out
       goto bad;
     if (op.precision == WS_PREC_MIXED) {
       const bool fused2d = gr.ndim == 2 && !getenv("WS_NO_FUSED");
-      if (fused2d) {  // FP32 rows padded to a multiple of four floats (TMA boxes)
+      const bool fused3d = gr.ndim == 3 && !getenv("WS_NO_FUSED");
+      if (fused2d || fused3d) {  // FP32 rows padded to a multiple of four floats (TMA boxes)
         g.st32[1] = (g.P[0] + 3) / 4 * 4;
         g.st32[2] = g.st32[1] * g.P[1];
-        g.N32 = g.st32[2];
+        g.N32 = g.st32[2] * g.P[2];
       }
       if ((rc = dalloc(c, &c->Q32, std::max((int64_t)(g.nv + 1) * g.N, (int64_t)g.nv * g.N32)))) goto bad;
       if (fused2d) {
@@ -493,9 +497,9 @@ int ws_init(const ws_grid* grid, const ws_opts* opts, void* stream, ws_ctx** out
         encode_maps(c);
         c->stage_tma = c->tmap_ok == 0x7u ? 1 : 0;
       }
-      if (gr.ndim == 3 && !getenv("WS_NO_FUSED")) {
-        if ((rc = dalloc(c, &c->Ka, (int64_t)g.nv * g.N)) || (rc = dalloc(c, &c->Kb, (int64_t)g.nv * g.N)) ||
-            (rc = dalloc(c, &c->Lp, (int64_t)g.nv * g.N)) || (rc = dalloc(c, &c->census, 4)))
+      if (fused3d) {
+        if ((rc = dalloc(c, &c->Ka, (int64_t)g.nv * g.N32)) || (rc = dalloc(c, &c->Kb, (int64_t)g.nv * g.N32)) ||
+            (rc = dalloc(c, &c->Lp, (int64_t)g.nv * g.N32)) || (rc = dalloc(c, &c->census, 4)))
           goto bad;
         if (fused3d_prepare() != cudaSuccess) {
           rc = fail(c, WS_ECUDA, "cannot enable %d bytes of shared memory for the fused stage", fused3d_smem_bytes());
@@ -503,6 +507,8 @@ int ws_init(const ws_grid* grid, const ws_opts* opts, void* stream, ws_ctx** out
         }
         c->fused = true;
         c->stage_sched = 1;  // the 3D passes measured faster with plain launches
+        encode_maps(c);
+        c->stage_tma = c->tmap_ok == 0x7u ? 1 : 0;
       }
       if (c->fused) {  // slots of consecutive plain steps, cleared once here
         if ((rc = dalloc(c, &c->chain, 4))) goto bad;
@@ -1096,10 +1102,9 @@ int ws_gate_stats(ws_ctx* c, double out[6]) {
 
 // Fused stage configurations: index = 2 x tile slot + schedule (0 stage
 // launches with programmatic dependent launch, 1 plain stage launches).
-// Stage configurations: index = (2 x tile + loads) x 2 + schedule in 2D
-// (loads: 0 cell by cell, 1 TMA boxes for interior tiles), 2 x tile +
-// schedule in 3D.
-static int stage_load_modes(const ws_ctx* c) { return c->gd.ndim == 2 ? 2 : 1; }
+// Stage configurations: index = (2 x tile + loads) x 2 + schedule (loads: 0
+// cell by cell, 1 TMA boxes for interior tiles -- in 3D, of the first pass).
+static int stage_load_modes(const ws_ctx*) { return 2; }
 
 static bool stage_config_valid(const ws_ctx* c, int index) {
   return index >= 0 && index < 2 * stage_load_modes(c) * fused_num_tiles(c->gd.ndim);

@@ -45,15 +45,16 @@
 // since no tile reads U's FP64 values after stage 0.  K0 and K1 live in
 // separate buffers because neighbouring tiles read K in their halos.
 //
-// The FP32 buffers (image, K) have a layout of their own (GridDev st32, N32):
-// in 2D their rows are padded to a multiple of four floats, so that the halo
-// of every tile starts on a 16-byte boundary (padded column x0 - 3 + 3 = x0,
-// a multiple of 32).  A 2D tile whose halo lies inside the grid then loads
-// the image and K of tile and halo as two TMA boxes (cp.async.bulk.tensor,
-// completion on an mbarrier) straight into shared memory, with no per-cell
-// address arithmetic; tiles on the boundary, the FP64 loads of a first
-// stage 0 and the 3D passes load cell by cell and apply the boundary
-// conditions while loading.
+// The FP32 buffers (image, K, the 3D partial divergence) have a layout of
+// their own (GridDev st32, N32): their rows are padded to a multiple of four
+// floats, so that the halo of every tile starts on a 16-byte boundary (padded
+// column x0 - 3 + 3 = x0, a multiple of 32).  A tile of the 2D stage or of
+// the first 3D pass whose halo lies inside the grid then loads the image and
+// K of tile and halo as two TMA boxes (cp.async.bulk.tensor, completion on an
+// mbarrier) straight into shared memory, with no per-cell address
+// arithmetic; tiles on the boundary, the FP64 loads of a first stage 0 and
+// the second 3D pass load cell by cell and apply the boundary conditions
+// while loading.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
@@ -488,6 +489,16 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, i
       "l"(map), "r"(x), "r"(y), "r"(f), "r"(b)
       : "memory");
 }
+// The same for a 4D box (x, row, plane, field) of a 3D grid's FP32 buffer.
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int x, int y, int z, int f,
+                                            unsigned long long* bar) {
+  unsigned d = (unsigned)__cvta_generic_to_shared(dst), b = (unsigned)__cvta_generic_to_shared(bar);
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cta.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+      "[%6];\n" ::"r"(d),
+      "l"(map), "r"(x), "r"(y), "r"(z), "r"(f), "r"(b)
+      : "memory");
+}
 // Waits for phase 0 of the barrier, at most `limit` polls; false if it gave up.
 __device__ __forceinline__ bool mbar_wait0(unsigned long long* bar, unsigned limit) {
   unsigned b = (unsigned)__cvta_generic_to_shared(bar);
@@ -517,7 +528,7 @@ __global__ void __launch_bounds__(TL::NT, 1024 / TL::NT) k_stage(const __grid_co
   extern __shared__ __align__(128) unsigned char smem_raw[];
   SM& S = *reinterpret_cast<SM*>(smem_raw);
   // a TMA load stages K of tile and halo in fx and fy, and the image in q
-  static_assert(MODE != 0 || (sizeof(S.fx) + sizeof(S.fy) >= sizeof(float) * NQ_ * T::HY * T::QP &&
+  static_assert(MODE == 2 || (sizeof(S.fx) + sizeof(S.fy) >= sizeof(float) * NQ_ * T::HY * T::QP &&
                               offsetof(SM, fy) == offsetof(SM, fx) + sizeof(S.fx)),
                 "the K box does not fit the flux arrays");
   static_assert(T::QP * sizeof(float) % 16 == 0, "TMA box rows are multiples of 16 bytes");
@@ -543,28 +554,36 @@ __global__ void __launch_bounds__(TL::NT, 1024 / TL::NT) k_stage(const __grid_co
   const int64_t pbase = (int64_t)(g.G[AXP] + plane) * g.st[AXP] + g.G[0];  // cell (x, a) at pbase + (G1 + a) S1 + x
   const int tid = threadIdx.x;
   // index in the FP32 buffers (image, K, the 3D partial divergence) of cell
-  // (x, a) of the tile's plane, computed where it is used; in 3D the FP32
-  // layout is the state's own (st32 = st, N32 = N)
+  // (x, a) of the tile's plane, computed where it is used
+  // (3D: the plane's base and the row stride are formed once, like pbase and S1)
+  const int64_t pbase32 = MODE == 0 ? 0 : (int64_t)(g.G[AXP] + plane) * g.st32[AXP] + g.G[0];
+  const int64_t S1f = MODE == 0 ? 0 : g.st32[AX1];
   auto idx32 = [&](int a_, int x_) -> int64_t {
-    if constexpr (MODE != 0)
-      return pbase + (int64_t)(g.G[AX1] + a_) * S1 + x_;
-    else
+    if constexpr (MODE == 0)
       return (int64_t)(g.G[1] + a_) * g.st32[1] + g.G[0] + x_;
+    else
+      return pbase32 + (int64_t)(g.G[AX1] + a_) * S1f + x_;
   };
-  const int64_t N32 = MODE != 0 ? N : g.N32;
-  // A 2D tile whose halo lies inside the grid, in a stage that reads the FP32
-  // image (and K), takes both as TMA boxes: no boundary mapping, one
-  // instruction per array.  They are issued first thing and land while the
-  // CTA sets up; the barrier below publishes the mbarrier to all threads.
-  const bool tma = MODE == 0 && a.tma && (a.stage == 1 || a.stage == 2 || (a.stage == 0 && a.img_in)) &&
+  const int64_t N32 = g.N32;
+  // A tile of the 2D stage or of the first 3D pass whose halo lies inside the
+  // grid, in a stage that reads the FP32 image (and K), takes both as TMA
+  // boxes: no boundary mapping, one instruction per array.  They are issued
+  // first thing and land while the CTA sets up; the barrier below publishes
+  // the mbarrier to all threads.
+  const bool tma = MODE != 2 && a.tma && (a.stage == 1 || a.stage == 2 || (a.stage == 0 && a.img_in)) &&
                    x0 >= NG && x0 + TX + NG <= nx && y0 >= NG && y0 + TY + NG <= n1;
   if (tma && tid == 0) {
     mbar_init(&S.mbar, 1);
     // boxes of the halo: padded column x0 - NG + NG, padded row y0, all fields
     constexpr unsigned box = (unsigned)(NQ_ * T::HY * T::QP * sizeof(float));
     mbar_expect_tx(&S.mbar, a.stage == 0 ? box : 2 * box);
-    tma_load_3d(&S.q[0][0][0], &a.tm_v, x0, y0, 0, &S.mbar);
-    if (a.stage != 0) tma_load_3d(&S.fx[0][0][0], &a.tm_k, x0, y0, 0, &S.mbar);
+    if constexpr (MODE == 0) {
+      tma_load_3d(&S.q[0][0][0], &a.tm_v, x0, y0, 0, &S.mbar);
+      if (a.stage != 0) tma_load_3d(&S.fx[0][0][0], &a.tm_k, x0, y0, 0, &S.mbar);
+    } else {  // the tile's z plane
+      tma_load_4d(&S.q[0][0][0], &a.tm_v, x0, y0, g.G[2] + plane, 0, &S.mbar);
+      if (a.stage != 0) tma_load_4d(&S.fx[0][0][0], &a.tm_k, x0, y0, g.G[2] + plane, 0, &S.mbar);
+    }
   }
   if (tma && a.stage == 0) __syncthreads();
   if (a.stage == 1 || a.stage == 2) {
@@ -1313,23 +1332,34 @@ template <class TL>
 static bool encode_map(const GridDev& g, const float* buf, CUtensorMap* out) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = encode_tiled();
   if (!enc || !buf) return false;
-  // (padded column, padded row, field); a box is the q tile of one CTA:
-  // HXP columns (the halo's HX and the pitch's padding) x HY rows x all fields
-  const cuuint64_t dims[3] = {(cuuint64_t)g.st32[1], (cuuint64_t)g.P[1], (cuuint64_t)g.nv};
-  const cuuint64_t strides[2] = {(cuuint64_t)g.st32[1] * sizeof(float), (cuuint64_t)g.N32 * sizeof(float)};
-  const cuuint32_t box[3] = {(cuuint32_t)TL::HXP, (cuuint32_t)TL::HY, (cuuint32_t)g.nv};
-  const cuuint32_t estr[3] = {1, 1, 1};
-  CUresult r = enc(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(buf), dims, strides, box, estr,
+  // 2D (padded column, padded row, field), 3D (padded column, padded row,
+  // padded plane, field); a box is the q tile of one CTA: HXP columns (the
+  // halo's HX and the pitch's padding) x HY rows (x one plane) x all fields
+  const cuuint32_t rank = g.ndim == 3 ? 4 : 3;
+  cuuint64_t dims[4] = {(cuuint64_t)g.st32[1], (cuuint64_t)g.P[1], (cuuint64_t)g.nv, 1};
+  cuuint64_t strides[3] = {(cuuint64_t)g.st32[1] * sizeof(float), (cuuint64_t)g.N32 * sizeof(float), 0};
+  cuuint32_t box[4] = {(cuuint32_t)TL::HXP, (cuuint32_t)TL::HY, (cuuint32_t)g.nv, 1};
+  if (rank == 4) {
+    dims[2] = (cuuint64_t)g.P[2];
+    dims[3] = (cuuint64_t)g.nv;
+    strides[1] = (cuuint64_t)g.st32[2] * sizeof(float);
+    strides[2] = (cuuint64_t)g.N32 * sizeof(float);
+    box[2] = 1;
+    box[3] = (cuuint32_t)g.nv;
+  }
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  CUresult r = enc(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, rank, const_cast<float*>(buf), dims, strides, box, estr,
                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
 
 bool fused2d_encode_map(const GridDev& g, int tile, const float* buf, CUtensorMap* out) {
-  // the 16-byte rules of TMA: row and field pitches, and the first column of
-  // every box (x0 - NG + NG = x0, a multiple of 32) as a multiple of 4 floats
-  if (g.ndim != 2 || g.G[0] != NG || g.st32[1] % 4 != 0 || g.N32 % 4 != 0 ||
-      reinterpret_cast<uintptr_t>(buf) % 16 != 0)
+  // the 16-byte rules of TMA: row, plane and field pitches, and the first
+  // column of every box (x0 - NG + NG = x0, a multiple of 32) as a multiple
+  // of 4 floats
+  if ((g.ndim != 2 && g.ndim != 3) || g.G[0] != NG || g.st32[1] % 4 != 0 || g.st32[2] % 4 != 0 ||
+      g.N32 % 4 != 0 || reinterpret_cast<uintptr_t>(buf) % 16 != 0)
     return false;
   switch (tile) {
     case 1: return encode_map<TileB>(g, buf, out);
@@ -1373,6 +1403,7 @@ static void stage3d_passes(const GridDev& g, const StageArgs& a0, uint8_t* mask_
                            bool census, bool pdl, cudaStream_t s) {
   StageArgs a = a0;
   // pass 1: x and y faces of every z plane -> x + y part of the divergence
+  // (interior tiles by TMA when a0 carries the descriptors)
   a.mask_x = mask_x;
   a.mask_a = mask_y;
   a.clear0 = a.clear1 = nullptr;  // the stage's last pass clears
@@ -1384,6 +1415,7 @@ static void stage3d_passes(const GridDev& g, const StageArgs& a0, uint8_t* mask_
   // pass 2: z faces of every y plane, the whole divergence and the RK stage
   a.mask_x = nullptr;
   a.mask_a = mask_z;
+  a.tma = 0;
   a.clear0 = a0.clear0;
   a.clear1 = a0.clear1;
   dim3 g2((g.n[0] + TL::TX - 1) / TL::TX, (g.n[2] + TL::TY - 1) / TL::TY, g.n[1]);
@@ -1397,10 +1429,16 @@ void launch_stage3d(const GridDev& g, int stage, double* U, float* U32, const fl
                     double dt_fixed, double cfl, unsigned long long* lmax, double* dt_out, uint8_t* mask_x,
                     uint8_t* mask_y, uint8_t* mask_z, float eps_rel, int mood, int weights, unsigned long long* nbad,
                     unsigned long long* census, int tile, bool pdl, bool img_in, float* img_out,
-                    unsigned long long* clear0, unsigned long long* clear1, cudaStream_t s) {
+                    unsigned long long* clear0, unsigned long long* clear1, const CUtensorMap* tmk,
+                    const CUtensorMap* tmv, cudaStream_t s) {
   StageArgs a = stage_args(g, stage, U, U32, Kin, Kout, dt_fixed, cfl, lmax, dt_out, eps_rel, mood, weights, nbad);
   a.clear0 = clear0;
   a.clear1 = clear1;
+  if (tmk && tmv && !census) {
+    a.tma = 1;
+    a.tm_k = *tmk;
+    a.tm_v = *tmv;
+  }
   a.Lp = Lp;
   a.census = census;
   a.img_in = img_in ? 1 : 0;

@@ -204,8 +204,9 @@ void launch_stage2d(const GridDev& g, int stage, double* U, float* U32, const fl
 // tmk, tmv (nullable, both or neither; plain and census launches): TMA
 // descriptors of Kin and U32 from fused2d_encode_map for the launch's tile;
 // interior tiles then load both as boxes.
-// Describes an FP32 buffer of the fused 2D layout (g.st32, g.N32, g.nv
-// fields) with boxes of one tile's halo; false if the driver refuses.
+// Describes an FP32 buffer of the fused 2D or 3D layout (g.st32, g.N32, g.nv
+// fields) with boxes of one tile's halo (of one z plane in 3D); false if the
+// driver refuses.  3D: tile 0 or 2 (the first pass's tiles).
 bool fused2d_encode_map(const GridDev& g, int tile, const float* buf, CUtensorMap* out);
 // census (nullable, without a gate): the same stage, also counting the
 // flat-stencil decisions into census[4] (face-variables, flat ones, warp
@@ -218,7 +219,8 @@ void launch_stage3d(const GridDev& g, int stage, double* U, float* U32, const fl
                     double dt_fixed, double cfl, unsigned long long* lmax, double* dt_out, uint8_t* mask_x,
                     uint8_t* mask_y, uint8_t* mask_z, float eps_rel, int mood, int weights, unsigned long long* nbad,
                     unsigned long long* census, int tile, bool pdl, bool img_in, float* img_out,
-                    unsigned long long* clear0, unsigned long long* clear1, cudaStream_t s);
+                    unsigned long long* clear0, unsigned long long* clear1, const CUtensorMap* tmk,
+                    const CUtensorMap* tmv, cudaStream_t s);
 void launch_gate_decide(const float* lstat, unsigned long long* nbad, unsigned long long* lmax, int flags, int* redo,
                         double* stats, int* drift_dev, cudaGraphConditionalHandle cond, cudaStream_t s);
 void launch_restore(const int* redo, const double* src, double* dst, int64_t n, cudaStream_t s);

@@ -522,14 +522,14 @@ def test_run_host_unbanded_matches_device_steps(kind):
 @pytest.mark.parametrize("ndim,n,bc", [(2, (70, 47), "transmissive"), (2, (33, 65), "periodic"),
                                        (2, (40, 31), "reflective"), (2, (100, 64), "periodic"),
                                        (2, (104, 50), "reflective"), (3, (37, 19, 17), "transmissive"),
-                                       (3, (16, 20, 33), "periodic")])
+                                       (3, (16, 20, 33), "periodic"), (3, (72, 40, 12), "reflective")])
 def test_stage_configs_bit_identical(ndim, n, bc):
     """Every fused-stage configuration ws_autotune chooses among (tile shape,
     CTA size, loads cell by cell or as TMA boxes, launch mode) gives the same
     state, dt and MOOD record bit for bit: the per-face arithmetic does not
     depend on the tile, and a TMA box holds the values the cell-by-cell loads
-    read (the larger 2D grids have tiles whose halo lies inside the grid, the
-    ones that load by TMA).  ws_autotune then keeps one of them and reports
+    read (the larger 2D and 3D grids have tiles whose halo lies inside the
+    grid, the ones that load by TMA).  ws_autotune then keeps one of them and reports
     it."""
     kind = "two_phase"
     case = wl.random_state(ndim, n, seed=23, kind=kind)
@@ -537,7 +537,7 @@ def test_stage_configs_bit_identical(ndim, n, bc):
     stream = torch.cuda.Stream()
     ref = None
     s = ws.Solver(ndim, case.n, case.dx, bcs, precision="mixed", stream=stream)
-    cands = list(range(12)) if ndim == 2 else list(range(4))
+    cands = list(range(12)) if ndim == 2 else list(range(8))
     with torch.cuda.stream(stream):
         U0 = s.prim_to_cons(s.tensor(case.Q))
         with pytest.raises(ws.WsError):
@@ -546,7 +546,7 @@ def test_stage_configs_bit_identical(ndim, n, bc):
             ws.ws_set_stage_config(s.ctx, k)
             cfg = ws.ws_get_stage_config(s.ctx)
             assert cfg["index"] == k and cfg["schedule"] == k % 2
-            assert cfg["tma"] == ((k // 2) % 2 if ndim == 2 else 0)
+            assert cfg["tma"] == (k // 2) % 2
             U = U0.clone()
             dts = [s.step(U, want_dt=True) for _ in range(3)]
             _, mask = s.mood(with_mask=True)
@@ -608,7 +608,8 @@ def test_resident_steps_bit_identical(n, bc, cfg):
         assert np.array_equal(ma, mb)
 
 
-@pytest.mark.parametrize("n,bc,cfg", [((37, 19, 17), "transmissive", 1), ((16, 20, 33), "periodic", 2)])
+@pytest.mark.parametrize("n,bc,cfg", [((37, 19, 17), "transmissive", 1), ((16, 20, 33), "periodic", 4),
+                                      ((72, 40, 12), "transmissive", 3), ((72, 40, 12), "periodic", 7)])
 def test_resident_steps_bit_identical_3d(n, bc, cfg):
     """The carried image in 3D: written by the second pass of stage 2, read by
     both passes of the next stage 0; bit-identical to ordinary steps."""
