@@ -80,7 +80,8 @@ def test_riemann_tubes_keep_clear_of_vacuum():
             sides.append(er.Side(rho, u, p, gamma, P / (G + 1.0)))
         L, R = sides
         floor = max(-L.pinf, -R.pinf)
-        gain = -(er._f(floor, L)[0] + er._f(floor, R)[0])
+        with np.errstate(divide="ignore"):  # the slope is infinite at the floor
+            gain = -(er._f(floor, L)[0] + er._f(floor, R)[0])
         assert R.u - L.u < 0.5 * gain, t
         ps, _ = er.star_state(L, R)
         assert ps > floor, t
