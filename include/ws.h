@@ -286,6 +286,11 @@ WS_API int ws_gate_stats(ws_ctx *ctx, double out[6]);
  *    a CTA owns and its thread count -- 32 x 15 cells on 512 threads (two CTAs
  *    per SM), 32 x 31 on 1024 (one CTA per SM; 2D only: with 7 fields its
  *    shared memory exceeds a CTA's limit) or 32 x 7 on 256 (four CTAs per SM)
+ *    -- or, 2D only, rows of 32 x 15 tiles closed by rows of 32 x 7 tiles,
+ *    both on 512 threads in one launch (the smaller closing CTAs even out the
+ *    end of the launch's last wave; the split is chosen for the GPU's SM
+ *    count by a list schedule of the launch's CTAs, 0.6 the cost of a full
+ *    one for a 32 x 7 CTA, and reported as tail_rows)
  *    -- the loads: 0 every CTA loads its tile and 3-cell halo cell by cell,
  *    applying the boundary conditions; 1 a CTA whose halo lies inside the
  *    grid loads the stage's FP32 image and increments as two TMA boxes (the
@@ -295,7 +300,8 @@ WS_API int ws_gate_stats(ws_ctx *ctx, double out[6]);
  *    dependent launch (the next launch's CTAs wait on the device for the
  *    previous grid instead of being launched after it); 1 the same launches
  *    without it.  Candidate index = 4 x tile + 2 x loads + schedule; tiles
- *    0, 1, 2 = 32 x 15, 32 x 31, 32 x 7 in 2D, 0, 1 = 32 x 15, 32 x 7 in 3D.
+ *    0, 1, 2, 3 = 32 x 15, 32 x 31, 32 x 7, 32 x 15 closed by 32 x 7 in 2D
+ *    (16 candidates), 0, 1 = 32 x 15, 32 x 7 in 3D (8 candidates).
  *    ws_get_stage_config reports the choice.
  *  - Batched tubes in mixed precision: the chunk of cells a CTA of the
  *    persistent stage kernel processes and its thread count, from (256, 128),
@@ -317,10 +323,13 @@ WS_API int ws_autotune(ws_ctx *ctx, const double *U, int steps, int *choice);
 WS_API int ws_set_stage_config(ws_ctx *ctx, int index);
 
 /* The fused stages' configuration (HOST outs, each nullable): candidate
- * index, tile width and height in cells, threads per CTA, schedule and loads
- * (0 or 1 each, as in ws_autotune).  WS_EINVAL without fused stages. */
+ * index, tile width and height in cells (of the first tile shape for 2D tile
+ * 3), threads per CTA, schedule and loads (0 or 1 each, as in ws_autotune),
+ * and tail_rows: for 2D tile 3 the number of 32 x 15 tile rows before the
+ * 32 x 7 rows (all the grid's tile rows when no split pays), otherwise -1.
+ * WS_EINVAL without fused stages. */
 WS_API int ws_get_stage_config(ws_ctx *ctx, int *index, int *tile_x, int *tile_y, int *threads, int *schedule,
-                               int *tma);
+                               int *tma, int *tail_rows);
 
 /* enable = 1 declares that U, the state of consecutive ws_step calls of this
  * context, changes between them only through those calls.  The fused 2D and

@@ -83,7 +83,7 @@ def load():
         "ws_set_graph": (ctypes.c_int, [vp, ctypes.c_int]),
         "ws_set_stage_config": (ctypes.c_int, [vp, ctypes.c_int]),
         "ws_set_resident": (ctypes.c_int, [vp, ctypes.c_int]),
-        "ws_get_stage_config": (ctypes.c_int, [vp] + [ctypes.POINTER(ctypes.c_int)] * 6),
+        "ws_get_stage_config": (ctypes.c_int, [vp] + [ctypes.POINTER(ctypes.c_int)] * 7),
         "ws_autotune": (ctypes.c_int, [vp, vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
         "ws_set_mlp": (ctypes.c_int, [vp, vp, ctypes.c_float, ctypes.c_int]),
         "ws_gate_eval": (ctypes.c_int, [vp, vp, vp]),
@@ -289,9 +289,9 @@ def ws_set_stage_config(ctx, index: int):
 
 
 def ws_get_stage_config(ctx) -> dict:
-    v = [ctypes.c_int(0) for _ in range(6)]
+    v = [ctypes.c_int(0) for _ in range(7)]
     _check(ctx, load().ws_get_stage_config(ctx, *[ctypes.byref(x) for x in v]))
-    return dict(zip(("index", "tile_x", "tile_y", "threads", "schedule", "tma"), (x.value for x in v)))
+    return dict(zip(("index", "tile_x", "tile_y", "threads", "schedule", "tma", "tail_rows"), (x.value for x in v)))
 
 
 def ws_set_graph(ctx, enable: bool):

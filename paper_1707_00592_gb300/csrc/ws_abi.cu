@@ -44,9 +44,12 @@ int check_launch(ws_ctx* c, const char* what) {
 void encode_maps(ws_ctx* c) {
   c->tmap_ok = 0;
   if (!c->fused) return;
+  const bool tail = c->gd.ndim == 2 && c->stage_tile == 3;
   const float* bufs[5] = {c->Ka, c->Kb, c->Q32, c->img[0], c->img[1]};
   for (int k = 0; k < 5; ++k)
-    if (bufs[k] && fused2d_encode_map(c->gd, c->stage_tile, bufs[k], &c->tmap[k])) c->tmap_ok |= 1u << k;
+    if (bufs[k] && fused2d_encode_map(c->gd, c->stage_tile, bufs[k], &c->tmap[k]) &&
+        (!tail || fused2d_encode_map(c->gd, 4, bufs[k], &c->tmap[5 + k])))
+      c->tmap_ok |= 1u << k;
 }
 
 // the descriptors of a launch's K and image buffers, or null (then every tile
@@ -57,6 +60,11 @@ const CUtensorMap* map_of(const ws_ctx* c, const float* buf) {
   for (int k = 0; k < 5; ++k)
     if (buf && bufs[k] == buf) return (c->tmap_ok >> k & 1u) ? &c->tmap[k] : nullptr;
   return nullptr;
+}
+
+// the descriptor of the closing rows' boxes (tile 3) beside map_of's
+const CUtensorMap* map2_of(const ws_ctx* c, const CUtensorMap* m) {
+  return m ? m + 5 : nullptr;
 }
 
 template <typename T>
@@ -302,7 +310,8 @@ int fused_run3(ws_ctx* c, double* U, double dt, const GateArgs* gate, const int*
       launch_stage2d(g, s, U, u32, Kin, Kout, dt, c->opts.cfl, lmax, c->dt_dev, mb + c->mask_off[0],
                      mb + c->mask_off[1], (float)c->opts.eps, c->opts.mood, c->opts.weights, nbad, gate, run_if,
                      census, c->stage_tile, c->stage_sched == 0, s == 0 && img_in, s == 2 ? img_out : nullptr, tmk,
-                     tmv, s == 2 ? clr0 : nullptr, s == 2 ? clr1 : nullptr, c->stream);
+                     tmv, s == 2 ? clr0 : nullptr, s == 2 ? clr1 : nullptr, c->tail_rows, map2_of(c, tmk),
+                     map2_of(c, tmv), c->stream);
     }
   }
   return check_launch(c, "fused stage");
@@ -1087,7 +1096,8 @@ int ws_gate_eval(ws_ctx* c, double* U, uint8_t* smooth) {
   c->img_cur = -1;
   launch_stage2d(c->gd, 3, U, c->Q32, c->Ka, c->Kb, 0.0, c->opts.cfl, c->lmax, c->dt_dev, smooth,
                  smooth + c->mask_off[1], (float)c->opts.eps, c->opts.mood, c->opts.weights, c->nbad, &ga, nullptr,
-                 nullptr, 0, false, false, nullptr, nullptr, nullptr, nullptr, nullptr, c->stream);
+                 nullptr, 0, false, false, nullptr, nullptr, nullptr, nullptr, nullptr, 0, nullptr, nullptr,
+                 c->stream);
   return check_launch(c, "gate eval");
 }
 
@@ -1116,6 +1126,12 @@ static void set_stage_config(ws_ctx* c, int index) {
   c->stage_tile = fused_tile_index(c->gd.ndim, index / (2 * nl));
   c->stage_tma = nl == 2 ? (index / 2) % 2 : 0;
   c->stage_sched = index % 2;
+  if (c->gd.ndim == 2 && c->stage_tile == 3) {  // two resident CTAs per SM
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    c->tail_rows = fused2d_tail_rows(c->gd, 2 * nsm);
+  }
   encode_maps(c);
   if (c->stage_tma && (c->tmap_ok & 0x7u) != 0x7u) c->stage_tma = 0;  // the driver refused a descriptor
   if (c->graph_exec) {
@@ -1247,7 +1263,8 @@ int ws_set_stage_config(ws_ctx* c, int index) {
   return WS_OK;
 }
 
-int ws_get_stage_config(ws_ctx* c, int* index, int* tile_x, int* tile_y, int* threads, int* schedule, int* tma) {
+int ws_get_stage_config(ws_ctx* c, int* index, int* tile_x, int* tile_y, int* threads, int* schedule, int* tma,
+                        int* tail_rows) {
   if (!c) return fail(c, WS_EINVAL, "null context");
   if (!c->fused) return fail(c, WS_EINVAL, "the context has no fused stage (2D/3D mixed precision)");
   if (index) *index = stage_config_index(c);
@@ -1256,6 +1273,7 @@ int ws_get_stage_config(ws_ctx* c, int* index, int* tile_x, int* tile_y, int* th
   if (threads) *threads = fused_tile_threads(c->stage_tile);
   if (schedule) *schedule = c->stage_sched;
   if (tma) *tma = c->stage_tma;
+  if (tail_rows) *tail_rows = c->gd.ndim == 2 && c->stage_tile == 3 ? c->tail_rows : -1;
   return WS_OK;
 }
 

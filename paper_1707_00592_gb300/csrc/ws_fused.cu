@@ -59,6 +59,11 @@
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <functional>
+#include <queue>
+#include <vector>
+
 #include <cuda_bf16.h>
 
 #include "face_fp32.cuh"
@@ -85,6 +90,7 @@ struct Tile {
 using TileA = Tile<32, 15, 512>;   // two CTAs per SM (the default)
 using TileB = Tile<32, 31, 1024>;  // one CTA per SM, 15 % fewer halo cells per cell
 using TileC = Tile<32, 7, 256>;    // four CTAs per SM
+using TileH = Tile<32, 7, 512>;    // the closing rows of a tail-filled launch (TileA's CTA size)
 
 // Per-pass constants.  NQ: fields (rho, velocities, E or p, Gamma, Pi), 6 in
 // 2D and 7 in 3D; the q tile holds them as primitives plus the sound speed.
@@ -199,6 +205,11 @@ struct StageArgs {
   int tma;
   alignas(64) CUtensorMap tm_k;
   alignas(64) CUtensorMap tm_v;
+  // a tail-filled 2D launch: tile rows of the first tile shape, and the
+  // descriptors of the closing rows' boxes
+  int rows_full;
+  alignas(64) CUtensorMap tm_k2;
+  alignas(64) CUtensorMap tm_v2;
   // nullable: slots block (0, 0, 0) clears once the previous grid has
   // completed (a step's last launch clears the next step's CFL maximum and
   // inadmissible-cell count, so consecutive steps need no memset between them)
@@ -514,8 +525,10 @@ __device__ __forceinline__ bool mbar_wait0(unsigned long long* bar, unsigned lim
   return false;
 }
 
-template <int GATE, int NQ_, int MODE, class TL>
-__global__ void __launch_bounds__(TL::NT, 1024 / TL::NT) k_stage(const __grid_constant__ StageArgs a) {  // 64 registers
+// One CTA's work: the tile in tile row `trow` of tiles TL starting at grid row
+// `ybase`.  MAP 1 takes the second pair of TMA descriptors (boxes of TL).
+template <int GATE, int NQ_, int MODE, class TL, int MAP>
+__device__ __forceinline__ void stage_body(const StageArgs& a, const int trow, const int ybase) {
   using T = Tr<NQ_, MODE, TL>;
   using SM = Smem<GATE, NQ_, MODE, TL>;
   constexpr int TX = TL::TX, TY = TL::TY, NT = TL::NT, NF = TL::NF, NMT = TL::NMT;
@@ -547,9 +560,8 @@ __global__ void __launch_bounds__(TL::NT, 1024 / TL::NT) k_stage(const __grid_co
   }
   const GridDev& g = a.g;
   const int nx = g.n[0], n1 = g.n[AX1];
-  const int trow = blockIdx.y + a.row0;  // tile row
   const int tile = trow * gridDim.x + blockIdx.x;
-  const int x0 = blockIdx.x * TX, y0 = trow * TY, plane = blockIdx.z;
+  const int x0 = blockIdx.x * TX, y0 = ybase + trow * TY, plane = blockIdx.z;
   const int64_t N = g.N, S1 = g.st[AX1];
   const int64_t pbase = (int64_t)(g.G[AXP] + plane) * g.st[AXP] + g.G[0];  // cell (x, a) at pbase + (G1 + a) S1 + x
   const int tid = threadIdx.x;
@@ -578,8 +590,8 @@ __global__ void __launch_bounds__(TL::NT, 1024 / TL::NT) k_stage(const __grid_co
     constexpr unsigned box = (unsigned)(NQ_ * T::HY * T::QP * sizeof(float));
     mbar_expect_tx(&S.mbar, a.stage == 0 ? box : 2 * box);
     if constexpr (MODE == 0) {
-      tma_load_3d(&S.q[0][0][0], &a.tm_v, x0, y0, 0, &S.mbar);
-      if (a.stage != 0) tma_load_3d(&S.fx[0][0][0], &a.tm_k, x0, y0, 0, &S.mbar);
+      tma_load_3d(&S.q[0][0][0], MAP ? &a.tm_v2 : &a.tm_v, x0, y0, 0, &S.mbar);
+      if (a.stage != 0) tma_load_3d(&S.fx[0][0][0], MAP ? &a.tm_k2 : &a.tm_k, x0, y0, 0, &S.mbar);
     } else {  // the tile's z plane
       tma_load_4d(&S.q[0][0][0], &a.tm_v, x0, y0, g.G[2] + plane, 0, &S.mbar);
       if (a.stage != 0) tma_load_4d(&S.fx[0][0][0], &a.tm_k, x0, y0, g.G[2] + plane, 0, &S.mbar);
@@ -1101,6 +1113,24 @@ __global__ void __launch_bounds__(TL::NT, 1024 / TL::NT) k_stage(const __grid_co
   }
 }
 
+template <int GATE, int NQ_, int MODE, class TL>
+__global__ void __launch_bounds__(TL::NT, 1024 / TL::NT) k_stage(const __grid_constant__ StageArgs a) {  // 64 registers
+  stage_body<GATE, NQ_, MODE, TL, 0>(a, blockIdx.y + a.row0, 0);
+}
+
+// A 2D stage whose first a.rows_full tile rows are tiles TL and whose closing
+// rows are the lower tiles TH of the same CTA size: a CTA of TH costs about
+// 0.6 of one of TL, so the launch's last wave of CTAs ends more evenly across
+// the SMs (the CTAs are scheduled in launch order, the TH rows last).
+template <int NQ_, class TL, class TH>
+__global__ void __launch_bounds__(TL::NT, 1024 / TL::NT) k_stage_tail(const __grid_constant__ StageArgs a) {
+  static_assert(TL::NT == TH::NT && TL::TX == TH::TX, "one CTA shape");
+  if ((int)blockIdx.y < a.rows_full)
+    stage_body<0, NQ_, 0, TL, 0>(a, blockIdx.y, 0);
+  else
+    stage_body<0, NQ_, 0, TH, 1>(a, blockIdx.y - a.rows_full, a.rows_full * TL::TY);
+}
+
 }  // namespace
 
 // After a gated step: decide on the device whether to redo it without the gate
@@ -1150,6 +1180,11 @@ constexpr int smem_of() {
   return (int)(sizeof(Smem<GATE, NQ, MODE, TL>) + ((GATE == 1 || GATE == 2) ? sizeof(SmemGate<TL>) : 0));
 }
 
+// the tail-filled 2D launch: room for either tile shape
+constexpr int tail_smem() {
+  return smem_of<0, 6, 0, TileA>() > smem_of<0, 6, 0, TileH>() ? smem_of<0, 6, 0, TileA>() : smem_of<0, 6, 0, TileH>();
+}
+
 template <int GATE, int NQ, int MODE, class TL>
 static cudaError_t allow_smem() {
   return cudaFuncSetAttribute(k_stage<GATE, NQ, MODE, TL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1164,7 +1199,59 @@ cudaError_t fused2d_prepare() {
       (e = allow_smem<3, 6, 0, TileA>()) || (e = allow_smem<0, 6, 0, TileB>()) || (e = allow_smem<3, 6, 0, TileB>()) ||
       (e = allow_smem<0, 6, 0, TileC>()) || (e = allow_smem<3, 6, 0, TileC>()))
     return e;
-  return cudaSuccess;
+  return cudaFuncSetAttribute(k_stage_tail<6, TileA, TileH>, cudaFuncAttributeMaxDynamicSharedMemorySize, tail_smem());
+}
+
+// Tile rows of a tail-filled 2D launch (tile 3): the number R of TileA rows,
+// the rest of the grid's rows in TileH rows, chosen by a list schedule of the
+// launch's CTAs, in launch order, on `slots` CTA slots.  A TileA CTA counts 1,
+// a TileH CTA 0.6 (per-CTA times measured on the shock-bubble: the load
+// latency is the same, the face work halves), a CTA of a partial row by the
+// fraction of its rows it holds.  R = all rows (no tail) when no split is
+// expected to end sooner.
+int fused2d_tail_rows(const GridDev& g, int slots) {
+  const int n1 = g.n[1], ncol = (g.n[0] + TileA::TX - 1) / TileA::TX;
+  const int rows = (n1 + TileA::TY - 1) / TileA::TY;
+  if (slots < 1) return rows;
+  std::vector<double> fin((size_t)slots);
+  auto makespan = [&](int R) {
+    std::fill(fin.begin(), fin.end(), 0.0);
+    std::priority_queue<double, std::vector<double>, std::greater<double>> q(fin.begin(), fin.end());
+    auto put = [&](double cost, int n) {
+      for (int k = 0; k < n; ++k) {
+        double t = q.top();
+        q.pop();
+        q.push(t + cost);
+      }
+    };
+    auto cost = [](double full, int held, int ty) { return full * (0.4 + 0.6 * held / ty); };
+    const int rem = n1 - R * TileA::TY;
+    if (rem <= 0) {  // TileA rows only, the last one possibly partial
+      put(1.0, ncol * (rows - 1));
+      put(cost(1.0, n1 - (rows - 1) * TileA::TY, TileA::TY), ncol);
+    } else {
+      const int H = (rem + TileH::TY - 1) / TileH::TY;
+      put(1.0, ncol * R);
+      put(0.6, ncol * (H - 1));
+      put(cost(0.6, rem - (H - 1) * TileH::TY, TileH::TY), ncol);
+    }
+    double m = 0.0;
+    while (!q.empty()) {
+      m = std::max(m, q.top());
+      q.pop();
+    }
+    return m;
+  };
+  int best = rows;
+  double bm = makespan(rows);
+  for (int R = rows - 1; R >= 0 && R >= rows - 64; --R) {
+    const double m = makespan(R);
+    if (m < bm * 0.999) {
+      bm = m;
+      best = R;
+    }
+  }
+  return best;
 }
 
 int64_t fused2d_gate_flag_bytes(const GridDev& g) {
@@ -1188,16 +1275,15 @@ cudaError_t fused3d_prepare() {
 // Launch with programmatic stream serialization (pdl): the stage's CTAs may
 // be scheduled before the previous kernel on the stream has finished and wait
 // in griddepcontrol.wait, which hides the launch latency between the stages.
-template <int GATE, int NQ, int MODE, class TL>
-static void launch_k(dim3 grid, bool pdl, cudaStream_t s, const StageArgs& a) {
-  constexpr int smem = smem_of<GATE, NQ, MODE, TL>();
+static void launch_kernel(void (*k)(StageArgs), int nt, int smem, dim3 grid, bool pdl, cudaStream_t s,
+                          const StageArgs& a) {
   if (!pdl) {
-    k_stage<GATE, NQ, MODE, TL><<<grid, TL::NT, smem, s>>>(a);
+    k<<<grid, nt, smem, s>>>(a);
     return;
   }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = grid;
-  cfg.blockDim = dim3(TL::NT);
+  cfg.blockDim = dim3(nt);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
@@ -1205,8 +1291,14 @@ static void launch_k(dim3 grid, bool pdl, cudaStream_t s, const StageArgs& a) {
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  cudaLaunchKernelEx(&cfg, k_stage<GATE, NQ, MODE, TL>, a);
+  cudaLaunchKernelEx(&cfg, k, a);
 }
+
+template <int GATE, int NQ, int MODE, class TL>
+static void launch_k(dim3 grid, bool pdl, cudaStream_t s, const StageArgs& a) {
+  launch_kernel(k_stage<GATE, NQ, MODE, TL>, TL::NT, smem_of<GATE, NQ, MODE, TL>(), grid, pdl, s, a);
+}
+
 
 template <class TL>
 static dim3 grid2d(const GridDev& g, int nrows = -1) {
@@ -1251,14 +1343,15 @@ static StageArgs stage_args(const GridDev& g, int stage, double* U, float* U32, 
   a.census = nullptr;
   a.img_in = 0;
   a.img_out = nullptr;
+  a.rows_full = 0;
   return a;
 }
 
 // The stage configurations ws_autotune chooses among: tile (0 TileA, 1 TileB,
-// 2 TileC) and whether consecutive stages are launched with programmatic
+// 2 TileC, 3 TileA rows closed by TileH rows) and whether consecutive stages are launched with programmatic
 // dependent launch.  3D launches take TileA or TileC (TileB's shared memory
 // exceeds a CTA's limit with 7 fields).
-int fused_num_tiles(int ndim) { return ndim == 3 ? 2 : 3; }
+int fused_num_tiles(int ndim) { return ndim == 3 ? 2 : 4; }
 int fused_tile_index(int ndim, int k) { return ndim == 3 ? (k == 0 ? 0 : 2) : k; }
 
 void launch_stage2d(const GridDev& g, int stage, double* U, float* U32, const float* Kin, float* Kout,
@@ -1266,7 +1359,8 @@ void launch_stage2d(const GridDev& g, int stage, double* U, float* U32, const fl
                     uint8_t* mask_y, float eps_rel, int mood, int weights, unsigned long long* nbad,
                     const GateArgs* gate, const int* run_if, unsigned long long* census, int tile, bool pdl,
                     bool img_in, float* img_out, const CUtensorMap* tmk, const CUtensorMap* tmv,
-                    unsigned long long* clear0, unsigned long long* clear1, cudaStream_t s) {
+                    unsigned long long* clear0, unsigned long long* clear1, int rows_full, const CUtensorMap* tmk2,
+                    const CUtensorMap* tmv2, cudaStream_t s) {
   StageArgs a = stage_args(g, stage, U, U32, Kin, Kout, dt_fixed, cfl, lmax, dt_out, eps_rel, mood, weights, nbad);
   a.clear0 = clear0;
   a.clear1 = clear1;
@@ -1303,6 +1397,21 @@ void launch_stage2d(const GridDev& g, int stage, double* U, float* U32, const fl
       case 2: launch_k<3, 6, 0, TileC>(grid2d<TileC>(g), false, s, a); break;
       default: launch_k<3, 6, 0, TileA>(grid2d<TileA>(g), false, s, a); break;
     }
+    return;
+  }
+  if (tile == 3 && rows_full >= 0 && rows_full * TileA::TY < g.n[1]) {
+    a.rows_full = rows_full;
+    if (a.tma) {
+      if (tmk2 && tmv2) {
+        a.tm_k2 = *tmk2;
+        a.tm_v2 = *tmv2;
+      } else {
+        a.tma = 0;
+      }
+    }
+    const int hrows = (g.n[1] - rows_full * TileA::TY + TileH::TY - 1) / TileH::TY;
+    launch_kernel(k_stage_tail<6, TileA, TileH>, TileA::NT, tail_smem(), dim3(grid2d<TileA>(g).x, rows_full + hrows),
+                  pdl, s, a);
     return;
   }
   switch (tile) {
@@ -1364,18 +1473,20 @@ bool fused2d_encode_map(const GridDev& g, int tile, const float* buf, CUtensorMa
   switch (tile) {
     case 1: return encode_map<TileB>(g, buf, out);
     case 2: return encode_map<TileC>(g, buf, out);
+    case 4: return g.ndim == 2 && encode_map<TileH>(g, buf, out);  // the closing rows of tile 3
     default: return encode_map<TileA>(g, buf, out);
   }
 }
 
+// tile 3 reports its first tile shape (the one its bands and gated launches use)
 int fused2d_tile_height(int tile) {
-  const int ty[3] = {TileA::TY, TileB::TY, TileC::TY};
-  return ty[tile >= 0 && tile < 3 ? tile : 0];
+  const int ty[4] = {TileA::TY, TileB::TY, TileC::TY, TileA::TY};
+  return ty[tile >= 0 && tile < 4 ? tile : 0];
 }
 
 int fused_tile_threads(int tile) {
-  const int nt[3] = {TileA::NT, TileB::NT, TileC::NT};
-  return nt[tile >= 0 && tile < 3 ? tile : 0];
+  const int nt[4] = {TileA::NT, TileB::NT, TileC::NT, TileA::NT};
+  return nt[tile >= 0 && tile < 4 ? tile : 0];
 }
 
 void launch_stage2d_band(const GridDev& g, int stage, double* U, float* U32, const float* Kin, float* Kout,

@@ -76,9 +76,11 @@ struct ws_ctx {
   unsigned long long* nbad_last = nullptr;
   bool capturing = false;       // a step is being captured into a graph (no chained slots)
   // fused 2D: TMA descriptors of Ka, Kb, Q32, img[0], img[1] for the current
-  // tile shape; tmap_ok bit k: descriptor k is valid
-  CUtensorMap tmap[5];
+  // tile shape, and [5..9] the same for the closing rows of tile 3; tmap_ok
+  // bit k: descriptors k (and k + 5 for tile 3) are valid
+  CUtensorMap tmap[10];
   unsigned tmap_ok = 0;
+  int tail_rows = 0;            // fused 2D, tile 3: tile rows of the first shape (fused2d_tail_rows)
   bool resident = false;        // fused 2D/3D: carry the FP32 image of U between steps (ws_set_resident)
   float* img[2] = {nullptr, nullptr};  // the two image buffers (one read by a step, one written)
   int img_cur = -1;             // image valid for the next step on img_U, or -1
@@ -181,11 +183,14 @@ struct GateArgs {
 int64_t fused2d_gate_flag_bytes(const GridDev& g);
 // plain 2D stage over the tile rows [row0, row0 + nrows) only
 // tile shapes of the fused stages (index 0, 1, 2: 32 x 15 cells per CTA of
-// 512 threads, 32 x 31 of 1024, 32 x 7 of 256); 3D takes 0 and 2
+// 512 threads, 32 x 31 of 1024, 32 x 7 of 256; 3, 2D only: rows of 32 x 15
+// closed by rows of 32 x 7, both on 512 threads); 3D takes 0 and 2
 int fused_num_tiles(int ndim);
 int fused_tile_index(int ndim, int k);
 int fused2d_tile_height(int tile);
 int fused_tile_threads(int tile);
+// tile 3: the number of 32 x 15 tile rows for `slots` resident CTAs
+int fused2d_tail_rows(const GridDev& g, int slots);
 
 void launch_stage2d_band(const GridDev& g, int stage, double* U, float* U32, const float* Kin, float* Kout,
                          double dt_fixed, double cfl, unsigned long long* lmax, double* dt_out, uint8_t* mask_x,
@@ -198,7 +203,10 @@ void launch_stage2d(const GridDev& g, int stage, double* U, float* U32, const fl
                     uint8_t* mask_y, float eps_rel, int mood, int weights, unsigned long long* nbad,
                     const GateArgs* gate, const int* run_if, unsigned long long* census, int tile, bool pdl,
                     bool img_in, float* img_out, const CUtensorMap* tmk, const CUtensorMap* tmv,
-                    unsigned long long* clear0, unsigned long long* clear1, cudaStream_t s);
+                    unsigned long long* clear0, unsigned long long* clear1, int rows_full, const CUtensorMap* tmk2,
+                    const CUtensorMap* tmv2, cudaStream_t s);
+// rows_full, tmk2, tmv2 (tile 3): the tile rows of the first shape and the
+// descriptors (tile code 4) of the closing rows' boxes
 // clear0, clear1 (nullable): device slots the launch sets to zero once the
 // previous grid has completed (before any of its CTAs reads them)
 // tmk, tmv (nullable, both or neither; plain and census launches): TMA
@@ -206,7 +214,8 @@ void launch_stage2d(const GridDev& g, int stage, double* U, float* U32, const fl
 // interior tiles then load both as boxes.
 // Describes an FP32 buffer of the fused 2D or 3D layout (g.st32, g.N32, g.nv
 // fields) with boxes of one tile's halo (of one z plane in 3D); false if the
-// driver refuses.  3D: tile 0 or 2 (the first pass's tiles).
+// driver refuses.  3D: tile 0 or 2 (the first pass's tiles); 2D: 0..3, and
+// 4 for the boxes of tile 3's closing rows.
 bool fused2d_encode_map(const GridDev& g, int tile, const float* buf, CUtensorMap* out);
 // census (nullable, without a gate): the same stage, also counting the
 // flat-stencil decisions into census[4] (face-variables, flat ones, warp

@@ -521,7 +521,8 @@ def test_run_host_unbanded_matches_device_steps(kind):
 
 @pytest.mark.parametrize("ndim,n,bc", [(2, (70, 47), "transmissive"), (2, (33, 65), "periodic"),
                                        (2, (40, 31), "reflective"), (2, (100, 64), "periodic"),
-                                       (2, (104, 50), "reflective"), (3, (37, 19, 17), "transmissive"),
+                                       (2, (104, 50), "reflective"), (2, (512, 300), "transmissive"),
+                                       (3, (37, 19, 17), "transmissive"),
                                        (3, (16, 20, 33), "periodic"), (3, (72, 40, 12), "reflective")])
 def test_stage_configs_bit_identical(ndim, n, bc):
     """Every fused-stage configuration ws_autotune chooses among (tile shape,
@@ -537,7 +538,7 @@ def test_stage_configs_bit_identical(ndim, n, bc):
     stream = torch.cuda.Stream()
     ref = None
     s = ws.Solver(ndim, case.n, case.dx, bcs, precision="mixed", stream=stream)
-    cands = list(range(12)) if ndim == 2 else list(range(8))
+    cands = list(range(16)) if ndim == 2 else list(range(8))
     with torch.cuda.stream(stream):
         U0 = s.prim_to_cons(s.tensor(case.Q))
         with pytest.raises(ws.WsError):
@@ -547,6 +548,11 @@ def test_stage_configs_bit_identical(ndim, n, bc):
             cfg = ws.ws_get_stage_config(s.ctx)
             assert cfg["index"] == k and cfg["schedule"] == k % 2
             assert cfg["tma"] == (k // 2) % 2
+            rows = -(-n[1] // 15)
+            if ndim == 2 and k >= 12:  # 32 x 15 rows closed by 32 x 7 rows
+                assert 0 <= cfg["tail_rows"] <= rows and cfg["tile_y"] == 15 and cfg["threads"] == 512
+            else:
+                assert cfg["tail_rows"] == -1
             U = U0.clone()
             dts = [s.step(U, want_dt=True) for _ in range(3)]
             _, mask = s.mood(with_mask=True)
