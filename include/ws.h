@@ -313,10 +313,10 @@ WS_API int ws_gate_stats(ws_ctx *ctx, double out[6]);
 WS_API int ws_autotune(ws_ctx *ctx, const double *U, int steps, int *choice);
 
 /* Sets the fused stages' configuration to candidate `index` of ws_autotune
- * (the default is 2 in 2D: 32 x 15 tiles, TMA loads, stage launches with
- * programmatic dependent launch -- 0 if the driver cannot describe the
- * buffers for TMA; 3 in 3D: 32 x 15 tiles, TMA loads, plain launches -- 1
- * without TMA).  A TMA candidate
+ * (the default is 14 in 2D: 32 x 15 tile rows closed by 32 x 7 rows, TMA
+ * loads, stage launches with programmatic dependent launch -- 12 if the
+ * driver cannot describe the buffers for TMA; 3 in 3D: 32 x 15 tiles, TMA
+ * loads, plain launches -- 1 without TMA).  A TMA candidate
  * falls back to cell-by-cell loads when the driver refuses a descriptor
  * (ws_get_stage_config then reports loads 0).  WS_EINVAL on a context without
  * fused stages or an index that is not a candidate. */

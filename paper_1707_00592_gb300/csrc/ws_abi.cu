@@ -39,6 +39,15 @@ int check_launch(ws_ctx* c, const char* what) {
   return WS_OK;
 }
 
+// fused 2D, tile 3: the split of the grid's tile rows for this GPU (two
+// resident CTAs per SM)
+static void set_tail_rows(ws_ctx* c) {
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  c->tail_rows = fused2d_tail_rows(c->gd, 2 * nsm);
+}
+
 // fused 2D and 3D: TMA descriptors of the FP32 buffers for the current tile
 // shape (3D: of the first pass)
 void encode_maps(ws_ctx* c) {
@@ -503,6 +512,8 @@ int ws_init(const ws_grid* grid, const ws_opts* opts, void* stream, ws_ctx** out
           goto bad;
         }
         c->fused = true;
+        c->stage_tile = 3;  // 32 x 15 tile rows closed by 32 x 7 rows
+        set_tail_rows(c);
         encode_maps(c);
         c->stage_tma = c->tmap_ok == 0x7u ? 1 : 0;
       }
@@ -1126,12 +1137,7 @@ static void set_stage_config(ws_ctx* c, int index) {
   c->stage_tile = fused_tile_index(c->gd.ndim, index / (2 * nl));
   c->stage_tma = nl == 2 ? (index / 2) % 2 : 0;
   c->stage_sched = index % 2;
-  if (c->gd.ndim == 2 && c->stage_tile == 3) {  // two resident CTAs per SM
-    int dev = 0, nsm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    c->tail_rows = fused2d_tail_rows(c->gd, 2 * nsm);
-  }
+  if (c->gd.ndim == 2 && c->stage_tile == 3) set_tail_rows(c);
   encode_maps(c);
   if (c->stage_tma && (c->tmap_ok & 0x7u) != 0x7u) c->stage_tma = 0;  // the driver refused a descriptor
   if (c->graph_exec) {
