@@ -902,7 +902,7 @@ def main():
     ap.add_argument("--drop-l1-n", type=int, default=128)
     ap.add_argument("--drop-l1-steps", type=int, default=500)
     ap.add_argument("--setup-steps", type=int, default=10)
-    ap.add_argument("--autotune", type=int, default=3, help="steps per candidate of ws_autotune (0: default)")
+    ap.add_argument("--autotune", type=int, default=10, help="steps per candidate of ws_autotune (0: default)")
     ap.add_argument("--resident", type=int, default=1, help="carry the FP32 image between steps (ws_set_resident)")
     ap.add_argument("--learned", type=int, default=1)
     ap.add_argument("--learned-n", type=int, default=2048)

@@ -280,7 +280,8 @@ WS_API int ws_gate_stats(ws_ctx *ctx, double out[6]);
 
 /* Chooses the kernel configuration of the context by timing each candidate
  * for `steps` CFL steps (after one warm-up step) on a scratch copy of U
- * (DEVICE; U itself is not modified).  Every candidate gives bit-identical
+ * (DEVICE; U itself is not modified), in two rounds over the candidates; a
+ * candidate's time is its faster round.  Every candidate gives bit-identical
  * results; only the time differs.
  *  - Fused 2D/3D mixed-precision stages (learned gate off): the tile of cells
  *    a CTA owns and its thread count -- 32 x 15 cells on 512 threads (two CTAs
