@@ -510,19 +510,28 @@ __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, i
       "l"(map), "r"(x), "r"(y), "r"(z), "r"(f), "r"(b)
       : "memory");
 }
-// Waits for phase 0 of the barrier, at most `limit` polls; false if it gave up.
-__device__ __forceinline__ bool mbar_wait0(unsigned long long* bar, unsigned limit) {
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Waits for phase 0 of the barrier, at most `limit_ns` nanoseconds; false if
+// it gave up.  Each try suspends the thread until the phase completes or up
+// to a millisecond passes, so waiting warps issue nothing meanwhile (a plain
+// poll would take issue slots from the co-resident CTA).
+__device__ __forceinline__ bool mbar_wait0(unsigned long long* bar, unsigned long long limit_ns) {
   unsigned b = (unsigned)__cvta_generic_to_shared(bar);
-  for (unsigned k = 0; k < limit; ++k) {
+  const unsigned long long t0 = global_ns();
+  for (;;) {
     unsigned ok;
     asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}\n"
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0, %2;\n selp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(ok)
-        : "r"(b)
+        : "r"(b), "r"(1000000u)
         : "memory");
     if (ok) return true;
+    if (global_ns() - t0 > limit_ns) return false;
   }
-  return false;
 }
 
 // One CTA's work: the tile in tile row `trow` of tiles TL starting at grid row
@@ -640,118 +649,40 @@ __device__ __forceinline__ void stage_body(const StageArgs& a, const int trow, c
   }
 
   // ---- phase A: stage-state primitives of tile + halo ----
-  // A thread owns up to HPT q-tile cells; all their global loads are issued
-  // before any of them is used, so that a CTA has its whole halo in flight.
-  // A TMA tile (above) reads both from shared memory once its boxes land.
+  // A TMA tile (above) reads image and K from shared memory once its boxes
+  // land and takes its cells one at a time.  Otherwise a thread owns up to HPT
+  // q-tile cells and issues all their global loads before any of them is
+  // used, so that a CTA has its whole halo in flight.
   {
-    float ld[T::HPT][NQ];
-    float rk[T::HPT][NQ], rv[T::HPT][NQ];  // stages 1, 2: increment and FP32 image as loaded
-    int hh[T::HPT];
-    bool flx[T::HPT], fla[T::HPT], own[T::HPT];
-    if (tma) {
-      // a copy that never lands is reported as an impossible count of
-      // inadmissible cells (the results of the launch are then void)
-      if (!mbar_wait0(&S.mbar, 1u << 24) && (tid & 31) == 0) atomicAdd(a.nbad, 1ULL << 40);
-      const float* kst = &S.fx[0][0][0];  // K of tile and halo, [field][row][column] like q
+    // stages 1, 2: the stage state from the image and the increments (E - Pi
+    // with Pi's increment); the own cells' values are kept for phase C
+    auto stage_state = [&](float (&ld)[NQ], const float (&rk)[NQ], const float (&rv)[NQ], int hy, int hx,
+                           bool ownc) {
 #pragma unroll
-      for (int t = 0; t < T::HPT; ++t) {
-        int h = tid + t * NT;
-        int hy = h / T::QW, hx = h - hy * T::QW;
-        hh[t] = h < T::NH ? h : -1;
-        flx[t] = fla[t] = false;
-        own[t] = hx >= T::QX && hx < T::QX + TX && hy >= NG && hy < NG + TY;
-        if (h >= T::NH) continue;
+      for (int m = 0; m < NQ; ++m) {
+        if (m == NQ - 3)
+          ld[m] = fmaf(coef, rk[m] - rk[NQ - 1], rv[m]);
+        else
+          ld[m] = fmaf(coef, rk[m], rv[m]);
+      }
+      if (CACHE && ownc) {  // phase C reads these instead of global memory
+        const int j = hy - NG, i = hx - T::QX;
 #pragma unroll
         for (int m = 0; m < NQ; ++m) {
-          rv[t][m] = S.q[m][hy][hx];
-          if (a.stage == 0)
-            ld[t][m] = rv[t][m];
-          else
-            rk[t][m] = kst[(m * T::HY + hy) * T::QP + hx];
+          S.own.k[m][j][i] = rk[m];
+          if (a.stage == 2) S.own.v[m][j][i] = rv[m];
         }
       }
-    } else {
-#pragma unroll
-    for (int t = 0; t < T::HPT; ++t) {
-      int h = tid + t * NT;
-      int hy = h / T::QW, hx = h - hy * T::QW;
-      int gx = x0 + hx - T::QX, ga = y0 + hy - NG;
-      bool outx = gx < 0 || gx >= nx, outa = ga < 0 || ga >= n1;
-      // corners are never read, nor (without x faces) columns past the grid
-      bool skip = h >= T::NH || (outx && outa) || (!T::XF && outx);
-      hh[t] = skip ? -1 : h;
-      if (skip) continue;
-      bool fx = false, fa = false;
-      int mx = map_bc(gx, nx, g.bc[0][0], g.bc[0][1], fx);
-      int ma = map_bc(ga, n1, g.bc[AX1][0], g.bc[AX1][1], fa);
-      flx[t] = fx;
-      fla[t] = fa;
-      own[t] = hx >= T::QX && hx < T::QX + TX && hy >= NG && hy < NG + TY && !outx && !outa;
-      if (a.stage == 0 && a.img_in) {  // the image the previous step's stage 2 left
-        const int64_t i32 = idx32(ma, mx);
-#pragma unroll
-        for (int m = 0; m < NQ; ++m) ld[t][m] = __ldg(&a.U32[m * N32 + i32]);
-      } else if (a.stage == 0 || a.stage == 3) {
-        const int64_t i = pbase + (int64_t)(g.G[AX1] + ma) * S1 + mx;  // FP64 state
-        const double* U = a.U;
-#pragma unroll
-        for (int m = 0; m < NQ; ++m) {
-          if (m == NQ - 3)
-            ld[t][m] = f64_to_f32(U[m * N + i] - U[(NQ - 1) * N + i]);  // E - Pi in FP64
-          else
-            ld[t][m] = f64_to_f32(U[m * N + i]);
-        }
-        if (a.stage == 0 && MODE != 2 && own[t]) {
-          if (LEARNED) {
-#pragma unroll
-            for (int m = 0; m < NQ; ++m) a.Ubackup[m * N + i] = U[m * N + i];
-          }
-          const int64_t i32 = idx32(ma, mx);
-#pragma unroll
-          for (int m = 0; m < NQ; ++m) a.U32[m * N32 + i32] = ld[t][m];
-        }
-      } else {
-        const int64_t i32 = idx32(ma, mx);
-#pragma unroll
-        for (int m = 0; m < NQ; ++m) {
-          rk[t][m] = __ldg(&a.Kin[m * N32 + i32]);
-          rv[t][m] = __ldg(&a.U32[m * N32 + i32]);
-        }
-      }
-    }
-    }
-    if (a.stage == 1 || a.stage == 2) {
-#pragma unroll
-      for (int t = 0; t < T::HPT; ++t) {
-        if (hh[t] < 0) continue;
-#pragma unroll
-        for (int m = 0; m < NQ; ++m) {
-          if (m == NQ - 3)
-            ld[t][m] = fmaf(coef, rk[t][m] - rk[t][NQ - 1], rv[t][m]);
-          else
-            ld[t][m] = fmaf(coef, rk[t][m], rv[t][m]);
-        }
-        if (CACHE && own[t]) {  // phase C reads these instead of global memory
-          int j = hh[t] / T::QW - NG, i = hh[t] % T::QW - T::QX;
-#pragma unroll
-          for (int m = 0; m < NQ; ++m) {
-            S.own.k[m][j][i] = rk[t][m];
-            if (a.stage == 2) S.own.v[m][j][i] = rv[t][m];
-          }
-        }
-      }
-    }
-#pragma unroll
-    for (int t = 0; t < T::HPT; ++t) {
-      if (hh[t] < 0) continue;
-      int hy = hh[t] / T::QW, hx = hh[t] - hy * T::QW;
-      float rho = ld[t][0], eint = ld[t][NQ - 3], Gam = ld[t][NQ - 2], Pi = ld[t][NQ - 1];
+    };
+    // primitives and sound speed into the q tile; stage 0: the CFL rate
+    auto primitives = [&](const float (&ld)[NQ], int hy, int hx, bool fx, bool fa, bool ownc) {
+      float rho = ld[0], eint = ld[NQ - 3], Gam = ld[NQ - 2], Pi = ld[NQ - 1];
       float irho = frcp(rho);
       float vel[ND];
 #pragma unroll
-      for (int d = 0; d < ND; ++d) vel[d] = ld[t][1 + d] * irho;
-      if (flx[t]) vel[0] = -vel[0];
-      if (fla[t]) vel[AX1] = -vel[AX1];
+      for (int d = 0; d < ND; ++d) vel[d] = ld[1 + d] * irho;
+      if (fx) vel[0] = -vel[0];
+      if (fa) vel[AX1] = -vel[AX1];
       float ksq = ND == 2 ? fmaf(vel[0], vel[0], vel[1] * vel[1])
                           : fmaf(vel[0], vel[0], fmaf(vel[1], vel[1], vel[ND - 1] * vel[ND - 1]));
       float p = fmaf(-0.5f * rho, ksq, eint) * frcp(Gam);
@@ -763,10 +694,97 @@ __device__ __forceinline__ void stage_body(const StageArgs& a, const int trow, c
       S.q[T::IPI][hy][hx] = Pi;
       float c = fsqrt(sound_speed2(rho, p, Gam, Pi));
       S.q[T::IC][hy][hx] = c;
-      if (a.stage == 0 && MODE != 2 && own[t]) {
+      if (a.stage == 0 && MODE != 2 && ownc) {
         float lam = fmaf(fabsf(vel[0]) + c, a.idx, (fabsf(vel[1]) + c) * a.idy);
         if (ND == 3) lam = fmaf(fabsf(vel[ND - 1]) + c, a.idz, lam);
         if (!(lam <= lam_max)) lam_max = lam;  // NaN propagates
+      }
+    };
+    if (tma) {
+      // a copy that never lands is reported as an impossible count of
+      // inadmissible cells (the results of the launch are then void)
+      if (!mbar_wait0(&S.mbar, 1000000000ULL) && (tid & 31) == 0) atomicAdd(a.nbad, 1ULL << 40);
+      const float* kst = &S.fx[0][0][0];  // K of tile and halo, [field][row][column] like q
+#pragma unroll
+      for (int t = 0; t < T::HPT; ++t) {
+        const int h = tid + t * NT;
+        if (h >= T::NH) continue;
+        const int hy = h / T::QW, hx = h - hy * T::QW;
+        const bool ownc = hx >= T::QX && hx < T::QX + TX && hy >= NG && hy < NG + TY;
+        float ld[NQ];
+        if (a.stage == 0) {
+#pragma unroll
+          for (int m = 0; m < NQ; ++m) ld[m] = S.q[m][hy][hx];
+        } else {
+          float rk[NQ], rv[NQ];
+#pragma unroll
+          for (int m = 0; m < NQ; ++m) {
+            rv[m] = S.q[m][hy][hx];
+            rk[m] = kst[(m * T::HY + hy) * T::QP + hx];
+          }
+          stage_state(ld, rk, rv, hy, hx, ownc);
+        }
+        primitives(ld, hy, hx, false, false, ownc);
+      }
+    } else {
+      float ld[T::HPT][NQ];
+      float rk[T::HPT][NQ], rv[T::HPT][NQ];  // stages 1, 2: increment and FP32 image as loaded
+      int hh[T::HPT];
+      bool flx[T::HPT], fla[T::HPT], own[T::HPT];
+#pragma unroll
+      for (int t = 0; t < T::HPT; ++t) {
+        int h = tid + t * NT;
+        int hy = h / T::QW, hx = h - hy * T::QW;
+        int gx = x0 + hx - T::QX, ga = y0 + hy - NG;
+        bool outx = gx < 0 || gx >= nx, outa = ga < 0 || ga >= n1;
+        // corners are never read, nor (without x faces) columns past the grid
+        bool skip = h >= T::NH || (outx && outa) || (!T::XF && outx);
+        hh[t] = skip ? -1 : h;
+        if (skip) continue;
+        bool fx = false, fa = false;
+        int mx = map_bc(gx, nx, g.bc[0][0], g.bc[0][1], fx);
+        int ma = map_bc(ga, n1, g.bc[AX1][0], g.bc[AX1][1], fa);
+        flx[t] = fx;
+        fla[t] = fa;
+        own[t] = hx >= T::QX && hx < T::QX + TX && hy >= NG && hy < NG + TY && !outx && !outa;
+        if (a.stage == 0 && a.img_in) {  // the image the previous step's stage 2 left
+          const int64_t i32 = idx32(ma, mx);
+#pragma unroll
+          for (int m = 0; m < NQ; ++m) ld[t][m] = __ldg(&a.U32[m * N32 + i32]);
+        } else if (a.stage == 0 || a.stage == 3) {
+          const int64_t i = pbase + (int64_t)(g.G[AX1] + ma) * S1 + mx;  // FP64 state
+          const double* U = a.U;
+#pragma unroll
+          for (int m = 0; m < NQ; ++m) {
+            if (m == NQ - 3)
+              ld[t][m] = f64_to_f32(U[m * N + i] - U[(NQ - 1) * N + i]);  // E - Pi in FP64
+            else
+              ld[t][m] = f64_to_f32(U[m * N + i]);
+          }
+          if (a.stage == 0 && MODE != 2 && own[t]) {
+            if (LEARNED) {
+#pragma unroll
+              for (int m = 0; m < NQ; ++m) a.Ubackup[m * N + i] = U[m * N + i];
+            }
+            const int64_t i32 = idx32(ma, mx);
+#pragma unroll
+            for (int m = 0; m < NQ; ++m) a.U32[m * N32 + i32] = ld[t][m];
+          }
+        } else {
+          const int64_t i32 = idx32(ma, mx);
+#pragma unroll
+          for (int m = 0; m < NQ; ++m) {
+            rk[t][m] = __ldg(&a.Kin[m * N32 + i32]);
+            rv[t][m] = __ldg(&a.U32[m * N32 + i32]);
+          }
+        }
+      }
+#pragma unroll
+      for (int t = 0; t < T::HPT; ++t) {
+        if (hh[t] < 0) continue;
+        const int hy = hh[t] / T::QW, hx = hh[t] - hy * T::QW;
+        if (a.stage == 1 || a.stage == 2) stage_state(ld[t], rk[t], rv[t], hy, hx, own[t]);
+        primitives(ld[t], hy, hx, flx[t], fla[t], own[t]);
       }
     }
   }
