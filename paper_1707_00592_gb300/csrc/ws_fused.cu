@@ -589,8 +589,7 @@ __device__ __forceinline__ void stage_body(const StageArgs& a, const int trow, c
   // A tile of the 2D stage or of the first 3D pass whose halo lies inside the
   // grid, in a stage that reads the FP32 image (and K), takes both as TMA
   // boxes: no boundary mapping, one instruction per array.  They are issued
-  // first thing and land while the CTA sets up; the barrier below publishes
-  // the mbarrier to all threads.
+  // first thing and land while the CTA sets up.
   const bool tma = MODE != 2 && a.tma && (a.stage == 1 || a.stage == 2 || (a.stage == 0 && a.img_in)) &&
                    x0 >= NG && x0 + TX + NG <= nx && y0 >= NG && y0 + TY + NG <= n1;
   if (tma && tid == 0) {
@@ -606,12 +605,18 @@ __device__ __forceinline__ void stage_body(const StageArgs& a, const int trow, c
       if (a.stage != 0) tma_load_4d(&S.fx[0][0][0], &a.tm_k, x0, y0, g.G[2] + plane, 0, &S.mbar);
     }
   }
-  if (tma && a.stage == 0) __syncthreads();
-  if (a.stage == 1 || a.stage == 2) {
-    if (tid == 0) {  // one FP64 division per CTA
-      double d = a.dt_fixed > 0.0 ? a.dt_fixed : (double)a.cfl / __longlong_as_double((long long)*a.lmax);
-      if (a.stage == 1 && MODE != 2 && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0) *a.dt_out = d;
-      S.dt = f64_to_f32(d);
+  if (a.stage == 1 || a.stage == 2 || tma) {
+    if (tid == 0) {
+      if (a.stage == 1 || a.stage == 2) {  // one FP64 division per CTA
+        double d = a.dt_fixed > 0.0 ? a.dt_fixed : (double)a.cfl / __longlong_as_double((long long)*a.lmax);
+        if (a.stage == 1 && MODE != 2 && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0) *a.dt_out = d;
+        S.dt = f64_to_f32(d);
+      }
+      // The boxes: this thread, which set the mbarrier up, waits for them; the
+      // other warps wait at the barrier below, where they issue nothing.  A
+      // copy that never lands is reported as an impossible count of
+      // inadmissible cells (the results of the launch are then void).
+      if (tma && !mbar_wait0(&S.mbar, 1000000000ULL)) atomicAdd(a.nbad, 1ULL << 40);
     }
     __syncthreads();
   }
@@ -700,10 +705,7 @@ __device__ __forceinline__ void stage_body(const StageArgs& a, const int trow, c
         if (!(lam <= lam_max)) lam_max = lam;  // NaN propagates
       }
     };
-    if (tma) {
-      // a copy that never lands is reported as an impossible count of
-      // inadmissible cells (the results of the launch are then void)
-      if (!mbar_wait0(&S.mbar, 1000000000ULL) && (tid & 31) == 0) atomicAdd(a.nbad, 1ULL << 40);
+    if (tma) {  // the boxes have landed (barrier above)
       const float* kst = &S.fx[0][0][0];  // K of tile and halo, [field][row][column] like q
 #pragma unroll
       for (int t = 0; t < T::HPT; ++t) {
