@@ -109,11 +109,11 @@ def cell_update_bytes(ndim: int) -> int:
 # DRAM bytes moved by one launch of the fused 2D mixed stage on the 1024^2
 # shock-bubble, in the default tail-filled configuration (ncu, one resident
 # step at step 10 of a 60-step run): stage 0 reads the carried FP32 image
-# (25.48 MB read, 0.03 MB written), stage 1 the image and K0 (50.85 + 0.47 MB),
-# stage 2 also the FP64 state it updates (101.59 + 24.93 MB; the rest of its
+# (25.49 MB read, 0.03 MB written), stage 1 the image and K0 (50.86 + 0.46 MB),
+# stage 2 also the FP64 state it updates (101.59 + 24.63 MB; the rest of its
 # writes are still in L2 at the end); the mean over the three launches (the
 # 32 x 15-only configuration moves 67.5 MB)
-STAGE2D_DRAM_BYTES = (25.510656 + 51.328000 + 126.517248) / 3 * 1e6
+STAGE2D_DRAM_BYTES = (25.513728 + 51.326464 + 126.210816) / 3 * 1e6
 STAGE2D_DRAM_SOURCE = ("dram__bytes_read.sum + dram__bytes_write.sum per fused-stage launch, mean of the three "
                        "stages of one resident step (1024^2, step 10 of 60; ncu)")
 
