@@ -554,6 +554,8 @@ __device__ __forceinline__ void stage_body(const StageArgs& a, const int trow, c
                               offsetof(SM, fy) == offsetof(SM, fx) + sizeof(S.fx)),
                 "the K box does not fit the flux arrays");
   static_assert(T::QP * sizeof(float) % 16 == 0, "TMA box rows are multiples of 16 bytes");
+  static_assert(offsetof(SM, q) % 128 == 0 && offsetof(SM, fx) % 128 == 0,
+                "TMA destinations start on 128-byte boundaries");
   SmemGate<TL>& SG = *reinterpret_cast<SmemGate<TL>*>(smem_raw + sizeof(SM));
   // Launched with programmatic stream serialization (the plain 2D stage), a
   // CTA may become resident while the previous stage is still finishing: it
