@@ -53,11 +53,12 @@ static void set_tail_rows(ws_ctx* c) {
 void encode_maps(ws_ctx* c) {
   c->tmap_ok = 0;
   if (!c->fused) return;
-  const bool tail = c->gd.ndim == 2 && c->stage_tile == 3;
+  // second descriptors: the closing rows of 2D tile 3, the second 3D pass
+  const int code2 = c->gd.ndim == 3 ? (c->stage_tile == 2 ? 7 : 6) : (c->stage_tile == 3 ? 4 : -1);
   const float* bufs[5] = {c->Ka, c->Kb, c->Q32, c->img[0], c->img[1]};
   for (int k = 0; k < 5; ++k)
     if (bufs[k] && fused2d_encode_map(c->gd, c->stage_tile, bufs[k], &c->tmap[k]) &&
-        (!tail || fused2d_encode_map(c->gd, 4, bufs[k], &c->tmap[5 + k])))
+        (code2 < 0 || fused2d_encode_map(c->gd, code2, bufs[k], &c->tmap[5 + k])))
       c->tmap_ok |= 1u << k;
 }
 
@@ -312,7 +313,8 @@ int fused_run3(ws_ctx* c, double* U, double dt, const GateArgs* gate, const int*
       launch_stage3d(g, s, U, u32, Kin, Kout, c->Lp, dt, c->opts.cfl, lmax, c->dt_dev, mb + c->mask_off[0],
                      mb + c->mask_off[1], mb + c->mask_off[2], (float)c->opts.eps, c->opts.mood, c->opts.weights, nbad,
                      census, c->stage_tile, c->stage_sched == 0, s == 0 && img_in, s == 2 ? img_out : nullptr,
-                     s == 2 ? clr0 : nullptr, s == 2 ? clr1 : nullptr, tmk, tmv, c->stream);
+                     s == 2 ? clr0 : nullptr, s == 2 ? clr1 : nullptr, tmk, tmv, map2_of(c, tmk), map2_of(c, tmv),
+                     c->stream);
     } else {
       const CUtensorMap *tmk = map_of(c, Kin), *tmv = map_of(c, u32);
       if (!tmk || !tmv) tmk = tmv = nullptr;

@@ -102,9 +102,10 @@ struct Tr {
   static constexpr int ND = NQ - 4;                 // velocity components
   static constexpr int NTG = NQ - 5;                // tangential components at a face
   static constexpr bool XF = MODE != 2;             // the pass has x faces (and an x halo)
-  static constexpr int QW = XF ? HX : TX;           // row width of the q tile
-  static constexpr int QP = XF ? TL::HXP : TX;      // row pitch of the q tile
-  static constexpr int QX = XF ? NG : 0;            // q column of the tile's first cell
+  static constexpr int QW = XF ? HX : TX;           // cells of a q row that phase A fills
+  static constexpr int QP = TL::HXP;                // row pitch of the q tile (a TMA box row)
+  static constexpr int QX = NG;                     // q column of the tile's first cell
+  static constexpr int QL = XF ? 0 : NG;            // q column of the first cell phase A fills
   static constexpr int NH = QW * HY;                // q tile cells
   static constexpr int FS = QP * HY;                // field stride in the q tile
   static constexpr int NFP = (XF ? NFX : 0) + NFY;  // faces of the pass
@@ -132,15 +133,19 @@ struct Smem {
   // fy first receive the increments K of tile and halo (read in phase A)
   alignas(128) float fx[T::XF ? NQ_ + 1 : 1][TY][TX + 1];
   float fy[NQ_ + 1][TY + 1][TX];              // fluxes + face velocity of the faces along the tile's 2nd axis
-  union {
+  static constexpr bool OWNV = CACHE && MODE != 2;  // the own cells' image kept (the second 3D pass reads it)
+  union alignas(128) {
     struct {                                     // this tile's own cells, for phase C
-      double u[CACHE ? NQ_ : 1][TY][TX];         // stage 2: FP64 state, copied in asynchronously from the start
+      double u[CACHE ? NQ_ : 1][TY][TX];         // stage 2: FP64 state, copied in asynchronously
       float k[CACHE ? NQ_ : 1][TY][TX];          // stages 1, 2: accumulated increments (kept from the phase-A loads)
-      float v[CACHE ? NQ_ : 1][TY][TX];          // stage 2: FP32 image of U^n (kept from the phase-A loads)
+      float v[OWNV ? NQ_ : 1][TY][TX];           // stage 2: FP32 image of U^n (kept from the phase-A loads)
       // 3D second pass: x + y part of the divergence (asynchronous copy)
       float l[MODE == 2 ? NQ_ : 1][MODE == 2 ? TY : 1][MODE == 2 ? TX : 1];
     } own;
     __nv_bfloat16 feat[GATE == 1 ? NF : 1][24];  // gate inputs (read before the reconstruction)
+    // 3D second pass, TMA load: the increments K of tile and z halo, read in
+    // phase A before the own cells' arrays are filled
+    float kbox[MODE == 2 ? NQ_ : 1][MODE == 2 ? HY : 1][MODE == 2 ? T::QP : 1];
   };
   unsigned long long red[NT / 32];  // per-warp CFL maxima
   unsigned long long mbar;          // completion of the TMA loads
@@ -153,6 +158,14 @@ struct Smem {
 // of 60 (measured: 10 % slower per-thread loads).
 static_assert(2 * (sizeof(Smem<0, 6, 0, Tile<32, 15, 512>>) + 1024) <= 196 * 1024,
               "the default 2D stage no longer leaves room for L1");
+// The 3D passes keep their CTAs per SM: four of 32 x 7 cells, two of 32 x 15
+// (228 KiB of shared memory per SM at most).
+static_assert(4 * (sizeof(Smem<0, 7, 2, Tile<32, 7, 256>>) + 1024) <= 228 * 1024 &&
+                  4 * (sizeof(Smem<0, 7, 1, Tile<32, 7, 256>>) + 1024) <= 228 * 1024,
+              "a 32 x 7 3D pass no longer fits four CTAs per SM");
+static_assert(2 * (sizeof(Smem<0, 7, 2, Tile<32, 15, 512>>) + 1024) <= 228 * 1024 &&
+                  2 * (sizeof(Smem<0, 7, 1, Tile<32, 15, 512>>) + 1024) <= 228 * 1024,
+              "a 32 x 15 3D pass no longer fits two CTAs per SM");
 
 template <class TL>
 struct SmemGate {
@@ -261,7 +274,7 @@ __device__ __forceinline__ bool face_geom(int f, int x0, int y0, int nx, int n1,
   int ff = XF ? f - TX * TY : f;
   int j = ff / TX, i = ff - j * TX;
   isx = false;
-  hx = i + (XF ? NG : 0);
+  hx = i + NG;
   hy = j;  // cell k at row hy + k
   return (x0 + i < nx) && (y0 + j - 1 <= n1 - 1);
 }
@@ -554,7 +567,7 @@ __device__ __forceinline__ void stage_body(const StageArgs& a, const int trow, c
                               offsetof(SM, fy) == offsetof(SM, fx) + sizeof(S.fx)),
                 "the K box does not fit the flux arrays");
   static_assert(T::QP * sizeof(float) % 16 == 0, "TMA box rows are multiples of 16 bytes");
-  static_assert(offsetof(SM, q) % 128 == 0 && offsetof(SM, fx) % 128 == 0,
+  static_assert(offsetof(SM, q) % 128 == 0 && offsetof(SM, fx) % 128 == 0 && offsetof(SM, kbox) % 128 == 0,
                 "TMA destinations start on 128-byte boundaries");
   SmemGate<TL>& SG = *reinterpret_cast<SmemGate<TL>*>(smem_raw + sizeof(SM));
   // Launched with programmatic stream serialization (the plain 2D stage), a
@@ -592,8 +605,10 @@ __device__ __forceinline__ void stage_body(const StageArgs& a, const int trow, c
   // grid, in a stage that reads the FP32 image (and K), takes both as TMA
   // boxes: no boundary mapping, one instruction per array.  They are issued
   // first thing and land while the CTA sets up.
-  const bool tma = MODE != 2 && a.tma && (a.stage == 1 || a.stage == 2 || (a.stage == 0 && a.img_in)) &&
-                   x0 >= NG && x0 + TX + NG <= nx && y0 >= NG && y0 + TY + NG <= n1;
+  // (The second 3D pass has a z halo only; its boxes also cover the x halo
+  // columns, which it does not read.)
+  const bool tma = a.tma && (a.stage == 1 || a.stage == 2 || (a.stage == 0 && a.img_in)) && y0 >= NG &&
+                   y0 + TY + NG <= n1 && (MODE == 2 || (x0 >= NG && x0 + TX + NG <= nx));
   if (tma && tid == 0) {
     mbar_init(&S.mbar, 1);
     // boxes of the halo: padded column x0 - NG + NG, padded row y0, all fields
@@ -602,9 +617,12 @@ __device__ __forceinline__ void stage_body(const StageArgs& a, const int trow, c
     if constexpr (MODE == 0) {
       tma_load_3d(&S.q[0][0][0], MAP ? &a.tm_v2 : &a.tm_v, x0, y0, 0, &S.mbar);
       if (a.stage != 0) tma_load_3d(&S.fx[0][0][0], MAP ? &a.tm_k2 : &a.tm_k, x0, y0, 0, &S.mbar);
-    } else {  // the tile's z plane
+    } else if constexpr (MODE == 1) {  // the tile's z plane
       tma_load_4d(&S.q[0][0][0], &a.tm_v, x0, y0, g.G[2] + plane, 0, &S.mbar);
       if (a.stage != 0) tma_load_4d(&S.fx[0][0][0], &a.tm_k, x0, y0, g.G[2] + plane, 0, &S.mbar);
+    } else {  // the tile's y plane: boxes of x, one y, z rows and all fields
+      tma_load_4d(&S.q[0][0][0], &a.tm_v, x0, g.G[1] + plane, y0, 0, &S.mbar);
+      if (a.stage != 0) tma_load_4d(&S.kbox[0][0][0], &a.tm_k, x0, g.G[1] + plane, y0, 0, &S.mbar);
     }
   }
   if (a.stage == 1 || a.stage == 2 || tma) {
@@ -624,8 +642,10 @@ __device__ __forceinline__ void stage_body(const StageArgs& a, const int trow, c
   }
   // The own cells' FP64 state (stage 2) and, in the second 3D pass, the x + y
   // part of their divergence are needed only in phase C: they are copied into
-  // shared memory while phases A and B run.
-  if (CACHE && (a.stage == 2 || MODE == 2)) {
+  // shared memory while phases A and B run (a second-pass tile that took its
+  // K as a box, which shares their memory, copies them once phase A has read
+  // it).
+  auto own_copies = [&]() {
     for (int c = tid; c < TX * TY; c += NT) {
       int j = c / TX, i = c - j * TX;
       if (x0 + i >= nx || y0 + j >= n1) continue;
@@ -641,7 +661,8 @@ __device__ __forceinline__ void stage_body(const StageArgs& a, const int trow, c
       }
     }
     cp_async_commit();
-  }
+  };
+  if (CACHE && (a.stage == 2 || MODE == 2) && !(MODE == 2 && tma)) own_copies();
   const float dt = (a.stage == 1 || a.stage == 2) ? S.dt : 0.0f;
   const float coef = a.stage == 0 ? 0.0f : (a.stage == 1 ? dt : 0.25f * dt);
   float lam_max = 0.0f;
@@ -677,7 +698,7 @@ __device__ __forceinline__ void stage_body(const StageArgs& a, const int trow, c
 #pragma unroll
         for (int m = 0; m < NQ; ++m) {
           S.own.k[m][j][i] = rk[m];
-          if (a.stage == 2) S.own.v[m][j][i] = rv[m];
+          if (SM::OWNV && a.stage == 2) S.own.v[m][j][i] = rv[m];
         }
       }
     };
@@ -707,13 +728,46 @@ __device__ __forceinline__ void stage_body(const StageArgs& a, const int trow, c
         if (!(lam <= lam_max)) lam_max = lam;  // NaN propagates
       }
     };
-    if (tma) {  // the boxes have landed (barrier above)
+    if (tma && MODE == 2) {  // the boxes have landed (barrier above)
+      // K lies in the own cells' arrays: every thread reads its cells' values
+      // before any of those arrays is written
+      const float* kst = &S.kbox[0][0][0];
+      float rk[T::HPT][NQ], rv[T::HPT][NQ];
+#pragma unroll
+      for (int t = 0; t < T::HPT; ++t) {
+        const int h = tid + t * NT;
+        if (h >= T::NH) continue;
+        const int hy = h / T::QW, hx = h - hy * T::QW + T::QL;
+#pragma unroll
+        for (int m = 0; m < NQ; ++m) {
+          rv[t][m] = S.q[m][hy][hx];
+          if (a.stage != 0) rk[t][m] = kst[(m * T::HY + hy) * T::QP + hx];
+        }
+      }
+      __syncthreads();
+      if (CACHE) own_copies();
+#pragma unroll
+      for (int t = 0; t < T::HPT; ++t) {
+        const int h = tid + t * NT;
+        if (h >= T::NH) continue;
+        const int hy = h / T::QW, hx = h - hy * T::QW + T::QL;
+        const bool ownc = hy >= NG && hy < NG + TY;
+        float ld[NQ];
+        if (a.stage == 0) {
+#pragma unroll
+          for (int m = 0; m < NQ; ++m) ld[m] = rv[t][m];
+        } else {
+          stage_state(ld, rk[t], rv[t], hy, hx, ownc);
+        }
+        primitives(ld, hy, hx, false, false, ownc);
+      }
+    } else if (tma) {  // the boxes have landed (barrier above)
       const float* kst = &S.fx[0][0][0];  // K of tile and halo, [field][row][column] like q
 #pragma unroll
       for (int t = 0; t < T::HPT; ++t) {
         const int h = tid + t * NT;
         if (h >= T::NH) continue;
-        const int hy = h / T::QW, hx = h - hy * T::QW;
+        const int hy = h / T::QW, hx = h - hy * T::QW + T::QL;
         const bool ownc = hx >= T::QX && hx < T::QX + TX && hy >= NG && hy < NG + TY;
         float ld[NQ];
         if (a.stage == 0) {
@@ -738,7 +792,7 @@ __device__ __forceinline__ void stage_body(const StageArgs& a, const int trow, c
 #pragma unroll
       for (int t = 0; t < T::HPT; ++t) {
         int h = tid + t * NT;
-        int hy = h / T::QW, hx = h - hy * T::QW;
+        int hy = h / T::QW, hx = h - hy * T::QW + T::QL;
         int gx = x0 + hx - T::QX, ga = y0 + hy - NG;
         bool outx = gx < 0 || gx >= nx, outa = ga < 0 || ga >= n1;
         // corners are never read, nor (without x faces) columns past the grid
@@ -786,7 +840,7 @@ __device__ __forceinline__ void stage_body(const StageArgs& a, const int trow, c
 #pragma unroll
       for (int t = 0; t < T::HPT; ++t) {
         if (hh[t] < 0) continue;
-        const int hy = hh[t] / T::QW, hx = hh[t] - hy * T::QW;
+        const int hy = hh[t] / T::QW, hx = hh[t] - hy * T::QW + T::QL;
         if (a.stage == 1 || a.stage == 2) stage_state(ld[t], rk[t], rv[t], hy, hx, own[t]);
         primitives(ld[t], hy, hx, flx[t], fla[t], own[t]);
       }
@@ -1118,7 +1172,7 @@ __device__ __forceinline__ void stage_body(const StageArgs& a, const int trow, c
         if (a.img_out) a.img_out[(NQ - 3) * N32 + gf] = f64_to_f32(uE - uPi);
         // admissibility of the new state (rho > 0, Gamma > 0, (Gamma+1) p + Pi > 0)
         // from its FP32 image: a diagnostic, not part of the update
-        auto v = [&](int m) { return CACHE ? S.own.v[m][j][i] : a.U32[m * N32 + gf]; };
+        auto v = [&](int m) { return SM::OWNV ? S.own.v[m][j][i] : a.U32[m * N32 + gf]; };
         float rho = v(0) + d[0];
         float msq = 0.0f;
 #pragma unroll
@@ -1459,8 +1513,10 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_tiled() {
   return fn;
 }
 
+// pass2 (3D): boxes of the second pass's tile -- HXP columns x one y plane x
+// HY z rows x all fields
 template <class TL>
-static bool encode_map(const GridDev& g, const float* buf, CUtensorMap* out) {
+static bool encode_map(const GridDev& g, const float* buf, CUtensorMap* out, bool pass2 = false) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = encode_tiled();
   if (!enc || !buf) return false;
   // 2D (padded column, padded row, field), 3D (padded column, padded row,
@@ -1477,6 +1533,10 @@ static bool encode_map(const GridDev& g, const float* buf, CUtensorMap* out) {
     strides[2] = (cuuint64_t)g.N32 * sizeof(float);
     box[2] = 1;
     box[3] = (cuuint32_t)g.nv;
+    if (pass2) {
+      box[1] = 1;
+      box[2] = (cuuint32_t)TL::HY;
+    }
   }
   const cuuint32_t estr[4] = {1, 1, 1, 1};
   CUresult r = enc(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, rank, const_cast<float*>(buf), dims, strides, box, estr,
@@ -1496,6 +1556,8 @@ bool fused2d_encode_map(const GridDev& g, int tile, const float* buf, CUtensorMa
     case 1: return encode_map<TileB>(g, buf, out);
     case 2: return encode_map<TileC>(g, buf, out);
     case 4: return g.ndim == 2 && encode_map<TileH>(g, buf, out);  // the closing rows of tile 3
+    case 6: return g.ndim == 3 && encode_map<TileA>(g, buf, out, true);  // second 3D pass, tile 0
+    case 7: return g.ndim == 3 && encode_map<TileC>(g, buf, out, true);  // second 3D pass, tile 2
     default: return encode_map<TileA>(g, buf, out);
   }
 }
@@ -1533,7 +1595,7 @@ void launch_stage2d_band(const GridDev& g, int stage, double* U, float* U32, con
 
 template <class TL>
 static void stage3d_passes(const GridDev& g, const StageArgs& a0, uint8_t* mask_x, uint8_t* mask_y, uint8_t* mask_z,
-                           bool census, bool pdl, cudaStream_t s) {
+                           bool census, bool pdl, const CUtensorMap* tmk2, const CUtensorMap* tmv2, cudaStream_t s) {
   StageArgs a = a0;
   // pass 1: x and y faces of every z plane -> x + y part of the divergence
   // (interior tiles by TMA when a0 carries the descriptors)
@@ -1546,9 +1608,15 @@ static void stage3d_passes(const GridDev& g, const StageArgs& a0, uint8_t* mask_
   else
     launch_k<0, 7, 1, TL>(g1, pdl, s, a);
   // pass 2: z faces of every y plane, the whole divergence and the RK stage
+  // (interior z rows by TMA with the second pair of descriptors)
   a.mask_x = nullptr;
   a.mask_a = mask_z;
-  a.tma = 0;
+  if (a0.tma && tmk2 && tmv2) {
+    a.tm_k = *tmk2;
+    a.tm_v = *tmv2;
+  } else {
+    a.tma = 0;
+  }
   a.clear0 = a0.clear0;
   a.clear1 = a0.clear1;
   dim3 g2((g.n[0] + TL::TX - 1) / TL::TX, (g.n[2] + TL::TY - 1) / TL::TY, g.n[1]);
@@ -1563,7 +1631,7 @@ void launch_stage3d(const GridDev& g, int stage, double* U, float* U32, const fl
                     uint8_t* mask_y, uint8_t* mask_z, float eps_rel, int mood, int weights, unsigned long long* nbad,
                     unsigned long long* census, int tile, bool pdl, bool img_in, float* img_out,
                     unsigned long long* clear0, unsigned long long* clear1, const CUtensorMap* tmk,
-                    const CUtensorMap* tmv, cudaStream_t s) {
+                    const CUtensorMap* tmv, const CUtensorMap* tmk2, const CUtensorMap* tmv2, cudaStream_t s) {
   StageArgs a = stage_args(g, stage, U, U32, Kin, Kout, dt_fixed, cfl, lmax, dt_out, eps_rel, mood, weights, nbad);
   a.clear0 = clear0;
   a.clear1 = clear1;
@@ -1577,9 +1645,9 @@ void launch_stage3d(const GridDev& g, int stage, double* U, float* U32, const fl
   a.img_in = img_in ? 1 : 0;
   a.img_out = img_out;
   if (tile == 2)
-    stage3d_passes<TileC>(g, a, mask_x, mask_y, mask_z, census != nullptr, pdl, s);
+    stage3d_passes<TileC>(g, a, mask_x, mask_y, mask_z, census != nullptr, pdl, tmk2, tmv2, s);
   else
-    stage3d_passes<TileA>(g, a, mask_x, mask_y, mask_z, census != nullptr, pdl, s);
+    stage3d_passes<TileA>(g, a, mask_x, mask_y, mask_z, census != nullptr, pdl, tmk2, tmv2, s);
 }
 
 }  // namespace ws

@@ -214,8 +214,9 @@ void launch_stage2d(const GridDev& g, int stage, double* U, float* U32, const fl
 // interior tiles then load both as boxes.
 // Describes an FP32 buffer of the fused 2D or 3D layout (g.st32, g.N32, g.nv
 // fields) with boxes of one tile's halo (of one z plane in 3D); false if the
-// driver refuses.  3D: tile 0 or 2 (the first pass's tiles); 2D: 0..3, and
-// 4 for the boxes of tile 3's closing rows.
+// driver refuses.  3D: tile 0 or 2 (the first pass's tiles), and 6 or 7
+// for the second pass's boxes of those tiles; 2D: 0..3, and 4 for the boxes
+// of tile 3's closing rows.
 bool fused2d_encode_map(const GridDev& g, int tile, const float* buf, CUtensorMap* out);
 // census (nullable, without a gate): the same stage, also counting the
 // flat-stencil decisions into census[4] (face-variables, flat ones, warp
@@ -229,7 +230,10 @@ void launch_stage3d(const GridDev& g, int stage, double* U, float* U32, const fl
                     uint8_t* mask_y, uint8_t* mask_z, float eps_rel, int mood, int weights, unsigned long long* nbad,
                     unsigned long long* census, int tile, bool pdl, bool img_in, float* img_out,
                     unsigned long long* clear0, unsigned long long* clear1, const CUtensorMap* tmk,
-                    const CUtensorMap* tmv, cudaStream_t s);
+                    const CUtensorMap* tmv, const CUtensorMap* tmk2, const CUtensorMap* tmv2, cudaStream_t s);
+// tmk2, tmv2 (nullable, with tmk and tmv): descriptors of the second pass's
+// boxes (fused2d_encode_map codes 6 and 7); interior z rows of the second
+// pass then load by TMA
 void launch_gate_decide(const float* lstat, unsigned long long* nbad, unsigned long long* lmax, int flags, int* redo,
                         double* stats, int* drift_dev, cudaGraphConditionalHandle cond, cudaStream_t s);
 void launch_restore(const int* redo, const double* src, double* dst, int64_t n, cudaStream_t s);
