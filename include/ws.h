@@ -295,7 +295,8 @@ WS_API int ws_gate_stats(ws_ctx *ctx, double out[6]);
  *    -- the loads: 0 every CTA loads its tile and 3-cell halo cell by cell,
  *    applying the boundary conditions; 1 a CTA whose halo lies inside the
  *    grid loads the stage's FP32 image and increments as two TMA boxes (the
- *    others as with 0; in 3D the first pass, of x and y faces) -- and the
+ *    others as with 0; in the second 3D pass, of z faces, a CTA whose z halo
+ *    lies inside the grid) -- and the
  *    launch schedule: 0 one launch per
  *    stage (per pass in 3D), consecutive launches with programmatic
  *    dependent launch (the next launch's CTAs wait on the device for the

@@ -49,7 +49,7 @@ static void set_tail_rows(ws_ctx* c) {
 }
 
 // fused 2D and 3D: TMA descriptors of the FP32 buffers for the current tile
-// shape (3D: of the first pass)
+// shape (3D: of the first pass, and [5..9] of the second)
 void encode_maps(ws_ctx* c) {
   c->tmap_ok = 0;
   if (!c->fused) return;
@@ -1126,7 +1126,7 @@ int ws_gate_stats(ws_ctx* c, double out[6]) {
 // Fused stage configurations: index = 2 x tile slot + schedule (0 stage
 // launches with programmatic dependent launch, 1 plain stage launches).
 // Stage configurations: index = (2 x tile + loads) x 2 + schedule (loads: 0
-// cell by cell, 1 TMA boxes for interior tiles -- in 3D, of the first pass).
+// cell by cell, 1 TMA boxes for interior tiles -- in 3D, of both passes).
 static int stage_load_modes(const ws_ctx*) { return 2; }
 
 static bool stage_config_valid(const ws_ctx* c, int index) {

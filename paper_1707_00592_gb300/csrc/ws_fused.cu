@@ -48,13 +48,12 @@
 // The FP32 buffers (image, K, the 3D partial divergence) have a layout of
 // their own (GridDev st32, N32): their rows are padded to a multiple of four
 // floats, so that the halo of every tile starts on a 16-byte boundary (padded
-// column x0 - 3 + 3 = x0, a multiple of 32).  A tile of the 2D stage or of
-// the first 3D pass whose halo lies inside the grid then loads the image and
-// K of tile and halo as two TMA boxes (cp.async.bulk.tensor, completion on an
-// mbarrier) straight into shared memory, with no per-cell address
-// arithmetic; tiles on the boundary, the FP64 loads of a first stage 0 and
-// the second 3D pass load cell by cell and apply the boundary conditions
-// while loading.
+// column x0 - 3 + 3 = x0, a multiple of 32).  A tile whose halo lies inside
+// the grid (in the second 3D pass: whose z halo does) then loads the image
+// and K of tile and halo as two TMA boxes (cp.async.bulk.tensor, completion
+// on an mbarrier) straight into shared memory, with no per-cell address
+// arithmetic; tiles on the boundary and the FP64 loads of a first stage 0
+// load cell by cell and apply the boundary conditions while loading.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
