@@ -133,13 +133,20 @@ struct Smem {
   alignas(128) float fx[T::XF ? NQ_ + 1 : 1][TY][TX + 1];
   float fy[NQ_ + 1][TY + 1][TX];              // fluxes + face velocity of the faces along the tile's 2nd axis
   static constexpr bool OWNV = CACHE && MODE != 2;  // the own cells' image kept (the second 3D pass reads it)
+  // the second pass's K box lies over k, v, l and this padding, not over u,
+  // so that u can be copied in while the box is still being read
+  static constexpr int KBOX = MODE == 2 ? (int)sizeof(float) * NQ_ * HY * T::QP : 0;
+  static constexpr int KVL = (int)sizeof(float) * TY * TX * ((CACHE ? NQ_ : 1) + (OWNV ? NQ_ : 1)) +
+                             (int)sizeof(float) * (MODE == 2 ? NQ_ * TY * TX : 1);
+  static constexpr int PAD = KBOX > KVL ? (KBOX - KVL + 7) / 8 * 8 : 8;
   union alignas(128) {
     struct {                                     // this tile's own cells, for phase C
-      double u[CACHE ? NQ_ : 1][TY][TX];         // stage 2: FP64 state, copied in asynchronously
       float k[CACHE ? NQ_ : 1][TY][TX];          // stages 1, 2: accumulated increments (kept from the phase-A loads)
       float v[OWNV ? NQ_ : 1][TY][TX];           // stage 2: FP32 image of U^n (kept from the phase-A loads)
       // 3D second pass: x + y part of the divergence (asynchronous copy)
       float l[MODE == 2 ? NQ_ : 1][MODE == 2 ? TY : 1][MODE == 2 ? TX : 1];
+      alignas(8) char pad[PAD];
+      double u[CACHE ? NQ_ : 1][TY][TX];         // stage 2: FP64 state, copied in asynchronously
     } own;
     __nv_bfloat16 feat[GATE == 1 ? NF : 1][24];  // gate inputs (read before the reconstruction)
     // 3D second pass, TMA load: the increments K of tile and z halo, read in
@@ -568,6 +575,7 @@ __device__ __forceinline__ void stage_body(const StageArgs& a, const int trow, c
   static_assert(T::QP * sizeof(float) % 16 == 0, "TMA box rows are multiples of 16 bytes");
   static_assert(offsetof(SM, q) % 128 == 0 && offsetof(SM, fx) % 128 == 0 && offsetof(SM, kbox) % 128 == 0,
                 "TMA destinations start on 128-byte boundaries");
+  static_assert(MODE != 2 || offsetof(decltype(S.own), u) >= sizeof(S.kbox), "the K box reaches the FP64 copies");
   SmemGate<TL>& SG = *reinterpret_cast<SmemGate<TL>*>(smem_raw + sizeof(SM));
   // Launched with programmatic stream serialization (the plain 2D stage), a
   // CTA may become resident while the previous stage is still finishing: it
@@ -644,16 +652,16 @@ __device__ __forceinline__ void stage_body(const StageArgs& a, const int trow, c
   // shared memory while phases A and B run (a second-pass tile that took its
   // K as a box, which shares their memory, copies them once phase A has read
   // it).
-  auto own_copies = [&]() {
+  auto own_copies = [&](bool u, bool l) {
     for (int c = tid; c < TX * TY; c += NT) {
       int j = c / TX, i = c - j * TX;
       if (x0 + i >= nx || y0 + j >= n1) continue;
-      int64_t gi = pbase + (int64_t)(g.G[AX1] + y0 + j) * S1 + x0 + i;
-      if (a.stage == 2) {
+      if (u) {
+        const int64_t gi = pbase + (int64_t)(g.G[AX1] + y0 + j) * S1 + x0 + i;
 #pragma unroll
         for (int m = 0; m < NQ; ++m) cp_async8(&S.own.u[m][j][i], &a.U[m * N + gi]);
       }
-      if constexpr (MODE == 2) {
+      if (MODE == 2 && l) {
         const int64_t gf = idx32(y0 + j, x0 + i);
 #pragma unroll
         for (int m = 0; m < NQ; ++m) cp_async4(&S.own.l[m][j][i], &a.Lp[m * N32 + gf]);
@@ -661,7 +669,7 @@ __device__ __forceinline__ void stage_body(const StageArgs& a, const int trow, c
     }
     cp_async_commit();
   };
-  if (CACHE && (a.stage == 2 || MODE == 2) && !(MODE == 2 && tma)) own_copies();
+  if (CACHE && (a.stage == 2 || MODE == 2)) own_copies(a.stage == 2, !(MODE == 2 && tma));
   const float dt = (a.stage == 1 || a.stage == 2) ? S.dt : 0.0f;
   const float coef = a.stage == 0 ? 0.0f : (a.stage == 1 ? dt : 0.25f * dt);
   float lam_max = 0.0f;
@@ -744,7 +752,7 @@ __device__ __forceinline__ void stage_body(const StageArgs& a, const int trow, c
         }
       }
       __syncthreads();
-      if (CACHE) own_copies();
+      if (CACHE) own_copies(false, true);
 #pragma unroll
       for (int t = 0; t < T::HPT; ++t) {
         const int h = tid + t * NT;
