@@ -395,8 +395,20 @@ def time_tubes(ws, stream, steps, seed=0, run_steps=1000, sample=64):
         b = U64[0, soff[k] + 3:soff[k + 1] - 3]
         num += float(np.abs(a - b).sum())
         den += float(np.abs(b).sum())
+    # the method's flops of a step: every tube's faces (one more than its
+    # cells) and cells, three stages; over the step's event time (the graph
+    # of the three stage launches)
+    ntubes = len(off) - 1
+    flops = 3 * ((cells + ntubes) * face_flops(1) + cells * (prim_flops(1) + divergence_flops(1)))
+    achieved = flops / (ms / steps * 1e-3) / 1e12
+    roofline = {"bound": "alu", "kernel": "persistent tube stage (mixed), three launches per step", "achieved": achieved,
+                "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
+                "flops_per_step": flops,
+                "flops_source": f"the method's flops (op-counting build of the FP64 oracle): {face_flops(1)} per "
+                                f"face, {prim_flops(1) + divergence_flops(1)} per cell and stage",
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 flops per FMA x 2.07 GHz"}
     return {"value": cells * steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps, "tubes": 4096,
-            "cells": cells, "chunk_config": choice, "graph": True, "nonphysical_cells": bad,
+            "cells": cells, "chunk_config": choice, "graph": True, "roofline": roofline, "nonphysical_cells": bad,
             "nonphysical_tubes": len(bad_tubes), "nonphysical_tubes_fp64_alone": same,
             "run_steps": run_steps, "timed_steps": f"{steps} spread evenly over the {run_steps}-step run",
             "workload": "4096 Riemann tubes, lengths log-uniform in [256, 8192], per-tube CFL, mixed precision",
