@@ -306,8 +306,9 @@ WS_API int ws_gate_stats(ws_ctx *ctx, double out[6]);
  *    (16 candidates), 0, 1 = 32 x 15, 32 x 7 in 3D (8 candidates).
  *    ws_get_stage_config reports the choice.
  *  - Batched tubes in mixed precision: the chunk of cells a CTA of the
- *    persistent stage kernel processes and its thread count, from (256, 128),
- *    (256, 256), (512, 256), (512, 512), (1024, 512).
+ *    persistent stage kernel processes and its thread count, from (255, 128),
+ *    (255, 256), (511, 256), (511, 512), (1023, 512) (a chunk of 2^k - 1
+ *    cells has 2^k faces, a whole number per thread).
  * *choice (HOST, nullable) receives the index chosen, or -1 when the context
  * has nothing to tune.  Allocates a scratch state for the duration of the
  * call.  Synchronises.  The choice stays with the context (a CUDA graph of

@@ -4,9 +4,11 @@
 // so tubes of very different lengths balance across the GPU.  Per chunk the
 // phases mirror the 2D fused stage: FP32 primitives of the chunk plus a
 // 3-cell halo in shared memory (transmissive tube ends applied on load, E - Pi
-// in FP64), WENO-IS per (face, characteristic variable) with the linear
-// weights for stencils flat to 1e-6, back-projection / MOOD / HLLC per face,
-// and the increment-form SSP-RK3 with FP64 accumulation (see ws_fused.cu).
+// in FP64); one loop over the faces, each thread taking a face through
+// WENO-IS of its characteristic variables (the linear weights for stencils
+// flat to 1e-6), back-projection, MOOD and HLLC; and the increment-form
+// SSP-RK3 with FP64 accumulation (see ws_fused.cu).  A chunk of CH = 2^k - 1
+// cells has 2^k faces, a whole number per thread.
 // Stage 0 also reduces each tube's CFL rate (atomicMax per tube); stages 1
 // and 2 take dt = CFL / max per tube.
 #include <cuda_runtime.h>
@@ -25,7 +27,6 @@ constexpr int NQ = 5;  // rho, u, p, Gamma, Pi
 template <int CH>
 struct TSmem {
   float q[NQ + 1][CH + 2 * NG];  // primitives + sound speed
-  float w[2][NQ][CH + 1];        // reconstructed characteristics per side
   float F[NQ + 1][CH + 1];       // face fluxes + face velocity
   int item;
   float dt;
@@ -54,7 +55,7 @@ struct TubeArgs {
 };
 
 template <int CH, int NTH>
-__global__ void __launch_bounds__(NTH) k_tube_stage(TubeArgs a) {
+__global__ void __launch_bounds__(NTH, 1024 / NTH) k_tube_stage(TubeArgs a) {  // 64 registers
   extern __shared__ __align__(16) unsigned char smem_raw[];
   TSmem<CH>& S = *reinterpret_cast<TSmem<CH>*>(smem_raw);
   constexpr int HW = CH + 2 * NG;
@@ -136,52 +137,41 @@ __global__ void __launch_bounds__(NTH) k_tube_stage(TubeArgs a) {
       for (int w = 0; w < NTH / 32; ++w) b = S.red[w] > b ? S.red[w] : b;
       if (b) atomicMax(&a.lmax[tube], b);
     }
-    // ---- phase B1: faces f = 0..nc (face f between chunk cells f-1 and f) ----
+    // ---- phase B: faces f = 0..nc (face f between chunk cells f-1 and f) ----
     const int nf = nc + 1;
-    for (int it = tid; it < NQ * nf; it += NTH) {
-      int r = it / nf, f = it - r * nf;
-      int h0 = f;  // stencil cell 0 = chunk cell f-3 -> halo index f
-      float rho_bar = 0.5f * (S.q[0][h0 + 2] + S.q[0][h0 + 3]);
-      float c_bar = 0.5f * (S.q[5][h0 + 2] + S.q[5][h0 + 3]);
-      float w[6];
-      if (r == 0 || r == NQ - 1) {
-        float rc = r == 0 ? -(rho_bar * c_bar) : rho_bar * c_bar;
-#pragma unroll
-        for (int k = 0; k < 6; ++k) w[k] = 0.5f * fmaf(rc, S.q[1][h0 + k], S.q[2][h0 + k]);
-      } else if (r == 1) {
-        float mic2 = -frcp(c_bar * c_bar);
-#pragma unroll
-        for (int k = 0; k < 6; ++k) w[k] = fmaf(mic2, S.q[2][h0 + k], S.q[0][h0 + k]);
-      } else {
-        int fld = r + 1;  // Gamma (r = 2), Pi (r = 3)
-#pragma unroll
-        for (int k = 0; k < 6; ++k) w[k] = S.q[fld][h0 + k];
-      }
-      float mn = fminf(fmin3(w[0], w[1], w[2]), fmin3(w[3], w[4], w[5]));
-      float mx = fmaxf(fmax3(w[0], w[1], w[2]), fmax3(w[3], w[4], w[5]));
-      // both sides at once: lanes (left, right) of the mirrored stencils
-      float2 p0 = make_float2(w[0], w[5]), p1 = make_float2(w[1], w[4]), p2 = make_float2(w[2], w[3]);
-      float2 p3 = make_float2(w[3], w[2]), p4 = make_float2(w[4], w[1]);
-      float2 v;
-      if (mx - mn <= 1e-6f * fmaxf(fabsf(mx), fabsf(mn)))
-        v = linear5_pair(p0, p1, p2, p3, p4);
-      else
-        v = weno5_pair(p0, p1, p2, p3, p4, a.P);
-      S.w[0][r][f] = v.x;
-      S.w[1][r][f] = v.y;
-    }
-    __syncthreads();
-    // ---- phase B2 ----
     for (int f = tid; f < nf; f += NTH) {
-      int ha = f + 2, hb = f + 3;
+      const int ha = f + 2, hb = f + 3, h0 = f;  // stencil cell 0 = chunk cell f-3 -> halo index f
       float rho_bar = 0.5f * (S.q[0][ha] + S.q[0][hb]);
       float c_bar = 0.5f * (S.q[5][ha] + S.q[5][hb]);
       float c2 = c_bar * c_bar, rc = rho_bar * c_bar;
       float inv = frcp(c2 * rc);
       float ic2 = rc * inv, irc = c2 * inv;
+      const float mic2 = -frcp(c2);
       float2 W[NQ], Q[NQ];  // (left, right) characteristics, then primitives
 #pragma unroll
-      for (int r = 0; r < NQ; ++r) W[r] = make_float2(S.w[0][r][f], S.w[1][r][f]);
+      for (int r = 0; r < NQ; ++r) {
+        float w[6];
+        if (r == 0 || r == NQ - 1) {
+          const float rcs = r == 0 ? -rc : rc;
+#pragma unroll
+          for (int k = 0; k < 6; ++k) w[k] = 0.5f * fmaf(rcs, S.q[1][h0 + k], S.q[2][h0 + k]);
+        } else if (r == 1) {
+#pragma unroll
+          for (int k = 0; k < 6; ++k) w[k] = fmaf(mic2, S.q[2][h0 + k], S.q[0][h0 + k]);
+        } else {
+#pragma unroll
+          for (int k = 0; k < 6; ++k) w[k] = S.q[r + 1][h0 + k];  // Gamma (r = 2), Pi (r = 3)
+        }
+        float mn = fminf(fmin3(w[0], w[1], w[2]), fmin3(w[3], w[4], w[5]));
+        float mx = fmaxf(fmax3(w[0], w[1], w[2]), fmax3(w[3], w[4], w[5]));
+        // both sides at once: lanes (left, right) of the mirrored stencils
+        float2 p0 = make_float2(w[0], w[5]), p1 = make_float2(w[1], w[4]), p2 = make_float2(w[2], w[3]);
+        float2 p3 = make_float2(w[3], w[2]), p4 = make_float2(w[4], w[1]);
+        if (mx - mn <= 1e-6f * fmaxf(fabsf(mx), fabsf(mn)))
+          W[r] = linear5_pair(p0, p1, p2, p3, p4);
+        else
+          W[r] = weno5_pair(p0, p1, p2, p3, p4, a.P);
+      }
       back_project_pair<NQ>(W, ic2, irc, Q);
       int code[2] = {0, 0};
       if (a.mood) {
@@ -293,8 +283,9 @@ void launch_one(const TubeArgs& a, int ctas_per_sm, cudaStream_t s) {
 
 }  // namespace
 
-// configurations the autotuner chooses from: chunk size x threads
-const int kTubeConfigs[][2] = {{256, 128}, {256, 256}, {512, 256}, {512, 512}, {1024, 512}};
+// configurations the autotuner chooses from: chunk size x threads (a chunk of
+// 2^k - 1 cells has 2^k faces)
+const int kTubeConfigs[][2] = {{255, 128}, {255, 256}, {511, 256}, {511, 512}, {1023, 512}};
 const int kNumTubeConfigs = 5;
 
 int tube_chunk_size(int config) { return kTubeConfigs[config][0]; }
@@ -324,11 +315,11 @@ void launch_tubes_stage_mixed(const TubesDev& t, int config, int stage, double* 
   a.mood = mood;
   a.nbad = nbad;
   switch (config) {
-    case 0: launch_one<256, 128>(a, 8, s); break;
-    case 1: launch_one<256, 256>(a, 4, s); break;
-    case 2: launch_one<512, 256>(a, 4, s); break;
-    case 3: launch_one<512, 512>(a, 2, s); break;
-    default: launch_one<1024, 512>(a, 2, s); break;
+    case 0: launch_one<255, 128>(a, 8, s); break;
+    case 1: launch_one<255, 256>(a, 4, s); break;
+    case 2: launch_one<511, 256>(a, 4, s); break;
+    case 3: launch_one<511, 512>(a, 2, s); break;
+    default: launch_one<1023, 512>(a, 2, s); break;
   }
 }
 
